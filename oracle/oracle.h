@@ -1,0 +1,105 @@
+/*
+ * CPU checker for the combined ray query of Bartels & Harada, "Combining GPU
+ * Tracing Methods within a Single Ray Query" (SIGGRAPH Asia 2022 Technical
+ * Communications).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is loaded by the test-suite, by the
+ * smoke check and by the CPU-baseline leg of the benchmark, and by nothing
+ * else.  It shares no source, header, table or helper with the device
+ * library; the only thing both sides see is the seeded input (triangles,
+ * rays, grid extents) produced by the separate `synth` generators.
+ *
+ * Plain, slow, obviously correct: double precision throughout (the "fp64"
+ * ground truth), plus a float mode of the distance-field march that performs
+ * the stated step rule operation by operation in IEEE single precision.
+ *
+ * Conventions
+ *   rays   : float32, 8 per ray: ox oy oz t_min dx dy dz t_max (Eq. 1, d unit)
+ *   mesh   : double vertices (nv*3), int32 triangles (nt*3)
+ *   grid   : values at lo + (i,j,k)*h, h = (hi-lo)/(n-1), x fastest
+ *   hits   : or_hit records; miss = {t=+inf, prim=-1, tracer=0}
+ */
+#ifndef GB300_RQ_ORACLE_H
+#define GB300_RQ_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double t, u, v;
+    int32_t prim;      /* triangle index, -1 for a miss or a distance-field hit */
+    int32_t tracer;    /* 0 miss, 1 triangle (BVH) segment, 2 distance-field segment */
+    uint32_t flags;    /* OR_FLAG_* */
+    int32_t steps;     /* distance-field march steps taken by this query */
+} or_hit;
+
+#define OR_FLAG_STEP_LIMIT 2u
+
+typedef struct {
+    int32_t mode;       /* 0 triangles only, 1 one split, 2 two splits, 3 distance field only */
+    int32_t any_hit;    /* f of Eq. 1: 0 closest hit, 1 any hit */
+    double m_near;      /* multiplier on the voxel size for t_1 (may be +inf) */
+    double m_far;       /* multiplier on the voxel size for t_2 (mode 2, may be +inf) */
+    int32_t max_steps;  /* march step limit */
+    int32_t pad;
+    double hit_eps_vox; /* hit threshold, in units of the smallest voxel edge */
+    double min_step_vox;/* minimum march step, same units */
+} or_params;
+
+typedef struct or_bvh or_bvh;
+typedef struct or_grid or_grid;
+
+/* Watertight ray/triangle test (Woop, Benthin & Wald, JCGT 2(1), 2013), fp64.
+ * Returns 1 when the ray's line meets the triangle; out = {t, u, v}. */
+int or_watertight(const double o[3], const double d[3], const double a[3], const double b[3],
+                  const double c[3], double out[3]);
+
+/* Closest hit by definition: every triangle tested, t in [t_min, t_max]. */
+void or_trace_brute(const double* V, const int32_t* F, int64_t nt, const float* rays, int64_t nr,
+                    int32_t nthreads, or_hit* hits);
+
+or_bvh* or_bvh_build(const double* V, int64_t nv, const int32_t* F, int64_t nt);
+void or_bvh_free(or_bvh* b);
+int64_t or_bvh_node_count(const or_bvh* b);
+void or_trace_bvh(const or_bvh* b, const float* rays, int64_t nr, int32_t any_hit, int32_t nthreads,
+                  or_hit* hits);
+
+/* Signed distance: exact closest point on the nearest triangle, sign from the
+ * angle-weighted pseudonormal of the closest feature.  feature[i] (nullable) =
+ * tri*8 + region (0 face, 1..3 vertex a/b/c, 4 edge ab, 5 edge bc, 6 edge ca). */
+void or_sdf_points_brute(const double* V, int64_t nv, const int32_t* F, int64_t nt, const double* P,
+                         int64_t np, int32_t nthreads, double* out, int64_t* feature);
+void or_sdf_points_bvh(const or_bvh* b, const double* P, int64_t np, int32_t nthreads, double* out,
+                       int64_t* feature);
+
+/* Grid of values at lo + (i,j,k)h.  values != NULL: dense copy; else values are
+ * computed on first use from `src` by or_sdf_points_bvh. */
+or_grid* or_grid_new(const double lo[3], const double hi[3], const int32_t n[3], const double* values,
+                     const or_bvh* src);
+void or_grid_free(or_grid* g);
+void or_grid_values(or_grid* g, const int64_t* idx, int64_t count, int32_t nthreads, double* out);
+
+/* Queries.  precision 64: everything in double; precision 32: the distance-field
+ * segment, the split and the trilinear sample in IEEE single precision (the
+ * triangle segments stay in double). */
+void or_trace_sdf(const or_grid* g, const float* rays, int64_t nr, const or_params* p, int32_t precision,
+                  int32_t nthreads, or_hit* hits);
+void or_trace_combined(const or_bvh* b, const or_grid* g, const float* rays, int64_t nr,
+                       const or_params* p, int32_t precision, int32_t nthreads, or_hit* hits);
+
+/* Trilinear value and gradient of the grid interpolant at points (fp64). */
+void or_grid_sample(const or_grid* g, const double* P, int64_t np, double* phi, double* grad);
+
+/* Adjoint of the distance-field hit distance (implicit differentiation at the
+ * root of phi = eps_hit inside the last march step).  For each ray with an SDF
+ * hit: t_root[i], and the 8 corner indices / weights dt/dtheta. Rays that miss:
+ * t_root = +inf, idx = -1. */
+void or_sdf_root_adjoint(const or_grid* g, const float* rays, int64_t nr, const or_params* p,
+                         double* t_root, int64_t* idx8, double* dtdtheta8);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,183 @@
+"""Seeded ray batches shaped like the paper's workloads.
+
+The paper's queries (Section 3) start at the surface point each pixel sees,
+run in tiles across the viewport, and have randomised, divergent directions
+within a tile.  Here:
+
+* primary rays: a pinhole camera, one ray through each pixel centre, emitted
+  in 8x8 pixel tiles;
+* GI rays: one cosine-weighted hemisphere ray per pixel from a point on a
+  camera-facing surface inside the view frustum.  Origins are sampled on the
+  triangles by area (not found by tracing primary rays, so that producing the
+  input never runs any part of the query), projected to their pixel and sorted
+  into the same 8x8 tile order, which keeps the per-tile spatial coherence of
+  the paper's set-up while the directions stay random;
+* free-space rays: uniform origins away from every object, uniform directions.
+
+Ray layout (float32, 8 per ray): ox, oy, oz, t_min, dx, dy, dz, t_max, the
+query (o, d, t_min, t_max) of Eq. 1 with d normalised.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import rng
+from .scene import Scene
+
+_S_GI_POS = 11
+_S_GI_DIR = 12
+_S_FREE = 13
+_S_AO = 14
+_S_SHADOW = 15
+TILE = 8
+
+
+def _tile_order(px: np.ndarray, py: np.ndarray, width: int) -> np.ndarray:
+    ntx = (width + TILE - 1) // TILE
+    key = ((py // TILE) * ntx + (px // TILE)) * (TILE * TILE) + (py % TILE) * TILE + (px % TILE)
+    return np.argsort(key, kind="stable")
+
+
+def pack(o: np.ndarray, d: np.ndarray, tmin, tmax) -> np.ndarray:
+    n = o.shape[0]
+    r = np.empty((n, 8), dtype=np.float32)
+    r[:, 0:3] = o
+    r[:, 3] = tmin
+    r[:, 4:7] = d
+    r[:, 7] = tmax
+    return r
+
+
+def primary_rays(scene: Scene, width: int | None = None, height: int | None = None,
+                 t_max: float | None = None) -> np.ndarray:
+    cam = scene.camera
+    W = width or cam.width
+    H = height or cam.height
+    py, px = np.mgrid[0:H, 0:W]
+    px = px.ravel()
+    py = py.ravel()
+    order = _tile_order(px, py, W)
+    px, py = px[order], py[order]
+    aspect = W / H
+    x = (2 * (px + 0.5) / W - 1) * cam.tan_half_fov * aspect
+    y = (1 - 2 * (py + 0.5) / H) * cam.tan_half_fov
+    d = cam.forward[None, :] + x[:, None] * cam.right[None, :] + y[:, None] * cam.up[None, :]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o = np.broadcast_to(cam.eye, d.shape)
+    tm = 1.01 * scene.diagonal if t_max is None else t_max
+    return _renorm(pack(o, d, 0.0, tm))
+
+
+def _renorm(r: np.ndarray) -> np.ndarray:
+    """Make the float32 direction unit length in float64 and round once."""
+    d = r[:, 4:7].astype(np.float64)
+    r[:, 4:7] = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    return r
+
+
+def onb(n: np.ndarray):
+    """Orthonormal basis around unit vectors n (Duff et al., JCGT 2017)."""
+    sign = np.where(n[:, 2] >= 0, 1.0, -1.0)
+    a = -1.0 / (sign + n[:, 2])
+    b = n[:, 0] * n[:, 1] * a
+    b1 = np.stack([1 + sign * n[:, 0] ** 2 * a, sign * b, -sign * n[:, 0]], axis=1)
+    b2 = np.stack([b, sign + n[:, 1] ** 2 * a, -n[:, 1]], axis=1)
+    return b1, b2
+
+
+def cosine_hemisphere(n: np.ndarray, u1: np.ndarray, u2: np.ndarray) -> np.ndarray:
+    """Cosine-weighted directions around unit normals n (Malley's method)."""
+    r = np.sqrt(u1)
+    phi = 2 * math.pi * u2
+    lx, ly, lz = r * np.cos(phi), r * np.sin(phi), np.sqrt(np.maximum(0.0, 1 - u1))
+    b1, b2 = onb(n)
+    d = lx[:, None] * b1 + ly[:, None] * b2 + lz[:, None] * n
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def _surface_frame(scene: Scene):
+    V = scene.verts.astype(np.float64)
+    F = scene.tris
+    e1 = V[F[:, 1]] - V[F[:, 0]]
+    e2 = V[F[:, 2]] - V[F[:, 0]]
+    cr = np.cross(e1, e2)
+    area2 = np.linalg.norm(cr, axis=1)
+    nrm = cr / np.maximum(area2, 1e-300)[:, None]
+    cdf = np.cumsum(area2)
+    cdf /= cdf[-1]
+    return V, F, nrm, cdf
+
+
+def gi_rays(scene: Scene, n: int, seed: int, t_max: float, bias_frac: float = 1e-3,
+            width: int | None = None, height: int | None = None) -> np.ndarray:
+    """n GI rays from camera-facing, in-frustum surface points, tile-ordered."""
+    cam = scene.camera
+    W = width or cam.width
+    H = height or cam.height
+    V, F, nrm, cdf = _surface_frame(scene)
+    aspect = W / H
+    got_p, got_n, got_px, got_py = [], [], [], []
+    have = 0
+    offset = 0
+    while have < n:
+        m = max(4 * (n - have), 1024)
+        u = rng.uniform(seed, _S_GI_POS, 3 * m, offset).reshape(m, 3)
+        offset += 3 * m
+        tri = np.minimum(np.searchsorted(cdf, u[:, 0], side="right"), F.shape[0] - 1)
+        s1 = np.sqrt(u[:, 1])
+        b0, b1, b2 = 1 - s1, s1 * (1 - u[:, 2]), s1 * u[:, 2]
+        p = b0[:, None] * V[F[tri, 0]] + b1[:, None] * V[F[tri, 1]] + b2[:, None] * V[F[tri, 2]]
+        nn = nrm[tri]
+        q = p - cam.eye
+        z = q @ cam.forward
+        zs = np.maximum(z, 1e-9)
+        x = (q @ cam.right) / (zs * cam.tan_half_fov * aspect)
+        y = (q @ cam.up) / (zs * cam.tan_half_fov)
+        keep = (np.einsum("ij,ij->i", nn, -q) > 0) & (z > 0.05) & (np.abs(x) < 1) & (np.abs(y) < 1)
+        idx = np.nonzero(keep)[0][: n - have]
+        got_p.append(p[idx])
+        got_n.append(nn[idx])
+        got_px.append(np.minimum(((x[idx] + 1) * 0.5 * W).astype(np.int64), W - 1))
+        got_py.append(np.minimum(((1 - y[idx]) * 0.5 * H).astype(np.int64), H - 1))
+        have += idx.size
+    p = np.concatenate(got_p)
+    nn = np.concatenate(got_n)
+    order = _tile_order(np.concatenate(got_px), np.concatenate(got_py), W)
+    p, nn = p[order], nn[order]
+    u = rng.uniform(seed, _S_GI_DIR, 2 * n).reshape(n, 2)
+    d = cosine_hemisphere(nn, u[:, 0], u[:, 1])
+    o = p + (bias_frac * scene.diagonal) * nn
+    return _renorm(pack(o, d, 0.0, t_max))
+
+
+def free_space_rays(scene: Scene, n: int, seed: int, margin: float, t_max: float | None = None) -> np.ndarray:
+    """Origins uniform in the room, at least `margin` outside every object's bounding
+    sphere and away from the walls; directions uniform on the sphere."""
+    room = np.array(scene.room, dtype=np.float64)
+    cs = np.array([o.center for o in scene.objects]).reshape(-1, 3)
+    rs = np.array([o.radius for o in scene.objects]).reshape(-1)
+    out = []
+    have = 0
+    offset = 0
+    while have < n:
+        m = max(2 * (n - have), 1024)
+        u = rng.uniform(seed, _S_FREE, 3 * m, offset).reshape(m, 3)
+        offset += 3 * m
+        o = margin + u * (room - 2 * margin)
+        ok = np.ones(m, dtype=bool)
+        for c0 in range(0, cs.shape[0], 256):
+            dd = np.linalg.norm(o[:, None, :] - cs[None, c0:c0 + 256, :], axis=2)
+            ok &= np.all(dd > rs[None, c0:c0 + 256] + margin, axis=1)
+        o = o[ok][: n - have]
+        out.append(o)
+        have += o.shape[0]
+    o = np.concatenate(out)
+    u = rng.uniform(seed, _S_FREE + 100, 2 * n).reshape(n, 2)
+    z = 1 - 2 * u[:, 0]
+    r = np.sqrt(np.maximum(0.0, 1 - z * z))
+    phi = 2 * math.pi * u[:, 1]
+    d = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+    tm = scene.diagonal if t_max is None else t_max
+    return _renorm(pack(o, d, 0.0, tm))
