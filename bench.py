@@ -1,0 +1,358 @@
+"""Benchmark of the combined ray query on the 1080p GI workload.
+
+Workload (the paper's GI rays, Section 3 "GI & Shadow Rays"): the seeded
+frame scene (20x6x20 m room, 400 subdivision-4 icospheres + 200 boxes =
+2,050,412 triangles), a 256^3 float32 distance field baked on the device,
+and 1920x1080 = 2,073,600 cosine-hemisphere GI rays with t_max = 30 m.  One
+step = one rt_trace_combined call over all rays at the middle split setting
+(m = 2 voxels); the pure techniques (m = inf: triangles only, m = 0: field
+only) are timed the same way for the comparison the metric asks for.
+
+Prints one JSON line.  `--impl reference` times the CPU checker instead (the
+only place besides the CPU-baseline leg where this script runs it).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import rays as R  # noqa: E402
+from synth import scene as S  # noqa: E402
+
+METRIC = "combined-query rays/s vs BVH-only & SDF-only at 1080p GI; hit-t err vs FP64"
+UNIT = "rays/s"
+M_MIDDLE = 2.0
+WORKLOAD = "frame-1080p-gi"
+TRACE_SOURCES = ["paper_2305_07253_gb300/csrc/rt_trace.cu", "paper_2305_07253_gb300/csrc/rt_trace_dev.cuh",
+                 "paper_2305_07253_gb300/csrc/rt_internal.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 18)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload():
+    s = S.make_scene("frame")
+    rays = R.gi_rays(s, 1920 * 1080, 7, 30.0)
+    return s, rays
+
+
+def config_dict(s, n_rays, extra=None):
+    c = {"workload": WORKLOAD, "scene": "frame", "n_tris": int(s.n_tris), "grid": [s.spec.grid_n] * 3,
+         "grid_dtype": "f32", "rays": int(n_rays), "ray_kind": "cosine-hemisphere GI", "t_max_m": 30.0,
+         "split": {"mode": "one split", "m": M_MIDDLE, "closest_hit": True},
+         "l2": "inputs larger than L2 (working set > 500 MB: nodes, triangles, grid, rays, hits)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def trace_hash():
+    h = hashlib.sha256()
+    for f in TRACE_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.rows = []
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max([num(r[2]) for r in rows if num(r[2]) is not None] or [0.0])}
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2305_07253_gb300 as rq
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    s, rays = make_workload()
+    n_rays = rays.shape[0]
+    n = s.spec.grid_n
+    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
+    grid = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    sdf = rq.rt_sdf_create(grid, s.lo, s.hi)
+    rq.rt_sdf_bake(scene, sdf, rq.BAKE_BVH)
+    rays_d = torch.from_numpy(rays).to(dev)
+    hits = torch.empty((n_rays, 6), dtype=torch.int32, device=dev)
+    p_mid = rq.split_params(mode=rq.MODE_SPLIT1, m_near=M_MIDDLE)
+    p_bvh = rq.split_params(mode=rq.MODE_SPLIT1, m_near=math.inf)
+    p_sdf = rq.split_params(mode=rq.MODE_SPLIT1, m_near=0.0)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def time_steps(p, K, W):
+        for _ in range(W):
+            rq.rt_trace_combined(scene, sdf, rays_d, p, hits)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            rq.rt_trace_combined(scene, sdf, rays_d, p, hits)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / K
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    K, W = args.steps, max(3, args.warmup)
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (str(uuid) if uuid else None)
+
+    # algorithmic bytes per launch, from the counted variant (untimed)
+    counts = {}
+    for name, p in (("combined", p_mid), ("bvh", p_bvh), ("sdf", p_sdf)):
+        _, c = rq.rt_trace_combined_counted(scene, sdf, rays_d, p)
+        counts[name] = [int(x) for x in c.cpu().tolist()]
+
+    def algo_bytes(c):
+        nodes, tris, steps, _ = c
+        return 32 * n_rays + 24 * n_rays + 64 * nodes + 48 * tris + 8 * 4 * steps
+
+    sampler = ClockSampler(uuid)
+    ms_mid = time_steps(p_mid, K, W)
+    clocks = sampler.stop()
+    ms_bvh = time_steps(p_bvh, K, W)
+    ms_sdf = time_steps(p_sdf, K, W)
+    rq.rt_trace_combined(scene, sdf, rays_d, p_mid, hits)
+    torch.cuda.synchronize()
+    hits_mid = hits.cpu().numpy()
+
+    # end to end through host buffers: pinned rays in, pinned hit records out
+    rays_h = torch.from_numpy(rays).pin_memory()
+    hits_h = torch.empty((n_rays, 6), dtype=torch.int32).pin_memory()
+    Ke = max(3, min(K, 50))
+    for _ in range(W):
+        rq.trace_combined_from_host(scene, sdf, rays_h, p_mid, hits_h, rays_d, hits)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        rq.trace_combined_from_host(scene, sdf, rays_h, p_mid, hits_h, rays_d, hits)
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / Ke
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    value = world * n_rays / (ms_mid * 1e-3)
+    peak, peak_kind = peaks()
+    ab = algo_bytes(counts["combined"])
+    achieved = ab / (ms_mid * 1e-3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        d = json.load(open(tf))
+        if d.get("trace_hash") == trace_hash() and d.get("workload") == WORKLOAD:
+            traffic = d.get("combined_bytes_per_launch")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_mid, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded procedural scene and rays)",
+        "config": config_dict(s, n_rays, {"parallelism": f"rays replicated per GPU x{world}" if world > 1 else "1 GPU"}),
+        "bvh_only": {"value": world * n_rays / (ms_bvh * 1e-3), "ms_per_step": ms_bvh},
+        "sdf_only": {"value": world * n_rays / (ms_sdf * 1e-3), "ms_per_step": ms_sdf},
+        "combined": {"value": value, "ms_per_step": ms_mid, "m": M_MIDDLE},
+        "ordering_ok": bool(ms_bvh > ms_mid >= ms_sdf),
+        "work_counts": {k: {"nodes": v[0], "tris": v[1], "steps": v[2], "field_queries": v[3]}
+                        for k, v in counts.items()},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "k_trace<false> (combined, m=2)",
+                     "algorithmic_bytes_per_launch": ab, "peak_kind": f"of {peak_kind}"},
+        "e2e": {"value": world * n_rays / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(rays.nbytes),
+                "d2h_bytes_per_step": int(n_rays * 24), "ms_per_step": ms_e2e},
+        "gpu_launches": K,
+        "clocks": clocks,
+        "trace_hash": trace_hash(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"], line["hit_t_err_vs_fp64"] = cpu_baseline(s, rays, hits_mid, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _oracle_world(s, sample_rays):
+    import oracle as O
+    n = s.spec.grid_n
+    bvh = O.BVH(s.verts, s.tris)
+    grid = O.Grid(s.lo, s.hi, [n, n, n], src=bvh)
+    prm = O.make_params(mode=1, m_near=M_MIDDLE)
+    # first pass evaluates the grid values the sample touches (the device grid
+    # is baked before its timed region, so the timed CPU pass is the warm one)
+    O.trace_combined(bvh, grid, sample_rays, prm, precision=64)
+    return O, bvh, grid, prm
+
+
+def cpu_baseline(s, rays, gpu_hits, sample):
+    idx = np.linspace(0, rays.shape[0] - 1, min(sample, rays.shape[0])).astype(np.int64)
+    sr = rays[idx]
+    O, bvh, grid, prm = _oracle_world(s, sr)
+    cores = O.default_threads()
+    t0 = time.perf_counter()
+    o = O.trace_combined(bvh, grid, sr, prm, precision=64, nthreads=cores)
+    dt = time.perf_counter() - t0
+    g = gpu_hits[idx]
+    gt = g[:, 0].view(np.float32).astype(np.float64)
+    gtr = g[:, 4]
+    err = {}
+    for name, tr in (("bvh_resolved", 1), ("sdf_resolved", 2)):
+        m = (gtr == tr) & (o["tracer"] == tr)
+        e = np.abs(gt[m] - o["t"][m]) / np.maximum(1.0, np.abs(o["t"][m]))
+        err[name] = {"n": int(m.sum()), "mean_rel": float(e.mean()) if e.size else 0.0,
+                     "p99_rel": float(np.quantile(e, 0.99)) if e.size else 0.0,
+                     "max_rel": float(e.max()) if e.size else 0.0}
+    err["tracer_agreement"] = float(np.mean(gtr == o["tracer"]))
+    err["sample"] = f"{len(idx)} rays evenly spaced over the batch, fp64 checker, m={M_MIDDLE}"
+    cb = {"value": len(idx) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": f"{len(idx)} of {rays.shape[0]} GI rays (evenly spaced), fp64 combined query m={M_MIDDLE}, "
+                    f"grid values evaluated before timing", "seconds": dt}
+    return cb, err
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    s, rays = make_workload()
+    per_step = 4096
+    idx0 = np.random.default_rng(5).permutation(rays.shape[0])
+    n_total = per_step * (args.warmup + args.steps)
+    sel = idx0[: min(n_total, rays.shape[0])]
+    O, bvh, grid, prm = _oracle_world(s, rays[sel])
+    cores = O.default_threads()
+    for k in range(args.warmup):
+        O.trace_combined(bvh, grid, rays[sel[(k * per_step) % len(sel):][:per_step]], prm, precision=64)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        off = ((args.warmup + k) * per_step) % len(sel)
+        batch = rays[sel[off:off + per_step]]
+        O.trace_combined(bvh, grid, batch, prm, precision=64, nthreads=cores)
+        done += batch.shape[0]
+    dt = time.perf_counter() - t0
+    v = done / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded procedural scene and rays)",
+            "config": config_dict(s, rays.shape[0]),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} GI rays per step, fp64 combined query m={M_MIDDLE}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

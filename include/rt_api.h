@@ -1,0 +1,216 @@
+/*
+ * rt_api.h -- C interface of the GB300 (sm_103a) combined ray query library.
+ *
+ * The library answers ray queries (o, d, t_min, t_max, f) -- Eq. 1 of Bartels
+ * & Harada, "Combining GPU Tracing Methods within a Single Ray Query"
+ * (SIGGRAPH Asia 2022 Technical Communications) -- by splitting [t_min, t_max]
+ * into mutually exclusive sub-intervals (Eq. 2) and tracing each one either
+ * exactly against the triangles (BVH traversal with a watertight test) or
+ * approximately through a dense signed distance field (sphere tracing).
+ *
+ * General rules for every entry point
+ *   - All ray, hit and grid buffers are DEVICE memory owned by the caller,
+ *     16-byte aligned.  Handles (rt_scene, rt_sdf) are owned by the library and
+ *     released with the matching *_destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; argument errors are
+ *     detected before anything is enqueued and returned synchronously.
+ *   - Every call returns an rt_status.  On failure rt_last_error() gives a
+ *     human-readable message (thread-local; valid until the next call on the
+ *     same thread).
+ *   - Device-side limits (traversal stack depth, march step budget) never
+ *     abort a kernel: they set bits in rt_hit.flags.
+ *   - The library uses the current CUDA device of the calling thread; a handle
+ *     must be used on the device it was created on.
+ */
+#ifndef GB300_RT_API_H
+#define GB300_RT_API_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RT_OK = 0,
+    RT_ERR_INVALID_ARG = 1,    /* null pointer, negative size, misaligned buffer, bad mode */
+    RT_ERR_CUDA = 2,           /* a CUDA runtime call failed (message has the CUDA error) */
+    RT_ERR_OOM = 3,            /* device allocation failed */
+    RT_ERR_DEVICE_LIMIT = 4,   /* a problem exceeds a device-side limit (e.g. tree depth) */
+    RT_ERR_NOT_IMPLEMENTED = 5
+} rt_status;
+
+/* One query of Eq. 1: origin o, t_min, unit direction d, t_max.  32 bytes,
+ * loaded as two 16-byte vectors.  The caller normalises d. */
+typedef struct {
+    float ox, oy, oz, tmin;
+    float dx, dy, dz, tmax;
+} rt_ray;
+
+/* Result of one query.  24 bytes.
+ *   t       hit distance along the ray (+inf on a miss)
+ *   prim    triangle index in the mesh given to rt_scene_build; -1 for a miss
+ *           or for a hit resolved by the distance field (the paper notes that
+ *           surface information is not directly available from a distance
+ *           field, Section 2 "Surface information")
+ *   u, v    barycentric weights of the triangle's second and third vertex
+ *           (hit = (1-u-v) v0 + u v1 + v v2); 0 for field hits
+ *   tracer  RT_TRACER_* : which technique resolved the query
+ *   flags   RT_FLAG_* */
+typedef struct {
+    float t;
+    int32_t prim;
+    float u, v;
+    int32_t tracer;
+    uint32_t flags;
+} rt_hit;
+
+enum { RT_TRACER_MISS = 0, RT_TRACER_BVH = 1, RT_TRACER_SDF = 2 };
+enum {
+    RT_FLAG_STACK_OVERFLOW = 1u, /* BVH traversal stack exhausted (result may miss a hit) */
+    RT_FLAG_STEP_LIMIT = 2u,     /* distance-field march used all max_steps without hit or exit */
+    RT_FLAG_ITER_LIMIT = 4u      /* traversal stopped by its iteration guard (corrupt structure) */
+};
+
+/* How [t_min, t_max] is split (Eq. 2) and processed (Section 2, after Eq. 2;
+ * the split rules of Section 3).  h = largest edge of one grid voxel.
+ *   mode 0  RT_MODE_BVH    : triangles on [t_min, t_max] (the pure technique)
+ *   mode 1  RT_MODE_SPLIT1 : t_1 = clamp(t_min + m_near*h, t_min, t_max);
+ *                            triangles on [t_min, t_1] (skipped if m_near == 0),
+ *                            field on [t_1, t_max] (skipped if t_1 == t_max and
+ *                            m_near > 0).  Section 3, occlusion queries and the
+ *                            first GI pass.
+ *   mode 2  RT_MODE_SPLIT2 : additionally t_2 = clamp(t_max - m_far*h, t_1, t_max);
+ *                            triangles on [t_min, t_1] and [t_2, t_max] (each
+ *                            skipped when its multiplier is 0), field on [t_1, t_2]
+ *                            (skipped when empty, unless both multipliers are 0).
+ *                            Section 3, shadow rays.
+ *   mode 3  RT_MODE_SDF    : field on [t_min, t_max] (the pure technique)
+ * any_hit = 0 (closest hit): sub-intervals in order, stop at the first that
+ * hits.  any_hit = 1: field sub-interval first, then the triangle ones.
+ * Triangle sub-intervals are closed: a hit exactly at t_1 belongs to them.
+ * Multipliers may be +INFINITY; they must not be negative or NaN.
+ * The field march (Section 1 names distance-field tracing; the step rule is
+ * this library's): clip the sub-interval to the grid box, t = start; up to
+ * max_steps times: phi = trilinear(o + t d); phi < hit_eps_vox*hmin -> hit at
+ * t; t += max(phi, min_step_vox*hmin); t > end -> miss.  hmin = smallest voxel
+ * edge.  refine_root = 1 replaces the hit t by the root of
+ * phi = hit_eps_vox*hmin inside the last step (bisection, 24 halvings), the
+ * point at which rt_trace_combined_backward differentiates. */
+typedef struct {
+    int32_t mode;
+    int32_t any_hit;
+    float m_near;
+    float m_far;
+    int32_t max_steps;
+    float hit_eps_vox;
+    float min_step_vox;
+    int32_t refine_root;
+} rt_split_params;
+
+enum { RT_MODE_BVH = 0, RT_MODE_SPLIT1 = 1, RT_MODE_SPLIT2 = 2, RT_MODE_SDF = 3 };
+enum { RT_GRID_F32 = 0, RT_GRID_F16 = 1 };
+enum { RT_BAKE_AUTO = 0, RT_BAKE_BRUTE = 1, RT_BAKE_BVH = 2 };
+
+typedef struct rt_scene rt_scene;
+typedef struct rt_sdf rt_sdf;
+
+typedef struct {
+    int64_t n_tris;
+    int64_t n_verts;
+    int64_t n_nodes;     /* internal BVH nodes (64 bytes each) */
+    int32_t max_depth;   /* deepest leaf; traversal stack holds RT_STACK_DEPTH entries */
+    int32_t stack_depth;
+    float lo[3], hi[3];  /* bounds of all triangles */
+    int64_t device_bytes;
+} rt_scene_info;
+
+/* Build the triangle acceleration structure (a linear BVH from 63-bit Morton
+ * codes of triangle centroids, hierarchy by Karras' split search, HPG 2012)
+ * and the angle-weighted pseudonormals used by rt_sdf_bake.  The triangle
+ * tracer stands in for the paper's hardware ray tracing (Section 3).
+ *   d_verts  n_verts x 3 float32 (x,y,z), device
+ *   d_tris   n_tris x 3 int32 vertex indices, device; winding gives the
+ *            outward normal (counter-clockwise seen from outside)
+ *   out      receives a new handle; inputs are copied and may be freed after
+ *            the call returns (the call synchronises `stream`)
+ * Errors: RT_ERR_INVALID_ARG (null pointers, n_tris < 1, n_verts < 3, more
+ * than 2^31-1 triangles), RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_DEVICE_LIMIT (tree
+ * deeper than the traversal stack). */
+rt_status rt_scene_build(const float* d_verts, int64_t n_verts, const int32_t* d_tris, int64_t n_tris,
+                         void* stream, rt_scene** out);
+rt_status rt_scene_info_get(const rt_scene* scene, rt_scene_info* info);
+rt_status rt_scene_destroy(rt_scene* scene);
+
+/* Describe a dense distance-field grid held in caller memory (not copied;
+ * the memory must outlive the handle).  Samples sit at lo + (i,j,k)*h with
+ * h = (hi - lo) / (n - 1) per axis, x fastest: value (i,j,k) is at element
+ * i + n0*(j + n1*k).  dtype RT_GRID_F32 or RT_GRID_F16 (converted exactly to
+ * float for the arithmetic).  n >= 2 per axis, hi > lo.  The paper's field is
+ * a set of camera-centred cascades (Section 3, "Distance Field Generation");
+ * this library uses one dense grid. */
+rt_status rt_sdf_create(const void* d_grid, int32_t dtype, const float lo[3], const float hi[3],
+                        const int32_t n[3], rt_sdf** out);
+rt_status rt_sdf_destroy(rt_sdf* sdf);
+
+/* Fill the grid of `sdf` with the signed distance to the nearest triangle of
+ * `scene`: exact closest point on each triangle, sign from the angle-weighted
+ * pseudonormal of the closest face, edge or vertex (positive on the side the
+ * normals point to).  This replaces the paper's voxelisation + jump flooding +
+ * fast sweeping build (Section 3, "Distance Field Generation") by its exact
+ * definition.  method: RT_BAKE_BRUTE tests every triangle for every sample
+ * (triangles staged through shared memory); RT_BAKE_BVH prunes with the BVH
+ * (same result); RT_BAKE_AUTO picks by problem size.  Writes through the
+ * grid pointer given to rt_sdf_create. */
+rt_status rt_sdf_bake(const rt_scene* scene, rt_sdf* sdf, int32_t method, void* stream);
+
+/* The pure triangle technique: closest hit (any_hit = 0) or any hit
+ * (any_hit = 1) on [t_min, t_max] for n rays.  d_rays: n rt_ray; d_hits: n
+ * rt_hit (written).  n may be 0. */
+rt_status rt_trace_bvh(const rt_scene* scene, const rt_ray* d_rays, int64_t n, int32_t any_hit,
+                       rt_hit* d_hits, void* stream);
+
+/* The pure distance-field technique on [t_min, t_max] (params->mode is
+ * ignored and taken as RT_MODE_SDF; the other fields apply). */
+rt_status rt_trace_sdf(const rt_sdf* sdf, const rt_ray* d_rays, int64_t n, const rt_split_params* params,
+                       rt_hit* d_hits, void* stream);
+
+/* The combined query (Eq. 2 and the rules of rt_split_params) for n rays.
+ * `params` is read on the host during the call. */
+rt_status rt_trace_combined(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
+                            const rt_split_params* params, rt_hit* d_hits, void* stream);
+
+/* Same as rt_trace_combined, and also adds per-query work counts into
+ * d_counters (device, 4 x uint64, caller zeroes): [0] BVH nodes visited,
+ * [1] triangles tested, [2] field march steps, [3] queries that ran a field
+ * sub-interval.  Slower; used to count algorithmic bytes. */
+rt_status rt_trace_combined_counted(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays,
+                                    int64_t n, const rt_split_params* params, rt_hit* d_hits,
+                                    unsigned long long* d_counters, void* stream);
+
+/* Adjoint of the field-resolved hit distance.  For each query whose hit
+ * record (from a forward call with the same params, refine_root = 1) has
+ * tracer == RT_TRACER_SDF, the root p* = o + t d of phi = eps satisfies
+ * phi_theta(p*) = eps; implicit differentiation gives
+ *   dt/dtheta_k = -w_k(p*) / (grad phi(p*) . d)
+ * with w_k the 8 trilinear weights.  Adds d_grad_t[i] * dt/dtheta_k into
+ * d_grad_grid[k] (float32, same layout as the grid; the caller zeroes it).
+ * Queries with grad phi . d > -1e-6 (tangent), a field hit at the start of
+ * the sub-interval, or another tracer contribute nothing.  The forward pass
+ * is not stored: the kernel re-marches each ray.  The grid must be
+ * RT_GRID_F32. */
+rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays,
+                                     int64_t n, const rt_split_params* params, const rt_hit* d_hits,
+                                     const float* d_grad_t, float* d_grad_grid, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* rt_last_error(void);
+
+/* Library version string. */
+const char* rt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,274 @@
+// C entry points: argument checks, handle bookkeeping and launch set-up.
+// Every step of the query itself runs in the kernels of rt_trace.cu,
+// rt_scene.cu, rt_bake.cu and rt_backward.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "rt_internal.cuh"
+
+static thread_local char g_err[512] = "";
+
+rt_status rt_fail(rt_status s, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+rt_status rt_cuda_fail(cudaError_t e, const char* what)
+{
+    cudaGetLastError();  // clear a non-sticky error so the next call starts clean
+    return rt_fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "%s: %s (%s)", what,
+                   cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+extern "C" const char* rt_last_error(void) { return g_err; }
+extern "C" const char* rt_version(void) { return "gb300-rayquery 0.1 (sm_103a)"; }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static rt_status check_params(const rt_split_params* p)
+{
+    if (!p) return rt_fail(RT_ERR_INVALID_ARG, "params is null");
+    if (p->mode < 0 || p->mode > 3) return rt_fail(RT_ERR_INVALID_ARG, "mode %d not in 0..3", p->mode);
+    if (!(p->m_near >= 0.f) || !(p->m_far >= 0.f))
+        return rt_fail(RT_ERR_INVALID_ARG, "multipliers must be >= 0 (got %g, %g)", p->m_near, p->m_far);
+    if (p->max_steps < 1) return rt_fail(RT_ERR_INVALID_ARG, "max_steps must be >= 1");
+    if (!(p->hit_eps_vox >= 0.f) || !(p->min_step_vox > 0.f) || isinf(p->hit_eps_vox) || isinf(p->min_step_vox))
+        return rt_fail(RT_ERR_INVALID_ARG, "hit_eps_vox must be >= 0 and min_step_vox > 0, both finite");
+    if (p->any_hit != 0 && p->any_hit != 1) return rt_fail(RT_ERR_INVALID_ARG, "any_hit must be 0 or 1");
+    return RT_OK;
+}
+
+static rt_status check_io(const rt_ray* rays, int64_t n, const rt_hit* hits)
+{
+    if (n < 0) return rt_fail(RT_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+    if (n == 0) return RT_OK;
+    if (!rays || !hits) return rt_fail(RT_ERR_INVALID_ARG, "null ray or hit buffer");
+    if (!aligned16(rays)) return rt_fail(RT_ERR_INVALID_ARG, "ray buffer not 16-byte aligned");
+    if (((uintptr_t)hits & 7u) != 0) return rt_fail(RT_ERR_INVALID_ARG, "hit buffer not 8-byte aligned");
+    return RT_OK;
+}
+
+// Host-side set-up of the split (the same float operations the queries use).
+void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, const rt_split_params* p)
+{
+    memset(&a, 0, sizeof(a));
+    if (sc) {
+        a.nodes = sc->nodes;
+        a.tris = sc->tris;
+        a.root = sc->n_tris == 0 ? INT32_MIN : (sc->n_tris == 1 ? ~0 : 0);
+    } else {
+        a.root = INT32_MIN;
+    }
+    if (sdf) {
+        a.grid = sdf->grid;
+        a.grid_f16 = sdf->dtype == RT_GRID_F16;
+        for (int k = 0; k < 3; ++k) {
+            a.glo[k] = sdf->lo[k];
+            a.ghi[k] = sdf->hi[k];
+            a.gih[k] = sdf->ih[k];
+            a.gn[k] = sdf->n[k];
+        }
+        float hmin = fminf(fminf(sdf->h[0], sdf->h[1]), sdf->h[2]);
+        a.hsplit = fmaxf(fmaxf(sdf->h[0], sdf->h[1]), sdf->h[2]);
+        a.eps_hit = p->hit_eps_vox * hmin;
+        a.eps_min = p->min_step_vox * hmin;
+    }
+    a.max_steps = p->max_steps;
+    a.mode = p->mode;
+    a.any_hit = p->any_hit;
+    a.refine_root = p->refine_root;
+    a.m_near = p->m_near;
+    a.m_far = p->m_far;
+}
+
+static rt_status device_matches(int dev)
+{
+    int cur = -1;
+    RT_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != dev) return rt_fail(RT_ERR_INVALID_ARG, "handle belongs to device %d, current device is %d", dev, cur);
+    return RT_OK;
+}
+
+extern "C" rt_status rt_scene_build(const float* d_verts, int64_t n_verts, const int32_t* d_tris, int64_t n_tris,
+                                    void* stream, rt_scene** out)
+{
+    if (!out) return rt_fail(RT_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (!d_verts || !d_tris) return rt_fail(RT_ERR_INVALID_ARG, "null vertex or triangle buffer");
+    if (n_tris < 1 || n_verts < 3) return rt_fail(RT_ERR_INVALID_ARG, "need n_tris >= 1 and n_verts >= 3");
+    if (n_tris > (int64_t)INT32_MAX / 2 || n_verts > (int64_t)INT32_MAX)
+        return rt_fail(RT_ERR_INVALID_ARG, "mesh too large (n_tris %lld)", (long long)n_tris);
+    if (((uintptr_t)d_verts & 3u) || ((uintptr_t)d_tris & 3u))
+        return rt_fail(RT_ERR_INVALID_ARG, "vertex/triangle buffers must be 4-byte aligned");
+    rt_scene* sc = new (std::nothrow) rt_scene();
+    if (!sc) return rt_fail(RT_ERR_OOM, "host allocation failed");
+    memset(sc, 0, sizeof(*sc));
+    cudaGetDevice(&sc->device);
+    rt_status st = rt_build_scene(d_verts, n_verts, d_tris, n_tris, (cudaStream_t)stream, sc);
+    if (st != RT_OK) {
+        rt_scene_destroy(sc);
+        return st;
+    }
+    *out = sc;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_scene_info_get(const rt_scene* sc, rt_scene_info* info)
+{
+    if (!sc || !info) return rt_fail(RT_ERR_INVALID_ARG, "null argument");
+    info->n_tris = sc->n_tris;
+    info->n_verts = sc->n_verts;
+    info->n_nodes = sc->n_nodes;
+    info->max_depth = sc->max_depth;
+    info->stack_depth = RT_STACK_DEPTH;
+    for (int k = 0; k < 3; ++k) {
+        info->lo[k] = sc->lo[k];
+        info->hi[k] = sc->hi[k];
+    }
+    info->device_bytes = sc->bytes;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_scene_destroy(rt_scene* sc)
+{
+    if (!sc) return RT_OK;
+    cudaFree(sc->nodes);
+    cudaFree(sc->tris);
+    cudaFree(sc->pn);
+    delete sc;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_sdf_create(const void* d_grid, int32_t dtype, const float lo[3], const float hi[3],
+                                   const int32_t n[3], rt_sdf** out)
+{
+    if (!out) return rt_fail(RT_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (!d_grid || !lo || !hi || !n) return rt_fail(RT_ERR_INVALID_ARG, "null argument");
+    if (dtype != RT_GRID_F32 && dtype != RT_GRID_F16) return rt_fail(RT_ERR_INVALID_ARG, "dtype %d", dtype);
+    if (!aligned16(d_grid)) return rt_fail(RT_ERR_INVALID_ARG, "grid not 16-byte aligned");
+    int64_t cnt = 1;
+    for (int k = 0; k < 3; ++k) {
+        if (n[k] < 2) return rt_fail(RT_ERR_INVALID_ARG, "n[%d] = %d < 2", k, n[k]);
+        if (!(hi[k] > lo[k]) || isinf(lo[k]) || isinf(hi[k]))
+            return rt_fail(RT_ERR_INVALID_ARG, "need finite hi > lo on axis %d", k);
+        cnt *= n[k];
+    }
+    if (cnt > ((int64_t)1 << 40)) return rt_fail(RT_ERR_INVALID_ARG, "grid too large");
+    rt_sdf* g = new (std::nothrow) rt_sdf();
+    if (!g) return rt_fail(RT_ERR_OOM, "host allocation failed");
+    g->grid = d_grid;
+    g->dtype = dtype;
+    for (int k = 0; k < 3; ++k) {
+        g->lo[k] = lo[k];
+        g->hi[k] = hi[k];
+        g->n[k] = n[k];
+        // spacing and its reciprocal, rounded once each in float
+        volatile float ext = hi[k] - lo[k];
+        g->h[k] = ext / (float)(n[k] - 1);
+        g->ih[k] = 1.0f / g->h[k];
+    }
+    *out = g;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_sdf_destroy(rt_sdf* sdf)
+{
+    delete sdf;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_sdf_bake(const rt_scene* sc, rt_sdf* sdf, int32_t method, void* stream)
+{
+    if (!sc || !sdf) return rt_fail(RT_ERR_INVALID_ARG, "null scene or grid");
+    if (method < 0 || method > 2) return rt_fail(RT_ERR_INVALID_ARG, "bake method %d", method);
+    rt_status st = device_matches(sc->device);
+    if (st != RT_OK) return st;
+    return rt_launch_bake(sc, sdf, method, (cudaStream_t)stream);
+}
+
+static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
+                              const rt_split_params* p, rt_hit* hits, unsigned long long* counters,
+                              void* stream)
+{
+    rt_status st = check_params(p);
+    if (st != RT_OK) return st;
+    st = check_io(rays, n, hits);
+    if (st != RT_OK) return st;
+    if (p->mode != RT_MODE_SDF && !sc) return rt_fail(RT_ERR_INVALID_ARG, "mode %d needs a scene", p->mode);
+    if (p->mode != RT_MODE_BVH && !sdf) return rt_fail(RT_ERR_INVALID_ARG, "mode %d needs a grid", p->mode);
+    if (sc) {
+        st = device_matches(sc->device);
+        if (st != RT_OK) return st;
+    }
+    if (counters && ((uintptr_t)counters & 7u)) return rt_fail(RT_ERR_INVALID_ARG, "counters misaligned");
+    if (n == 0) return RT_OK;
+    TraceArgs a;
+    rt_fill_trace_args(a, p->mode == RT_MODE_SDF ? nullptr : sc, p->mode == RT_MODE_BVH ? nullptr : sdf, p);
+    a.rays = reinterpret_cast<const float4*>(rays);
+    a.hits = hits;
+    a.n = n;
+    a.counters = counters;
+    return rt_launch_trace(a, counters != nullptr, (cudaStream_t)stream);
+}
+
+extern "C" rt_status rt_trace_bvh(const rt_scene* sc, const rt_ray* rays, int64_t n, int32_t any_hit, rt_hit* hits,
+                                  void* stream)
+{
+    if (!sc) return rt_fail(RT_ERR_INVALID_ARG, "scene is null");
+    rt_split_params p = {RT_MODE_BVH, any_hit, 0.f, 0.f, 1, 0.f, 1.f, 0};
+    return trace_common(sc, nullptr, rays, n, &p, hits, nullptr, stream);
+}
+
+extern "C" rt_status rt_trace_sdf(const rt_sdf* sdf, const rt_ray* rays, int64_t n, const rt_split_params* params,
+                                  rt_hit* hits, void* stream)
+{
+    if (!sdf || !params) return rt_fail(RT_ERR_INVALID_ARG, "null grid or params");
+    rt_split_params p = *params;
+    p.mode = RT_MODE_SDF;
+    return trace_common(nullptr, sdf, rays, n, &p, hits, nullptr, stream);
+}
+
+extern "C" rt_status rt_trace_combined(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
+                                       const rt_split_params* params, rt_hit* hits, void* stream)
+{
+    return trace_common(sc, sdf, rays, n, params, hits, nullptr, stream);
+}
+
+extern "C" rt_status rt_trace_combined_counted(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
+                                               const rt_split_params* params, rt_hit* hits,
+                                               unsigned long long* counters, void* stream)
+{
+    if (!counters) return rt_fail(RT_ERR_INVALID_ARG, "counters is null");
+    return trace_common(sc, sdf, rays, n, params, hits, counters, stream);
+}
+
+extern "C" rt_status rt_trace_combined_backward(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
+                                                const rt_split_params* params, const rt_hit* hits,
+                                                const float* grad_t, float* grad_grid, void* stream)
+{
+    rt_status st = check_params(params);
+    if (st != RT_OK) return st;
+    st = check_io(rays, n, hits);
+    if (st != RT_OK) return st;
+    if (!sdf) return rt_fail(RT_ERR_INVALID_ARG, "grid is null");
+    if (sdf->dtype != RT_GRID_F32) return rt_fail(RT_ERR_INVALID_ARG, "backward needs a float32 grid");
+    if (n > 0 && (!grad_t || !grad_grid)) return rt_fail(RT_ERR_INVALID_ARG, "null gradient buffer");
+    if (params->mode != RT_MODE_SDF && params->mode != RT_MODE_BVH && !sc)
+        return rt_fail(RT_ERR_INVALID_ARG, "combined modes need the scene");
+    if (n == 0) return RT_OK;
+    TraceArgs a;
+    rt_fill_trace_args(a, params->mode == RT_MODE_SDF ? nullptr : sc, sdf, params);
+    a.rays = reinterpret_cast<const float4*>(rays);
+    a.hits = const_cast<rt_hit*>(hits);
+    a.n = n;
+    return rt_launch_backward(a, grad_t, grad_grid, (cudaStream_t)stream);
+}

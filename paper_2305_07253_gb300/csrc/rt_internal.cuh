@@ -1,0 +1,83 @@
+// Internal data layout and device helpers of the combined ray query library.
+//
+// HBM layout (all arrays 16-byte aligned, built once per scene):
+//   nodes  : n_tris-1 internal BVH nodes, 64 B each (four 16-byte vectors):
+//              a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//              b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//              c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//              d = (child0, child1, -, -)   child >= 0: internal node,
+//                                           child < 0 : leaf = triangle ~child
+//   tris   : 48 B per triangle in leaf (Morton) order: v0.xyz|prim, v1.xyz|-, v2.xyz|-
+//   pn     : 112 B per triangle in leaf order: face normal, 3 edge and 3 vertex
+//            pseudonormals (float4 each), read only by the distance bake
+//   grid   : caller memory, dense n0*n1*n2 float32 or float16, x fastest
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rt_api.h"
+
+#define RT_STACK_DEPTH 64
+
+struct __align__(16) BNode {
+    float4 a, b, c;
+    int4 d;
+};
+
+struct rt_scene {
+    int device;
+    int64_t n_tris, n_verts, n_nodes;
+    int32_t max_depth;
+    BNode* nodes;
+    float4* tris;   // 3 per triangle
+    float4* pn;     // 7 per triangle
+    float lo[3], hi[3];
+    int64_t bytes;
+};
+
+struct rt_sdf {
+    const void* grid;
+    int32_t dtype;
+    float lo[3], hi[3], h[3], ih[3];
+    int32_t n[3];
+};
+
+// Everything one trace kernel needs, passed by value.
+struct TraceArgs {
+    const BNode* nodes;
+    const float4* tris;
+    int32_t root;        // 0 (internal), ~0 (single leaf) or INT32_MIN (no triangles)
+    const void* grid;    // null: no field
+    int32_t grid_f16;
+    float glo[3], ghi[3], gih[3];
+    int32_t gn[3];
+    float hsplit, eps_hit, eps_min;
+    int32_t max_steps;
+    int32_t mode, any_hit, refine_root;
+    float m_near, m_far;
+    const float4* rays;
+    rt_hit* hits;
+    int64_t n;
+    unsigned long long* counters;
+};
+
+// ---------------------------------------------------------------------------
+// host-side error reporting (rt_api.cu)
+// ---------------------------------------------------------------------------
+rt_status rt_fail(rt_status s, const char* fmt, ...);
+rt_status rt_cuda_fail(cudaError_t e, const char* what);
+#define RT_CUDA_TRY(expr)                                         \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) return rt_cuda_fail(_e, #expr);    \
+    } while (0)
+
+// launchers implemented in the .cu files
+rt_status rt_launch_trace(const TraceArgs& a, bool counted, cudaStream_t s);
+rt_status rt_launch_backward(const TraceArgs& a, const float* grad_t, float* grad_grid, cudaStream_t s);
+rt_status rt_build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, cudaStream_t s,
+                         rt_scene* out);
+rt_status rt_launch_bake(const rt_scene* sc, const rt_sdf* sdf, int32_t method, cudaStream_t s);
+void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, const rt_split_params* p);

@@ -1,0 +1,99 @@
+"""The C interface: the library builds for sm_103a, loads without a GPU and
+exports every entry point the public header declares; host-side argument
+checks reject bad input before any device work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rt_api.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def rtlib():
+    from paper_2305_07253_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for n in ("rt_scene_build", "rt_sdf_bake", "rt_trace_combined", "rt_trace_bvh", "rt_trace_sdf",
+              "rt_trace_combined_backward"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(rtlib):
+    missing = [n for n in _declared() if not hasattr(rtlib, n)]
+    assert not missing, missing
+
+
+def test_binding_export_list_matches_header():
+    import paper_2305_07253_gb300 as rq
+    assert sorted(rq.EXPORTS) == _declared()
+
+
+def test_struct_sizes_match_header():
+    import paper_2305_07253_gb300 as rq
+    assert ctypes.sizeof(rq.rt_split_params) == 32
+    assert ctypes.sizeof(rq.rt_scene_info) == 8 * 3 + 4 * 2 + 4 * 6 + 8
+
+
+def test_argument_errors_without_a_gpu(rtlib):
+    """Argument checks run on the host and return RT_ERR_INVALID_ARG with a message."""
+    rtlib.rt_last_error.restype = ctypes.c_char_p
+    out = ctypes.c_void_p()
+    # null buffers
+    rtlib.rt_scene_build.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_void_p, ctypes.c_void_p]
+    assert rtlib.rt_scene_build(None, 3, None, 1, None, ctypes.byref(out)) == 1
+    assert b"null" in rtlib.rt_last_error()
+    # grid with n < 2
+    rtlib.rt_sdf_create.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+    lo = (ctypes.c_float * 3)(0, 0, 0)
+    hi = (ctypes.c_float * 3)(1, 1, 1)
+    n = (ctypes.c_int32 * 3)(1, 4, 4)
+    assert rtlib.rt_sdf_create(ctypes.c_void_p(256), 0, lo, hi, n, ctypes.byref(out)) == 1
+    assert b"n[0]" in rtlib.rt_last_error()
+    # misaligned grid pointer
+    n2 = (ctypes.c_int32 * 3)(4, 4, 4)
+    assert rtlib.rt_sdf_create(ctypes.c_void_p(258), 0, lo, hi, n2, ctypes.byref(out)) == 1
+    # a valid wrap does not touch the device
+    assert rtlib.rt_sdf_create(ctypes.c_void_p(256), 0, lo, hi, n2, ctypes.byref(out)) == 0
+    rtlib.rt_sdf_destroy.argtypes = [ctypes.c_void_p]
+    rtlib.rt_sdf_destroy(out)
+
+
+def test_bad_split_params_rejected(rtlib):
+    import paper_2305_07253_gb300 as rq
+    out = ctypes.c_void_p()
+    lo = (ctypes.c_float * 3)(0, 0, 0)
+    hi = (ctypes.c_float * 3)(1, 1, 1)
+    n = (ctypes.c_int32 * 3)(4, 4, 4)
+    rtlib.rt_sdf_create.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+    assert rtlib.rt_sdf_create(ctypes.c_void_p(256), 0, lo, hi, n, ctypes.byref(out)) == 0
+    rtlib.rt_trace_sdf.argtypes = [ctypes.c_void_p] * 6 + []
+    rtlib.rt_trace_sdf.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p]
+    rtlib.rt_last_error.restype = ctypes.c_char_p
+    for bad in (rq.split_params(max_steps=0), rq.split_params(m_near=-1.0), rq.split_params(min_step_vox=0.0),
+                rq.split_params(hit_eps_vox=float("nan"))):
+        assert rtlib.rt_trace_sdf(out, ctypes.c_void_p(512), 4, ctypes.byref(bad), ctypes.c_void_p(1024), None) == 1
+    # misaligned ray buffer
+    good = rq.split_params()
+    assert rtlib.rt_trace_sdf(out, ctypes.c_void_p(520), 4, ctypes.byref(good), ctypes.c_void_p(1024), None) == 1
+    assert b"aligned" in rtlib.rt_last_error()
+    # n = 0 is a no-op that succeeds without touching the device
+    assert rtlib.rt_trace_sdf(out, None, 0, ctypes.byref(good), None, None) == 0
+    rtlib.rt_sdf_destroy.argtypes = [ctypes.c_void_p]
+    rtlib.rt_sdf_destroy(out)

@@ -1,0 +1,320 @@
+"""Device path against the CPU checker, element by element, on seeded inputs.
+
+Sizes: the tiny scene (344 triangles, 32^3 grid, 64x64 rays plus a ragged
+tail) and the medium scene (25,732 triangles, 64^3 grid) span many thread
+blocks and a partial last block; the full-size frame workload is sampled in
+test_gpu_fullsize.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import rays as R
+from synth import scene as S
+from tests.parity import check_bvh_resolved, check_sdf_resolved, gpu_hits_to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+class World:
+    def __init__(self, name, n_grid, gi_count, ragged=77, bake_oracle=True):
+        import paper_2305_07253_gb300 as rq
+        self.rq = rq
+        self.s = S.make_scene(name)
+        s = self.s
+        self.n = [n_grid] * 3
+        self.scene = rq.rt_scene_build(_cuda(s.verts), _cuda(s.tris))
+        self.bvh = O.BVH(s.verts, s.tris)
+        self.rays = np.concatenate([R.primary_rays(s), R.gi_rays(s, gi_count + ragged, 5, s.diagonal)])
+        self.rays_d = _cuda(self.rays)
+        if bake_oracle:
+            vals = O.bake_brute(s.verts, s.tris, s.lo, s.hi, self.n).reshape(-1)
+        else:
+            vals = None
+        self.vals64 = vals
+        # the checker's grid rounded to float: the same numbers on both sides
+        if vals is not None:
+            v32 = vals.astype(np.float32)
+            self.grid32 = O.Grid(s.lo, s.hi, self.n, values=v32.astype(np.float64))
+            self.grid64 = O.Grid(s.lo, s.hi, self.n, values=vals)
+            self.gridt = _cuda(v32.reshape(self.n[2], self.n[1], self.n[0]))
+            self.sdf = rq.rt_sdf_create(self.gridt, s.lo, s.hi)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return World("tiny", 32, 4096)
+
+
+@pytest.fixture(scope="module")
+def medium():
+    return World("medium", 64, 8192, bake_oracle=False)
+
+
+def test_scene_build_info(tiny, medium):
+    for w in (tiny, medium):
+        inf = w.scene.info()
+        assert inf.n_tris == w.s.n_tris and inf.n_nodes == w.s.n_tris - 1
+        assert 1 <= inf.max_depth <= inf.stack_depth
+        np.testing.assert_allclose(np.array(inf.lo), w.s.verts.min(axis=0), rtol=0, atol=0)
+        np.testing.assert_allclose(np.array(inf.hi), w.s.verts.max(axis=0), rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("which", ["tiny", "medium"])
+@pytest.mark.parametrize("any_hit", [False, True])
+def test_bvh_parity(which, any_hit, tiny, medium):
+    w = tiny if which == "tiny" else medium
+    g = gpu_hits_to_numpy(w.rq.rt_trace_bvh(w.scene, w.rays_d, any_hit=any_hit))
+    o = w.bvh.trace(w.rays)
+    if not any_hit:
+        check_bvh_resolved(g, o, w.rays, w.s.verts, w.s.tris)
+    else:
+        # any hit: same hit/miss; the reported hit is a real intersection in the interval
+        assert np.mean((g["tracer"] == 1) == (o["tracer"] == 1)) >= 0.9999
+        idx = np.nonzero(g["tracer"] == 1)[0][::7]
+        for i in idx:
+            f = w.s.tris[g["prim"][i]]
+            V = w.s.verts.astype(np.float64)
+            hit, (t, u, v) = O.watertight(w.rays[i, :3], w.rays[i, 4:7], V[f[0]], V[f[1]], V[f[2]])
+            assert hit and w.rays[i, 3] - 1e-5 <= t <= w.rays[i, 7] * (1 + 1e-5)
+            assert abs(t - g["t"][i]) <= 1e-4 * max(1, t)
+
+
+def test_bake_parity_tiny(tiny):
+    rq = tiny.rq
+    s = tiny.s
+    for method in (rq.BAKE_BRUTE, rq.BAKE_BVH):
+        gt = torch.empty((32, 32, 32), dtype=torch.float32, device="cuda")
+        sdf = rq.rt_sdf_create(gt, s.lo, s.hi)
+        rq.rt_sdf_bake(tiny.scene, sdf, method)
+        torch.cuda.synchronize()
+        got = gt.cpu().numpy().reshape(-1).astype(np.float64)
+        err = np.abs(got - tiny.vals64)
+        assert err.max() < 2e-5, err.max()
+    # both methods give the same numbers
+    a = torch.empty((32, 32, 32), dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    rq.rt_sdf_bake(tiny.scene, rq.rt_sdf_create(a, s.lo, s.hi), rq.BAKE_BRUTE)
+    rq.rt_sdf_bake(tiny.scene, rq.rt_sdf_create(b, s.lo, s.hi), rq.BAKE_BVH)
+    assert torch.equal(a, b)
+
+
+def test_bake_parity_medium_sampled(medium):
+    rq = medium.rq
+    s = medium.s
+    gt = torch.empty((64, 64, 64), dtype=torch.float32, device="cuda")
+    rq.rt_sdf_bake(medium.scene, rq.rt_sdf_create(gt, s.lo, s.hi), rq.BAKE_BVH)
+    got = gt.cpu().numpy().reshape(-1).astype(np.float64)
+    idx = np.random.default_rng(0).choice(got.size, 4096, replace=False)
+    grid = O.Grid(s.lo, s.hi, [64, 64, 64], src=medium.bvh)
+    ref = grid.values(idx)
+    assert np.max(np.abs(got[idx] - ref)) < 5e-5
+    # fp16 storage: the float result rounded once
+    gh = torch.empty((64, 64, 64), dtype=torch.float16, device="cuda")
+    rq.rt_sdf_bake(medium.scene, rq.rt_sdf_create(gh, s.lo, s.hi), rq.BAKE_BVH)
+    assert torch.equal(gh, gt.half())
+
+
+def test_sdf_trace_matches_float_march(tiny):
+    rq = tiny.rq
+    p = rq.split_params(mode=rq.MODE_SDF)
+    g = gpu_hits_to_numpy(rq.rt_trace_sdf(tiny.sdf, tiny.rays_d, p))
+    o = O.trace_sdf(tiny.grid32, tiny.rays, O.make_params(mode=3), precision=32)
+    summ = check_sdf_resolved(g, o)
+    assert np.array_equal(g["tracer"], o["tracer"])
+    assert summ["exact"] >= 0.999, summ
+    assert np.array_equal(g["flags"] & 2, o["flags"] & 2)
+
+
+@pytest.mark.parametrize("m", [0.0, 1.0, 2.0, 4.0, math.inf])
+def test_combined_one_split(tiny, m):
+    rq = tiny.rq
+    p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
+    g = gpu_hits_to_numpy(rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p))
+    o = O.trace_combined(tiny.bvh, tiny.grid32, tiny.rays, O.make_params(mode=1, m_near=m), precision=32)
+    same = g["tracer"] == o["tracer"]
+    assert same.mean() >= 0.9999
+    check_bvh_resolved(g, o, tiny.rays, tiny.s.verts, tiny.s.tris, sel=(o["tracer"] == 1) | (g["tracer"] == 1))
+    check_sdf_resolved(g, o, sel=same)
+
+
+def test_endpoint_identities(tiny):
+    """A multiplier of 0 is the pure field trace and +inf the pure triangle trace, bit for bit."""
+    rq = tiny.rq
+    for mode in (rq.MODE_SPLIT1, rq.MODE_SPLIT2):
+        for any_hit in (False, True):
+            p0 = rq.split_params(mode=mode, any_hit=any_hit, m_near=0.0, m_far=0.0)
+            a = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p0)
+            b = rq.rt_trace_sdf(tiny.sdf, tiny.rays_d, p0)
+            assert torch.equal(a, b)
+            pi = rq.split_params(mode=mode, any_hit=any_hit, m_near=math.inf, m_far=math.inf)
+            a = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, pi)
+            b = rq.rt_trace_bvh(tiny.scene, tiny.rays_d, any_hit=any_hit)
+            if not any_hit:
+                assert torch.equal(a, b)
+            else:
+                ga, gb = gpu_hits_to_numpy(a), gpu_hits_to_numpy(b)
+                assert np.array_equal(ga["tracer"] > 0, gb["tracer"] > 0)
+
+
+def _shadow_rays(s, n, seed):
+    src = R.gi_rays(s, n, seed, 1.0)
+    g = np.random.default_rng(seed)
+    lights = g.uniform([0.3, 0.3, 0.3], np.array(s.room) - 0.3, size=(n, 3))
+    o = src[:, :3].astype(np.float64)
+    d = lights - o
+    dist = np.linalg.norm(d, axis=1)
+    d /= dist[:, None]
+    return R.pack(o, d, 0.0, dist - 1e-3 * s.diagonal)
+
+
+@pytest.mark.parametrize("any_hit", [True, False])
+def test_combined_two_split_shadow(tiny, any_hit):
+    rq = tiny.rq
+    rays = _shadow_rays(tiny.s, 3000, 8)
+    p = rq.split_params(mode=rq.MODE_SPLIT2, any_hit=any_hit, m_near=2.0, m_far=2.0)
+    g = gpu_hits_to_numpy(rq.rt_trace_combined(tiny.scene, tiny.sdf, _cuda(rays), p))
+    o = O.trace_combined(tiny.bvh, tiny.grid32, rays, O.make_params(mode=2, any_hit=any_hit, m_near=2.0, m_far=2.0),
+                         precision=32)
+    assert np.mean((g["tracer"] > 0) == (o["tracer"] > 0)) >= 0.999
+    same = g["tracer"] == o["tracer"]
+    check_sdf_resolved(g, o, sel=same & (o["tracer"] == 2))
+    if not any_hit:
+        check_bvh_resolved(g, o, rays, tiny.s.verts, tiny.s.tris, sel=(o["tracer"] == 1) & same)
+
+
+def test_fp16_grid_matches_float_march_on_rounded_values(tiny):
+    rq = tiny.rq
+    s = tiny.s
+    v16 = tiny.vals64.astype(np.float16)
+    gt = _cuda(v16.reshape(32, 32, 32))
+    sdf16 = rq.rt_sdf_create(gt, s.lo, s.hi)
+    grid = O.Grid(s.lo, s.hi, tiny.n, values=v16.astype(np.float64))
+    for mode, m in ((rq.MODE_SDF, 0.0), (rq.MODE_SPLIT1, 2.0)):
+        p = rq.split_params(mode=mode, m_near=m)
+        g = gpu_hits_to_numpy(rq.rt_trace_combined(tiny.scene, sdf16, tiny.rays_d, p))
+        o = O.trace_combined(tiny.bvh, grid, tiny.rays, O.make_params(mode=mode, m_near=m), precision=32)
+        same = g["tracer"] == o["tracer"]
+        assert same.mean() >= 0.9999
+        summ = check_sdf_resolved(g, o, sel=same)
+        assert summ["exact"] >= 0.999
+
+
+def test_edge_cases(tiny):
+    rq = tiny.rq
+    p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=2.0)
+    # empty batch
+    empty = torch.empty((0, 8), dtype=torch.float32, device="cuda")
+    assert rq.rt_trace_combined(tiny.scene, tiny.sdf, empty, p).shape == (0, 6)
+    c = np.array(tiny.s.room) / 2
+    rays = np.array([
+        [*c, 1.0, 1, 0, 0, 1.0],            # zero-length interval t_min == t_max
+        [np.nan, 1, 1, 0, 1, 0, 0, 10],      # NaN origin -> miss
+        [-5, -5, -5, 0, 0, 0, 1, 100],       # outside the room, misses everything
+        [*c, 0.0, 0, 1, 0, 100],             # axis-aligned direction (zero components)
+        [*c, 0.0, 0, 0, -1, 100],
+        [*c, 3.0, 1, 0, 0, 2.0],             # t_min > t_max -> miss
+    ], dtype=np.float32)
+    for mode in range(4):
+        pm = rq.split_params(mode=mode, m_near=2.0, m_far=2.0)
+        g = gpu_hits_to_numpy(rq.rt_trace_combined(tiny.scene, tiny.sdf, _cuda(rays), pm))
+        o = O.trace_combined(tiny.bvh, tiny.grid32, rays, O.make_params(mode=mode, m_near=2.0, m_far=2.0), 32)
+        assert g["tracer"][1] == 0 and g["tracer"][2] == 0 and g["tracer"][5] == 0
+        assert np.array_equal(g["tracer"], o["tracer"]), (mode, g["tracer"], o["tracer"])
+        hit = g["tracer"] > 0
+        np.testing.assert_allclose(g["t"][hit], o["t"][hit], rtol=1e-4)
+
+
+def test_counted_variant_same_hits(tiny):
+    rq = tiny.rq
+    p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=2.0)
+    a = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p)
+    b, cnt = rq.rt_trace_combined_counted(tiny.scene, tiny.sdf, tiny.rays_d, p)
+    assert torch.equal(a, b)
+    c = cnt.cpu().numpy()
+    assert c[0] > 0 and c[1] > 0 and c[2] > 0 and 0 < c[3] <= tiny.rays.shape[0]
+
+
+def test_invalid_arguments_raise(tiny):
+    rq = tiny.rq
+    with pytest.raises(rq.RtError):
+        rq.rt_trace_combined(None, tiny.sdf, tiny.rays_d, rq.split_params(mode=rq.MODE_SPLIT1))
+    with pytest.raises(rq.RtError):
+        rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, rq.split_params(m_near=-1.0))
+
+
+# --------------------------------------------------------------------------
+# adjoint
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def noisy(tiny):
+    s = tiny.s
+    vals = tiny.vals64 + np.random.default_rng(3).normal(scale=0.01, size=tiny.vals64.size)
+    v32 = vals.astype(np.float32)
+    gt = _cuda(v32.reshape(32, 32, 32))
+    sdf = tiny.rq.rt_sdf_create(gt, s.lo, s.hi)
+    grid = O.Grid(s.lo, s.hi, tiny.n, values=v32.astype(np.float64))
+    rays = R.gi_rays(s, 1024, 31, s.diagonal)
+    return gt, sdf, grid, rays
+
+
+def test_backward_matches_oracle_adjoint(tiny, noisy):
+    rq = tiny.rq
+    gt, sdf, grid, rays = noisy
+    p = rq.split_params(mode=rq.MODE_SDF, refine_root=True)
+    rd = _cuda(rays)
+    hits = rq.rt_trace_combined(None, sdf, rd, p)
+    g = gpu_hits_to_numpy(hits)
+    t_o, idx, w = O.sdf_root_adjoint(grid, rays, O.make_params(mode=3))
+    # refined roots agree
+    both = (g["tracer"] == 2) & (idx[:, 0] >= 0)
+    np.testing.assert_allclose(g["t"][both], t_o[both], rtol=1e-4, atol=1e-5)
+    # keep rays that are far from tangent on both sides, weight them randomly
+    _, grad = grid.sample(rays[:, :3].astype(np.float64) + t_o[:, None] * rays[:, 4:7].astype(np.float64))
+    gd = np.einsum("ij,ij->i", grad, rays[:, 4:7].astype(np.float64))
+    keep = both & (gd < -0.1)
+    wt = np.random.default_rng(4).normal(size=len(rays)) * keep
+    gg = torch.zeros_like(gt)
+    rq.rt_trace_combined_backward(None, sdf, rd, p, hits, _cuda(wt.astype(np.float32)), gg)
+    ref = np.zeros(gt.numel())
+    np.add.at(ref, idx[keep].reshape(-1), (w[keep] * wt[keep, None]).reshape(-1))
+    got = gg.cpu().numpy().reshape(-1).astype(np.float64)
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(got - ref)) <= 1e-2 * scale
+
+
+def test_autograd_function_matches_central_differences(tiny, noisy):
+    rq = tiny.rq
+    gt, sdf, grid, rays = noisy
+    p = rq.split_params(mode=rq.MODE_SDF)
+    rd = _cuda(rays[:256])
+    gparam = gt.clone().requires_grad_(False)
+    sdf2 = rq.rt_sdf_create(gparam, sdf.lo, sdf.hi)
+    x = gparam.requires_grad_(True)
+    t, hits = rq.SdfHitDistance.apply(x, rd, None, sdf2, p)
+    ok = torch.isfinite(t)
+    loss = (t[ok] ** 2).sum()
+    loss.backward()
+    assert x.grad is not None and torch.isfinite(x.grad).all()
+    # central differences of the checker's fp64 refined root on the voxels with the largest gradient
+    vals = gparam.detach().cpu().numpy().reshape(-1).astype(np.float64)
+    grad = x.grad.cpu().numpy().reshape(-1)
+    top = np.argsort(-np.abs(grad))[:16]
+    t0, _, _ = O.sdf_root_adjoint(O.Grid(sdf.lo, sdf.hi, tiny.n, values=vals), rays[:256], O.make_params(mode=3))
+    fin = np.isfinite(t0)
+    for vi in top:
+        d = 1e-4
+        vp = vals.copy(); vp[vi] += d
+        vm = vals.copy(); vm[vi] -= d
+        tp, _, _ = O.sdf_root_adjoint(O.Grid(sdf.lo, sdf.hi, tiny.n, values=vp), rays[:256], O.make_params(mode=3))
+        tm, _, _ = O.sdf_root_adjoint(O.Grid(sdf.lo, sdf.hi, tiny.n, values=vm), rays[:256], O.make_params(mode=3))
+        m = fin & np.isfinite(tp) & np.isfinite(tm) & ok.cpu().numpy()
+        fd = np.sum((tp[m] ** 2 - tm[m] ** 2)) / (2 * d)
+        assert grad[vi] == pytest.approx(fd, rel=2e-2, abs=1e-3 * np.abs(grad).max())
