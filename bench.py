@@ -47,7 +47,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=1 << 18)
+    ap.add_argument("--cpu-sample", type=int, default=1920 * 1080)
+    ap.add_argument("--cpu-reps", type=int, default=3)
+    ap.add_argument("--profile", action="store_true",
+                    help="set up, then run only warmup+steps launches of the --only traces (for ncu); prints timings")
+    ap.add_argument("--only", default="all", choices=["all", "combined", "bvh", "sdf"])
     return ap.parse_args()
 
 
@@ -194,6 +198,15 @@ def run_ours(args):
         return ms
 
     K, W = args.steps, max(3, args.warmup)
+    if args.profile:
+        sel = {"combined": [("combined", p_mid)], "bvh": [("bvh", p_bvh)], "sdf": [("sdf", p_sdf)]}
+        todo = sel.get(args.only, [("combined", p_mid), ("bvh", p_bvh), ("sdf", p_sdf)])
+        out = {}
+        for name, p in todo:
+            out[name] = time_steps(p, args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"profile_ms_per_launch": out, "rays": n_rays}), flush=True)
+        return
     props = torch.cuda.get_device_properties(dev)
     uuid = getattr(props, "uuid", None)
     uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (str(uuid) if uuid else None)
@@ -268,7 +281,8 @@ def run_ours(args):
         "trace_hash": trace_hash(),
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"], line["hit_t_err_vs_fp64"] = cpu_baseline(s, rays, hits_mid, args.cpu_sample)
+        line["cpu_baseline"], line["hit_t_err_vs_fp64"] = cpu_baseline(s, rays, hits_mid, args.cpu_sample,
+                                                                       args.cpu_reps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -288,14 +302,17 @@ def _oracle_world(s, sample_rays):
     return O, bvh, grid, prm
 
 
-def cpu_baseline(s, rays, gpu_hits, sample):
+def cpu_baseline(s, rays, gpu_hits, sample, reps):
     idx = np.linspace(0, rays.shape[0] - 1, min(sample, rays.shape[0])).astype(np.int64)
     sr = rays[idx]
     O, bvh, grid, prm = _oracle_world(s, sr)
     cores = O.default_threads()
-    t0 = time.perf_counter()
-    o = O.trace_combined(bvh, grid, sr, prm, precision=64, nthreads=cores)
-    dt = time.perf_counter() - t0
+    times = []
+    for _ in range(max(1, reps)):
+        t0 = time.perf_counter()
+        o = O.trace_combined(bvh, grid, sr, prm, precision=64, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    dt = statistics.median(times)
     g = gpu_hits[idx]
     gt = g[:, 0].view(np.float32).astype(np.float64)
     gtr = g[:, 4]
@@ -310,7 +327,7 @@ def cpu_baseline(s, rays, gpu_hits, sample):
     err["sample"] = f"{len(idx)} rays evenly spaced over the batch, fp64 checker, m={M_MIDDLE}"
     cb = {"value": len(idx) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
           "sample": f"{len(idx)} of {rays.shape[0]} GI rays (evenly spaced), fp64 combined query m={M_MIDDLE}, "
-                    f"grid values evaluated before timing", "seconds": dt}
+                    f"grid values evaluated before timing, median of {max(1, reps)} passes", "seconds": dt}
     return cb, err
 
 

@@ -20,6 +20,8 @@
  *     same thread).
  *   - Device-side limits (traversal stack depth, march step budget) never
  *     abort a kernel: they set bits in rt_hit.flags.
+ *   - Eq. 1 is defined for real numbers: a query with a NaN in o, d, t_min or
+ *     t_max is answered with a miss.  t_min > t_max is an empty query (miss).
  *   - The library uses the current CUDA device of the calling thread; a handle
  *     must be used on the device it was created on.
  */
@@ -161,7 +163,7 @@ rt_status rt_sdf_destroy(rt_sdf* sdf);
  * fast sweeping build (Section 3, "Distance Field Generation") by its exact
  * definition.  method: RT_BAKE_BRUTE tests every triangle for every sample
  * (triangles staged through shared memory); RT_BAKE_BVH prunes with the BVH
- * (same result); RT_BAKE_AUTO picks by problem size.  Writes through the
+ * (same result up to float rounding); RT_BAKE_AUTO picks by problem size.  Writes through the
  * grid pointer given to rt_sdf_create. */
 rt_status rt_sdf_bake(const rt_scene* scene, rt_sdf* sdf, int32_t method, void* stream);
 

@@ -92,6 +92,16 @@ static void ray_load(const float* r, double o[3], double d[3], double* tmin, dou
     d[0] = r[4]; d[1] = r[5]; d[2] = r[6]; *tmax = r[7];
 }
 
+/* Eq. 1 is defined for real o, d, t_min, t_max with t_min <= t_max (the paper
+ * assumes this ordering, Section 2): any other query has no intersection and
+ * is reported as a miss. */
+static int ray_has_nan(const float* r)
+{
+    for (int k = 0; k < 8; ++k)
+        if (isnan(r[k])) return 1;
+    return !(r[3] <= r[7]);
+}
+
 static void hit_miss(or_hit* h)
 {
     h->t = INFINITY;
@@ -468,7 +478,7 @@ static void bvh_range(void* vctx, int64_t s, int64_t e)
         ray_load(c->rays + 8 * i, o, d, &ta, &tb);
         or_hit h;
         hit_miss(&h);
-        bvh_segment(c->b, o, d, ta, tb, c->any_hit, &h);
+        if (!ray_has_nan(c->rays + 8 * i)) bvh_segment(c->b, o, d, ta, tb, c->any_hit, &h);
         c->hits[i] = h;
     }
 }
@@ -811,6 +821,10 @@ static void combined_one(const comb_ctx* c, int64_t i)
     ray_load(r, o, d, &tmin, &tmax);
     or_hit h;
     hit_miss(&h);
+    if (ray_has_nan(r)) {
+        c->hits[i] = h;
+        return;
+    }
     int mode = p->mode;
     if (mode == 0 || !c->g) {
         bvh_segment(c->b, o, d, tmin, tmax, p->any_hit, &h);

@@ -28,8 +28,12 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
     Hit h = {__int_as_float(0x7f800000), -1, 0.f, 0.f};
     uint32_t flags = 0;
     int32_t tracer = RT_TRACER_MISS;
+    // Eq. 1 is defined for real o, d and t_min <= t_max; anything else has no intersection
+    const bool valid = !(isnan(o.x) || isnan(o.y) || isnan(o.z) || isnan(d.x) || isnan(d.y) || isnan(d.z)) &&
+                       (tmin <= tmax);
 
-    if (a.mode == RT_MODE_BVH) {
+    if (!valid) {
+    } else if (a.mode == RT_MODE_BVH) {
         if (bvh_segment<COUNT>(a, o, d, tmin, tmax, a.any_hit, h, flags, cnt)) tracer = RT_TRACER_BVH;
     } else if (a.mode == RT_MODE_SDF) {
         March m = sdf_march<COUNT>(a, o, d, tmin, tmax, flags, cnt);

@@ -72,8 +72,7 @@ def check_bvh_resolved(g: dict, o: np.ndarray, rays: np.ndarray, verts, tris, se
         i = idx[j]
         if not (_edge(o["u"][i], o["v"][i]) or _grazing(verts, tris, rays[i], o["prim"][i])):
             bad.append(("gpu miss", int(i)))
-    n = max(1, int(both.sum()))
-    frac_equal = float(same_prim.sum()) / n
+    frac_equal = float(same_prim.sum()) / int(both.sum()) if both.any() else 1.0
     terr = np.abs(g["t"][idx][same_prim] - o["t"][idx][same_prim]) / np.maximum(1.0, np.abs(o["t"][idx][same_prim]))
     assert not bad, f"unconfirmed mismatches: {bad[:10]} (of {len(bad)})"
     assert frac_equal >= min_equal, f"prim ids equal on {frac_equal:.6f}"

@@ -103,7 +103,9 @@ def test_bake_parity_tiny(tiny):
     b = torch.empty_like(a)
     rq.rt_sdf_bake(tiny.scene, rq.rt_sdf_create(a, s.lo, s.hi), rq.BAKE_BRUTE)
     rq.rt_sdf_bake(tiny.scene, rq.rt_sdf_create(b, s.lo, s.hi), rq.BAKE_BVH)
-    assert torch.equal(a, b)
+    assert torch.max(torch.abs(a - b)).item() <= 1e-6
+    far = torch.abs(a) > 1e-5
+    assert torch.equal(torch.sign(a[far]), torch.sign(b[far]))
 
 
 def test_bake_parity_medium_sampled(medium):

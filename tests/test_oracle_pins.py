@@ -371,6 +371,25 @@ def test_march_outside_grid_is_clipped():
     assert h["tracer"] == 2 and h["t"] == pytest.approx(5.0, abs=1e-12)
 
 
+def test_nan_query_is_a_miss():
+    s = S.make_scene("tiny")
+    bvh = O.BVH(s.verts, s.tris)
+    grid = O.Grid(s.lo, s.hi, [8, 8, 8], src=bvh)
+    base = np.array([2.0, 1.5, 2.0, 0.0, 1.0, 0.0, 0.0, 10.0], dtype=np.float32)
+    rays = np.tile(base, (9, 1))
+    for k in range(8):
+        rays[k + 1, k] = np.nan
+    for mode in range(4):
+        for prec in (64, 32):
+            h = O.trace_combined(bvh, grid, rays, O.make_params(mode=mode), prec)
+            assert h["tracer"][0] > 0 and np.all(h["tracer"][1:] == 0)
+    assert np.all(bvh.trace(rays)["tracer"][1:] == 0)
+    # t_min > t_max is empty even where a wall sits exactly at t_max
+    rev = np.array([[2.0, 1.5, 2.0, 2.5, 1.0, 0.0, 0.0, 2.0]], dtype=np.float32)
+    for mode in range(4):
+        assert O.trace_combined(bvh, grid, rev, O.make_params(mode=mode), 32)["tracer"][0] == 0
+
+
 def test_fp32_march_close_to_fp64():
     s = S.make_scene("tiny")
     bvh = O.BVH(s.verts, s.tris)
