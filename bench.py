@@ -37,7 +37,7 @@ UNIT = "rays/s"
 M_MIDDLE = 2.0
 WORKLOAD = "frame-1080p-gi"
 TRACE_SOURCES = ["paper_2305_07253_gb300/csrc/rt_trace.cu", "paper_2305_07253_gb300/csrc/rt_trace_dev.cuh",
-                 "paper_2305_07253_gb300/csrc/rt_internal.cuh"]
+                 "paper_2305_07253_gb300/csrc/rt_internal.cuh", "paper_2305_07253_gb300/csrc/rt_api.cu"]
 
 
 def parse():
@@ -211,25 +211,59 @@ def run_ours(args):
     uuid = getattr(props, "uuid", None)
     uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (str(uuid) if uuid else None)
 
-    # algorithmic bytes per launch, from the counted variant (untimed)
-    counts = {}
+    # algorithmic bytes, from the counted variant and the hit records (untimed)
+    counts, outcome = {}, {}
     for name, p in (("combined", p_mid), ("bvh", p_bvh), ("sdf", p_sdf)):
-        _, c = rq.rt_trace_combined_counted(scene, sdf, rays_d, p)
+        h, c = rq.rt_trace_combined_counted(scene, sdf, rays_d, p)
         counts[name] = [int(x) for x in c.cpu().tolist()]
+        tr = h[:, 4]
+        outcome[name] = {"bvh_hits": int((tr == rq.TRACER_BVH).sum()), "sdf_hits": int((tr == rq.TRACER_SDF).sum())}
+    step_bytes = 4 * 8  # eight float32 corners per march step
 
-    def algo_bytes(c):
-        nodes, tris, steps, _ = c
-        return 32 * n_rays + 24 * n_rays + 64 * nodes + 48 * tris + 8 * 4 * steps
+    def stage_bytes(name, stage):
+        """Algorithmic bytes one launch of `stage` moves (reads of rays, nodes, triangles,
+        grid cells and queue entries; writes of hit records and queue entries)."""
+        nodes, tris, steps, _ = counts[name]
+        n_bvh_hits = outcome[name]["bvh_hits"]
+        if stage == "all":
+            return 32 * n_rays + 24 * n_rays + 64 * nodes + 48 * tris + step_bytes * steps
+        if stage == "bvh_full":
+            return 32 * n_rays + 24 * n_rays + 64 * nodes + 48 * tris
+        if stage == "field_full":
+            return 32 * n_rays + 24 * n_rays + step_bytes * steps
+        if stage == "bvh_near":  # all rays in; hits written; the rest queued
+            fwd = n_rays - n_bvh_hits
+            return 32 * n_rays + 64 * nodes + 48 * tris + 24 * n_bvh_hits + 8 * fwd
+        if stage == "field_split":  # queued rays in; every record written here
+            fwd = n_rays - n_bvh_hits
+            return (8 + 32) * fwd + step_bytes * steps + 24 * fwd
+        raise ValueError(stage)
 
     sampler = ClockSampler(uuid)
     ms_mid = time_steps(p_mid, K, W)
     clocks = sampler.stop()
     ms_bvh = time_steps(p_bvh, K, W)
     ms_sdf = time_steps(p_sdf, K, W)
+    # per-kernel device times (events between the stage launches), untimed for the headline
+    Kt = max(3, min(K, 30))
+    stage_ms = {}
+    for name, p in (("combined", p_mid), ("bvh", p_bvh), ("sdf", p_sdf)):
+        acc = {}
+        for _ in range(Kt):
+            _, st = rq.rt_trace_combined_timed(scene, sdf, rays_d, p, hits)
+            for sname, ms in st:
+                acc.setdefault(sname, []).append(ms)
+        stage_ms[name] = {k: statistics.mean(v) for k, v in acc.items()}
+    # the same step with the one-thread-per-query kernel, for comparison
+    prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
+    try:
+        ms_simple = {name: time_steps(p, max(3, K // 4), W) for name, p in
+                     (("combined", p_mid), ("bvh", p_bvh), ("sdf", p_sdf))}
+    finally:
+        rq.rt_set_tuning(prev)
     rq.rt_trace_combined(scene, sdf, rays_d, p_mid, hits)
     torch.cuda.synchronize()
     hits_mid = hits.cpu().numpy()
-
     # end to end through host buffers: pinned rays in, pinned hit records out
     rays_h = torch.from_numpy(rays).pin_memory()
     hits_h = torch.empty((n_rays, 6), dtype=torch.int32).pin_memory()
@@ -252,31 +286,44 @@ def run_ours(args):
 
     value = world * n_rays / (ms_mid * 1e-3)
     peak, peak_kind = peaks()
-    ab = algo_bytes(counts["combined"])
-    achieved = ab / (ms_mid * 1e-3) / 1e9
+    dom_stage, dom_ms = max(stage_ms["combined"].items(), key=lambda kv: kv[1])
+    ab = stage_bytes("combined", dom_stage)
+    achieved = ab / (dom_ms * 1e-3) / 1e9
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tf):
         d = json.load(open(tf))
         if d.get("trace_hash") == trace_hash() and d.get("workload") == WORKLOAD:
-            traffic = d.get("combined_bytes_per_launch")
+            traffic = d.get("bytes_per_launch", {}).get(dom_stage)
+    kernel_names = {"bvh_near": "k_stage_bvh (near triangle sub-interval)",
+                    "field_split": "k_stage_field (distance-field sub-interval)",
+                    "bvh_full": "k_stage_bvh", "field_full": "k_stage_field", "all": "k_trace"}
+    stages = {name: {st: {"ms": ms, "algorithmic_bytes": stage_bytes(name, st),
+                          "GBps": stage_bytes(name, st) / (ms * 1e-3) / 1e9}
+                     for st, ms in v.items()} for name, v in stage_ms.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_mid, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded procedural scene and rays)",
-        "config": config_dict(s, n_rays, {"parallelism": f"rays replicated per GPU x{world}" if world > 1 else "1 GPU"}),
+        "config": config_dict(s, n_rays, {"parallelism": f"rays replicated per GPU x{world}" if world > 1 else "1 GPU",
+                                          "tuning": rq.rt_get_tuning().as_dict()}),
         "bvh_only": {"value": world * n_rays / (ms_bvh * 1e-3), "ms_per_step": ms_bvh},
         "sdf_only": {"value": world * n_rays / (ms_sdf * 1e-3), "ms_per_step": ms_sdf},
         "combined": {"value": value, "ms_per_step": ms_mid, "m": M_MIDDLE},
         "ordering_ok": bool(ms_bvh > ms_mid >= ms_sdf),
-        "work_counts": {k: {"nodes": v[0], "tris": v[1], "steps": v[2], "field_queries": v[3]}
+        "one_thread_per_query": {k: {"ms_per_step": v, "value": world * n_rays / (v * 1e-3)}
+                                 for k, v in ms_simple.items()},
+        "stages": stages,
+        "work_counts": {k: {"nodes": v[0], "tris": v[1], "steps": v[2], "field_queries": v[3], **outcome[k]}
                         for k, v in counts.items()},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "k_trace<false> (combined, m=2)",
-                     "algorithmic_bytes_per_launch": ab, "peak_kind": f"of {peak_kind}"},
+                     "traffic": traffic, "kernel": kernel_names.get(dom_stage, dom_stage) + ", combined m=2",
+                     "algorithmic_bytes_per_launch": ab, "launch_ms": dom_ms, "peak_kind": f"of {peak_kind}",
+                     "step": {"algorithmic_bytes": stage_bytes("combined", "all"),
+                              "GBps": stage_bytes("combined", "all") / (ms_mid * 1e-3) / 1e9}},
         "e2e": {"value": world * n_rays / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(rays.nbytes),
                 "d2h_bytes_per_step": int(n_rays * 24), "ms_per_step": ms_e2e},
-        "gpu_launches": K,
+        "gpu_launches": K * len(stage_ms["combined"]),
         "clocks": clocks,
         "trace_hash": trace_hash(),
     }

@@ -156,6 +156,17 @@ rt_status rt_sdf_create(const void* d_grid, int32_t dtype, const float lo[3], co
                         const int32_t n[3], rt_sdf** out);
 rt_status rt_sdf_destroy(rt_sdf* sdf);
 
+/* Build (or rebuild) the library's cell-corner copy of the grid of `sdf`:
+ * for every cell the 8 corner values stored together (32 bytes for float32,
+ * 16 bytes for float16), so that a march step reads one vector instead of 8
+ * scalars.  Same values, same arithmetic, same results.  rt_sdf_bake calls it
+ * itself; call it after writing the grid memory any other way (for example
+ * after an optimiser step), otherwise the traces keep reading the old copy.
+ * Traces read the plain grid until the first prepare, or when the tuning
+ * selects the plain layout.  Memory: 8x (cells) the grid, owned by the
+ * handle, released by rt_sdf_destroy.  Enqueued on `stream`. */
+rt_status rt_sdf_prepare(rt_sdf* sdf, void* stream);
+
 /* Fill the grid of `sdf` with the signed distance to the nearest triangle of
  * `scene`: exact closest point on each triangle, sign from the angle-weighted
  * pseudonormal of the closest face, edge or vertex (positive on the side the
@@ -191,6 +202,18 @@ rt_status rt_trace_combined_counted(const rt_scene* scene, const rt_sdf* sdf, co
                                     int64_t n, const rt_split_params* params, rt_hit* d_hits,
                                     unsigned long long* d_counters, void* stream);
 
+/* Same as rt_trace_combined, and also reports how long each kernel of the
+ * call ran: stage_ms[k] for the k-th launch (at most 3: one per sub-interval
+ * kind with the wavefront kernels, 1 with the simple kernel), *n_stages the
+ * number of launches, stage_kind[k] RT_STAGE_* (nullable).  Times come from
+ * CUDA events recorded on `stream` between the launches; the call
+ * synchronises `stream`.  Used to measure per-kernel throughput. */
+enum { RT_STAGE_ALL = 0, RT_STAGE_BVH_FULL = 1, RT_STAGE_BVH_NEAR = 2, RT_STAGE_BVH_FAR = 3,
+       RT_STAGE_FIELD_FULL = 4, RT_STAGE_FIELD_SPLIT = 5 };
+rt_status rt_trace_combined_timed(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
+                                  const rt_split_params* params, rt_hit* d_hits, float stage_ms[3],
+                                  int32_t stage_kind[3], int32_t* n_stages, void* stream);
+
 /* Adjoint of the field-resolved hit distance.  For each query whose hit
  * record (from a forward call with the same params, refine_root = 1) has
  * tracer == RT_TRACER_SDF, the root p* = o + t d of phi = eps satisfies
@@ -205,6 +228,33 @@ rt_status rt_trace_combined_counted(const rt_scene* scene, const rt_sdf* sdf, co
 rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays,
                                      int64_t n, const rt_split_params* params, const rt_hit* d_hits,
                                      const float* d_grad_t, float* d_grad_grid, void* stream);
+
+/* Launch tuning of the trace kernels (process-wide; applies to later calls).
+ *   kernel        RT_KERNEL_WAVEFRONT (default): persistent stage kernels, one
+ *                 per sub-interval kind, with per-lane refill from a global
+ *                 queue, so rays that switch tracer mid-query are regrouped
+ *                 across the whole batch; RT_KERNEL_SIMPLE: one thread per
+ *                 query runs all its sub-intervals.
+ *   block         threads per block (multiple of 32, 32..1024)
+ *   blocks_per_sm persistent grid = SMs x this (0: as many as fit)
+ *   refill_min    a warp fetches new queries when at least this many lanes
+ *                 are idle (1..32), or when all are
+ *   grid_layout   RT_LAYOUT_CELLS (default): use the cell-corner copy when it
+ *                 exists; RT_LAYOUT_PLAIN: always read the plain grid
+ * Results do not depend on the tuning. */
+typedef struct {
+    int32_t kernel;
+    int32_t block;
+    int32_t blocks_per_sm;
+    int32_t refill_min;
+    int32_t grid_layout;
+} rt_tuning;
+
+enum { RT_KERNEL_WAVEFRONT = 0, RT_KERNEL_SIMPLE = 1 };
+enum { RT_LAYOUT_CELLS = 0, RT_LAYOUT_PLAIN = 1 };
+
+rt_status rt_set_tuning(const rt_tuning* tuning);
+rt_status rt_get_tuning(rt_tuning* tuning);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* rt_last_error(void);

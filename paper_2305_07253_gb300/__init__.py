@@ -31,9 +31,14 @@ FLAG_STACK_OVERFLOW, FLAG_STEP_LIMIT, FLAG_ITER_LIMIT = 1, 2, 4
 GRID_F32, GRID_F16 = 0, 1
 BAKE_AUTO, BAKE_BRUTE, BAKE_BVH = 0, 1, 2
 
+KERNEL_WAVEFRONT, KERNEL_SIMPLE = 0, 1
+LAYOUT_CELLS, LAYOUT_PLAIN = 0, 1
+
 EXPORTS = ("rt_scene_build", "rt_scene_info_get", "rt_scene_destroy", "rt_sdf_create", "rt_sdf_destroy",
-           "rt_sdf_bake", "rt_trace_bvh", "rt_trace_sdf", "rt_trace_combined", "rt_trace_combined_counted",
-           "rt_trace_combined_backward", "rt_last_error", "rt_version")
+           "rt_sdf_prepare", "rt_sdf_bake", "rt_trace_bvh", "rt_trace_sdf", "rt_trace_combined",
+           "rt_trace_combined_counted", "rt_trace_combined_timed", "rt_trace_combined_backward", "rt_set_tuning",
+           "rt_get_tuning",
+           "rt_last_error", "rt_version")
 
 
 class RtError(RuntimeError):
@@ -46,6 +51,14 @@ class rt_split_params(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("any_hit", ctypes.c_int32), ("m_near", ctypes.c_float),
                 ("m_far", ctypes.c_float), ("max_steps", ctypes.c_int32), ("hit_eps_vox", ctypes.c_float),
                 ("min_step_vox", ctypes.c_float), ("refine_root", ctypes.c_int32)]
+
+
+class rt_tuning(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("refill_min", ctypes.c_int32), ("grid_layout", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class rt_scene_info(ctypes.Structure):
@@ -75,11 +88,15 @@ def lib() -> ctypes.CDLL:
             "rt_scene_destroy": [P],
             "rt_sdf_create": [P, i32, P, P, P, P],
             "rt_sdf_destroy": [P],
+            "rt_sdf_prepare": [P, P],
+            "rt_set_tuning": [P],
+            "rt_get_tuning": [P],
             "rt_sdf_bake": [P, P, i32, P],
             "rt_trace_bvh": [P, P, i64, i32, P, P],
             "rt_trace_sdf": [P, P, i64, P, P, P],
             "rt_trace_combined": [P, P, P, i64, P, P, P],
             "rt_trace_combined_counted": [P, P, P, i64, P, P, P, P],
+            "rt_trace_combined_timed": [P, P, P, i64, P, P, P, P, P, P],
             "rt_trace_combined_backward": [P, P, P, i64, P, P, P, P, P],
         }
         for name, args in sig.items():
@@ -184,7 +201,30 @@ def rt_sdf_create(grid: torch.Tensor, lo, hi) -> Sdf:
 
 
 def rt_sdf_bake(scene: Scene, sdf: Sdf, method: int = BAKE_AUTO, stream=None) -> None:
+    """Exact signed-distance bake into the grid of `sdf` (also refreshes its cell copy)."""
     _check(lib().rt_sdf_bake(scene.handle, sdf.handle, int(method), _stream(stream)))
+
+
+def rt_sdf_prepare(sdf: Sdf, stream=None) -> None:
+    """(Re)build the cell-corner copy of the grid; call after writing the grid tensor."""
+    _check(lib().rt_sdf_prepare(sdf.handle, _stream(stream)))
+
+
+def rt_get_tuning() -> rt_tuning:
+    t = rt_tuning()
+    _check(lib().rt_get_tuning(ctypes.byref(t)))
+    return t
+
+
+def rt_set_tuning(t: rt_tuning | None = None, **kw) -> rt_tuning:
+    """Set launch tuning (process-wide); keyword arguments override fields of `t`
+    (default: the current tuning).  Returns the previous tuning."""
+    prev = rt_get_tuning()
+    new = rt_tuning.from_buffer_copy(t if t is not None else prev)
+    for k, v in kw.items():
+        setattr(new, k, int(v))
+    _check(lib().rt_set_tuning(ctypes.byref(new)))
+    return prev
 
 
 def _rays_hits(rays: torch.Tensor, hits: torch.Tensor | None) -> torch.Tensor:
@@ -229,6 +269,22 @@ def rt_trace_combined_counted(scene: Scene | None, sdf: Sdf | None, rays: torch.
                                            _dptr(rays), rays.shape[0], ctypes.byref(params), _dptr(hits),
                                            _dptr(counters), _stream(stream)))
     return hits, counters
+
+
+STAGE_NAMES = {0: "all", 1: "bvh_full", 2: "bvh_near", 3: "bvh_far", 4: "field_full", 5: "field_split"}
+
+
+def rt_trace_combined_timed(scene: Scene | None, sdf: Sdf | None, rays: torch.Tensor, params: rt_split_params,
+                            hits: torch.Tensor | None = None, stream=None):
+    """Returns (hits, [(stage name, ms), ...]) with the device time of each kernel launch."""
+    hits = _rays_hits(rays, hits)
+    ms = (ctypes.c_float * 3)()
+    kinds = (ctypes.c_int32 * 3)()
+    n = ctypes.c_int32()
+    _check(lib().rt_trace_combined_timed(scene.handle if scene else None, sdf.handle if sdf else None, _dptr(rays),
+                                         rays.shape[0], ctypes.byref(params), _dptr(hits), ms, kinds,
+                                         ctypes.byref(n), _stream(stream)))
+    return hits, [(STAGE_NAMES[kinds[k]], float(ms[k])) for k in range(n.value)]
 
 
 def rt_trace_combined_backward(scene: Scene | None, sdf: Sdf, rays: torch.Tensor, params: rt_split_params,
@@ -279,6 +335,7 @@ class SdfHitDistance(torch.autograd.Function):
     def forward(ctx, grid, rays, scene, sdf, params):
         if sdf.grid.data_ptr() != grid.data_ptr():
             raise ValueError("grid must be the tensor wrapped by sdf")
+        rt_sdf_prepare(sdf)  # the grid may have changed since the last call
         p = rt_split_params.from_buffer_copy(params)
         p.refine_root = 1
         hits = rt_trace_combined(scene, sdf, rays, p)

@@ -12,6 +12,33 @@
 
 static thread_local char g_err[512] = "";
 
+// process-wide launch tuning (see rt_set_tuning)
+static rt_tuning g_tuning = {RT_KERNEL_WAVEFRONT, 128, 0, 16, RT_LAYOUT_CELLS};
+
+const rt_tuning& rt_current_tuning() { return g_tuning; }
+
+extern "C" rt_status rt_set_tuning(const rt_tuning* t)
+{
+    if (!t) return rt_fail(RT_ERR_INVALID_ARG, "tuning is null");
+    if (t->kernel != RT_KERNEL_WAVEFRONT && t->kernel != RT_KERNEL_SIMPLE)
+        return rt_fail(RT_ERR_INVALID_ARG, "kernel %d", t->kernel);
+    if (t->block < 32 || t->block > 1024 || t->block % 32)
+        return rt_fail(RT_ERR_INVALID_ARG, "block %d must be a multiple of 32 in [32, 1024]", t->block);
+    if (t->blocks_per_sm < 0 || t->blocks_per_sm > 64) return rt_fail(RT_ERR_INVALID_ARG, "blocks_per_sm %d", t->blocks_per_sm);
+    if (t->refill_min < 1 || t->refill_min > 32) return rt_fail(RT_ERR_INVALID_ARG, "refill_min %d", t->refill_min);
+    if (t->grid_layout != RT_LAYOUT_CELLS && t->grid_layout != RT_LAYOUT_PLAIN)
+        return rt_fail(RT_ERR_INVALID_ARG, "grid_layout %d", t->grid_layout);
+    g_tuning = *t;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_get_tuning(rt_tuning* t)
+{
+    if (!t) return rt_fail(RT_ERR_INVALID_ARG, "tuning is null");
+    *t = g_tuning;
+    return RT_OK;
+}
+
 rt_status rt_fail(rt_status s, const char* fmt, ...)
 {
     va_list ap;
@@ -69,6 +96,7 @@ void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, con
     }
     if (sdf) {
         a.grid = sdf->grid;
+        a.cells = sdf->cells;
         a.grid_f16 = sdf->dtype == RT_GRID_F16;
         for (int k = 0; k < 3; ++k) {
             a.glo[k] = sdf->lo[k];
@@ -165,6 +193,9 @@ extern "C" rt_status rt_sdf_create(const void* d_grid, int32_t dtype, const floa
     if (cnt > ((int64_t)1 << 40)) return rt_fail(RT_ERR_INVALID_ARG, "grid too large");
     rt_sdf* g = new (std::nothrow) rt_sdf();
     if (!g) return rt_fail(RT_ERR_OOM, "host allocation failed");
+    g->cells = nullptr;
+    g->cells_bytes = 0;
+    cudaGetDevice(&g->device);
     g->grid = d_grid;
     g->dtype = dtype;
     for (int k = 0; k < 3; ++k) {
@@ -182,8 +213,18 @@ extern "C" rt_status rt_sdf_create(const void* d_grid, int32_t dtype, const floa
 
 extern "C" rt_status rt_sdf_destroy(rt_sdf* sdf)
 {
+    if (!sdf) return RT_OK;
+    if (sdf->cells) cudaFree(sdf->cells);
     delete sdf;
     return RT_OK;
+}
+
+extern "C" rt_status rt_sdf_prepare(rt_sdf* sdf, void* stream)
+{
+    if (!sdf) return rt_fail(RT_ERR_INVALID_ARG, "grid is null");
+    rt_status st = device_matches(sdf->device);
+    if (st != RT_OK) return st;
+    return rt_launch_prepare(sdf, (cudaStream_t)stream);
 }
 
 extern "C" rt_status rt_sdf_bake(const rt_scene* sc, rt_sdf* sdf, int32_t method, void* stream)
@@ -192,12 +233,14 @@ extern "C" rt_status rt_sdf_bake(const rt_scene* sc, rt_sdf* sdf, int32_t method
     if (method < 0 || method > 2) return rt_fail(RT_ERR_INVALID_ARG, "bake method %d", method);
     rt_status st = device_matches(sc->device);
     if (st != RT_OK) return st;
-    return rt_launch_bake(sc, sdf, method, (cudaStream_t)stream);
+    st = rt_launch_bake(sc, sdf, method, (cudaStream_t)stream);
+    if (st != RT_OK) return st;
+    return rt_launch_prepare(sdf, (cudaStream_t)stream);
 }
 
 static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
                               const rt_split_params* p, rt_hit* hits, unsigned long long* counters,
-                              void* stream)
+                              void* stream, StageTiming* timing = nullptr)
 {
     rt_status st = check_params(p);
     if (st != RT_OK) return st;
@@ -217,7 +260,40 @@ static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ra
     a.hits = hits;
     a.n = n;
     a.counters = counters;
-    return rt_launch_trace(a, counters != nullptr, (cudaStream_t)stream);
+    return rt_launch_trace(a, counters != nullptr, (cudaStream_t)stream, timing);
+}
+
+extern "C" rt_status rt_trace_combined_timed(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
+                                             const rt_split_params* params, rt_hit* hits, float stage_ms[3],
+                                             int32_t stage_kind[3], int32_t* n_stages, void* stream)
+{
+    if (!stage_ms || !n_stages) return rt_fail(RT_ERR_INVALID_ARG, "null stage_ms or n_stages");
+    *n_stages = 0;
+    if (n == 0) return trace_common(sc, sdf, rays, n, params, hits, nullptr, stream);
+    StageTiming tm = {};
+    int made = 0;
+    rt_status st = RT_OK;
+    for (; made < 4; ++made) {
+        cudaError_t e = cudaEventCreate(&tm.events[made]);
+        if (e != cudaSuccess) { st = rt_cuda_fail(e, "cudaEventCreate"); break; }
+    }
+    if (st == RT_OK) st = trace_common(sc, sdf, rays, n, params, hits, nullptr, stream, &tm);
+    if (st == RT_OK) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) st = rt_cuda_fail(e, "cudaStreamSynchronize");
+    }
+    if (st == RT_OK) {
+        for (int k = 0; k < tm.n_launches; ++k) {
+            float ms = 0.f;
+            cudaError_t e = cudaEventElapsedTime(&ms, tm.events[k], tm.events[k + 1]);
+            if (e != cudaSuccess) { st = rt_cuda_fail(e, "cudaEventElapsedTime"); break; }
+            stage_ms[k] = ms;
+            if (stage_kind) stage_kind[k] = tm.kinds[k];
+        }
+        if (st == RT_OK) *n_stages = tm.n_launches;
+    }
+    for (int k = 0; k < made; ++k) cudaEventDestroy(tm.events[k]);
+    return st;
 }
 
 extern "C" rt_status rt_trace_bvh(const rt_scene* sc, const rt_ray* rays, int64_t n, int32_t any_hit, rt_hit* hits,

@@ -39,11 +39,12 @@ __global__ void __launch_bounds__(kBwdBlock) k_backward(const TraceArgs a, const
     const float t = refine(a, o, d, m.t_prev, m.t);
     const float px = __fmaf_rn(t, d.x, o.x), py = __fmaf_rn(t, d.y, o.y), pz = __fmaf_rn(t, d.z, o.z);
     Cell c = locate(a, px, py, pz);
+    const int64_t base = grid_base(a, c);
     const int64_t sy = a.gn[0], sz = (int64_t)a.gn[0] * a.gn[1];
     const int64_t off[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
     float v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = grid_at(a, c.base + off[k]);
+    for (int k = 0; k < 8; ++k) v[k] = grid_at(a, base + off[k]);
     const float fx = c.f[0], fy = c.f[1], fz = c.f[2];
     const float gx = c.clamped[0] ? 0.f
         : ((v[1] - v[0]) * (1 - fy) * (1 - fz) + (v[3] - v[2]) * fy * (1 - fz) + (v[5] - v[4]) * (1 - fy) * fz +
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(kBwdBlock) k_backward(const TraceArgs a, const
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const float w = ((k & 1) ? fx : 1 - fx) * ((k & 2) ? fy : 1 - fy) * ((k & 4) ? fz : 1 - fz);
-        atomicAdd(grad_grid + c.base + off[k], s * w);
+        atomicAdd(grad_grid + base + off[k], s * w);
     }
 }
 

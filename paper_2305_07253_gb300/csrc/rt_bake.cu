@@ -199,7 +199,51 @@ __global__ void __launch_bounds__(kBakeBlock) k_bake_bvh(const BakeArgs b)
     store(b, i, signed_distance(p, nb, b.tris, b.pn));
 }
 
+// cell-corner copy: the 8 corners of cell (i,j,k) stored together, order
+// v000 v100 v010 v110 v001 v101 v011 v111 (x fastest), cells x fastest
+__global__ void k_cells(const void* grid, int32_t f16, int32_t nx, int32_t ny, int32_t nz, void* cells)
+{
+    const int64_t cx = nx - 1, cy = ny - 1;
+    const int64_t count = cx * cy * (int64_t)(nz - 1);
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= count) return;
+    const int64_t i = c % cx, j = (c / cx) % cy, k = c / (cx * cy);
+    const int64_t b = i + (int64_t)nx * (j + (int64_t)ny * k);
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    const int64_t idx[8] = {b, b + 1, b + sy, b + sy + 1, b + sz, b + sz + 1, b + sz + sy, b + sz + sy + 1};
+    if (f16) {
+        const __half* g = reinterpret_cast<const __half*>(grid);
+        __half2 h[4];
+        for (int q = 0; q < 4; ++q) h[q] = __halves2half2(g[idx[2 * q]], g[idx[2 * q + 1]]);
+        reinterpret_cast<uint4*>(cells)[c] = *reinterpret_cast<const uint4*>(h);
+    } else {
+        const float* g = reinterpret_cast<const float*>(grid);
+        float4* out = reinterpret_cast<float4*>(cells) + 2 * c;
+        out[0] = make_float4(g[idx[0]], g[idx[1]], g[idx[2]], g[idx[3]]);
+        out[1] = make_float4(g[idx[4]], g[idx[5]], g[idx[6]], g[idx[7]]);
+    }
+}
+
 }  // namespace
+
+rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s)
+{
+    const int64_t count = (int64_t)(sdf->n[0] - 1) * (sdf->n[1] - 1) * (sdf->n[2] - 1);
+    const int64_t bytes = count * (sdf->dtype == RT_GRID_F16 ? 16 : 32);
+    if (!sdf->cells || sdf->cells_bytes != bytes) {
+        if (sdf->cells) cudaFree(sdf->cells);
+        sdf->cells = nullptr;
+        sdf->cells_bytes = 0;
+        RT_CUDA_TRY(cudaMalloc(&sdf->cells, (size_t)bytes));
+        sdf->cells_bytes = bytes;
+    }
+    const int64_t blocks = (count + 255) / 256;
+    if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "grid too large");
+    k_cells<<<(unsigned)blocks, 256, 0, s>>>(sdf->grid, sdf->dtype == RT_GRID_F16, sdf->n[0], sdf->n[1], sdf->n[2],
+                                             sdf->cells);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
 
 rt_status rt_launch_bake(const rt_scene* sc, const rt_sdf* sdf, int32_t method, cudaStream_t s)
 {

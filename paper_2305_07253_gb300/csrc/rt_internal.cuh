@@ -1,7 +1,7 @@
 // Internal data layout and device helpers of the combined ray query library.
 //
-// HBM layout (all arrays 16-byte aligned, built once per scene):
-//   nodes  : n_tris-1 internal BVH nodes, 64 B each (four 16-byte vectors):
+// HBM layout (built once per scene / per grid):
+//   nodes  : n_tris-1 internal BVH nodes, 64 B each, read as two 32-byte loads:
 //              a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
 //              b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
 //              c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
@@ -11,6 +11,10 @@
 //   pn     : 112 B per triangle in leaf order: face normal, 3 edge and 3 vertex
 //            pseudonormals (float4 each), read only by the distance bake
 //   grid   : caller memory, dense n0*n1*n2 float32 or float16, x fastest
+//   cells  : optional library copy of the grid with the 8 corners of every cell
+//            stored together (32 B float32 / 16 B float16 per cell, cells x
+//            fastest), so one march step is one vector load instead of eight
+//            scalar ones; identical values, identical arithmetic
 #pragma once
 
 #include <cuda_fp16.h>
@@ -21,7 +25,7 @@
 
 #define RT_STACK_DEPTH 64
 
-struct __align__(16) BNode {
+struct __align__(32) BNode {
     float4 a, b, c;
     int4 d;
 };
@@ -42,6 +46,9 @@ struct rt_sdf {
     int32_t dtype;
     float lo[3], hi[3], h[3], ih[3];
     int32_t n[3];
+    void* cells;        // library-owned cell-corner copy (null until rt_sdf_prepare)
+    int64_t cells_bytes;
+    int device;
 };
 
 // Everything one trace kernel needs, passed by value.
@@ -50,6 +57,7 @@ struct TraceArgs {
     const float4* tris;
     int32_t root;        // 0 (internal), ~0 (single leaf) or INT32_MIN (no triangles)
     const void* grid;    // null: no field
+    const void* cells;   // null: read the plain grid
     int32_t grid_f16;
     float glo[3], ghi[3], gih[3];
     int32_t gn[3];
@@ -74,10 +82,20 @@ rt_status rt_cuda_fail(cudaError_t e, const char* what);
         if (_e != cudaSuccess) return rt_cuda_fail(_e, #expr);    \
     } while (0)
 
+const rt_tuning& rt_current_tuning();
+
 // launchers implemented in the .cu files
-rt_status rt_launch_trace(const TraceArgs& a, bool counted, cudaStream_t s);
+// timing: when non-null, events[k] is recorded before launch k and events[n] after
+// the last; kinds[k] receives the RT_STAGE_* of launch k; *n_launches the count
+struct StageTiming {
+    cudaEvent_t events[4];
+    int32_t kinds[3];
+    int32_t n_launches;
+};
+rt_status rt_launch_trace(const TraceArgs& a, bool counted, cudaStream_t s, StageTiming* timing = nullptr);
 rt_status rt_launch_backward(const TraceArgs& a, const float* grad_t, float* grad_grid, cudaStream_t s);
 rt_status rt_build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, cudaStream_t s,
                          rt_scene* out);
 rt_status rt_launch_bake(const rt_scene* sc, const rt_sdf* sdf, int32_t method, cudaStream_t s);
+rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s);
 void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, const rt_split_params* p);

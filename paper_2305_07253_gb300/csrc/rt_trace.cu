@@ -1,24 +1,30 @@
-// Trace kernel: one query (Eq. 1) per thread, split into the sub-intervals of
-// Eq. 2 and processed by the ordering rule of Section 2 (closest hit: in
-// order, stop at the first sub-interval that hits; any hit: the distance
-// field sub-interval first).  Modes 0 and 3 are the pure techniques.
+// Trace kernels.  A query (Eq. 1) is split into the sub-intervals of Eq. 2 and
+// processed by the ordering rule of Section 2: a closest-hit query runs its
+// sub-intervals in order and stops at the first that hits; an any-hit query
+// runs the distance-field sub-interval first.
+//
+// Two implementations with identical results:
+//   * wavefront (default): one persistent kernel per sub-interval kind
+//     (triangles near, field, triangles far).  Each lane holds one query and
+//     takes a new one from a global counter as soon as its own is finished
+//     (per-lane refill), so no lane idles while the slowest query of its warp
+//     finishes.  Queries that miss a sub-interval are appended to the queue of
+//     the next kind: rays that switch tracer mid-query are regrouped across
+//     the whole batch instead of diverging inside a warp.
+//   * simple: one thread per query runs all of its sub-intervals.
+#include <mutex>
+
 #include "rt_trace_dev.cuh"
 
 using namespace rtdev;
 
 namespace {
 
-constexpr int kTraceBlock = 128;
+constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ void store_hit(rt_hit* out, float t, int32_t prim, float u, float v, int32_t tracer,
-                                          uint32_t flags)
-{
-    float2* p = reinterpret_cast<float2*>(out);
-    p[0] = make_float2(t, __int_as_float(prim));
-    p[1] = make_float2(u, v);
-    p[2] = make_float2(__int_as_float(tracer), __uint_as_float(flags));
-}
-
+// ---------------------------------------------------------------------------
+// simple kernel: one thread per query
+// ---------------------------------------------------------------------------
 template <bool COUNT>
 __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts& cnt)
 {
@@ -28,11 +34,8 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
     Hit h = {__int_as_float(0x7f800000), -1, 0.f, 0.f};
     uint32_t flags = 0;
     int32_t tracer = RT_TRACER_MISS;
-    // Eq. 1 is defined for real o, d and t_min <= t_max; anything else has no intersection
-    const bool valid = !(isnan(o.x) || isnan(o.y) || isnan(o.z) || isnan(d.x) || isnan(d.y) || isnan(d.z)) &&
-                       (tmin <= tmax);
 
-    if (!valid) {
+    if (!valid_query(o, d, tmin, tmax)) {
     } else if (a.mode == RT_MODE_BVH) {
         if (bvh_segment<COUNT>(a, o, d, tmin, tmax, a.any_hit, h, flags, cnt)) tracer = RT_TRACER_BVH;
     } else if (a.mode == RT_MODE_SDF) {
@@ -44,7 +47,6 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
     } else {
         const Split s = make_split(a, tmin, tmax);
         if (a.any_hit) {
-            // distance field first, then the triangle sub-intervals (Section 2)
             if (s.field) {
                 March m = sdf_march<COUNT>(a, o, d, s.t1, s.t2, flags, cnt);
                 if (m.hit) {
@@ -57,7 +59,6 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
             if (tracer == RT_TRACER_MISS && s.far_bvh && bvh_segment<COUNT>(a, o, d, s.t2, tmax, true, h, flags, cnt))
                 tracer = RT_TRACER_BVH;
         } else {
-            // closest hit: in order, early exit (Section 2)
             if (s.near_bvh && bvh_segment<COUNT>(a, o, d, tmin, s.t1, false, h, flags, cnt)) tracer = RT_TRACER_BVH;
             if (tracer == RT_TRACER_MISS && s.field) {
                 March m = sdf_march<COUNT>(a, o, d, s.t1, s.t2, flags, cnt);
@@ -77,28 +78,376 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
     store_hit(a.hits + i, h.t, h.prim, h.u, h.v, tracer, flags);
 }
 
+__device__ __forceinline__ void flush_counts(const TraceArgs& a, const Counts& cnt)
+{
+    if (cnt.nodes) atomicAdd(&a.counters[0], (unsigned long long)cnt.nodes);
+    if (cnt.tris) atomicAdd(&a.counters[1], (unsigned long long)cnt.tris);
+    if (cnt.steps) atomicAdd(&a.counters[2], (unsigned long long)cnt.steps);
+    if (cnt.field) atomicAdd(&a.counters[3], (unsigned long long)cnt.field);
+}
+
 template <bool COUNT>
-__global__ void __launch_bounds__(kTraceBlock) k_trace(const TraceArgs a)
+__global__ void k_trace(const TraceArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     Counts cnt = {0, 0, 0, 0};
     if (i < a.n) trace_one<COUNT>(a, i, cnt);
-    if (COUNT) {
-        if (cnt.nodes) atomicAdd(&a.counters[0], (unsigned long long)cnt.nodes);
-        if (cnt.tris) atomicAdd(&a.counters[1], (unsigned long long)cnt.tris);
-        if (cnt.steps) atomicAdd(&a.counters[2], (unsigned long long)cnt.steps);
-        if (cnt.field) atomicAdd(&a.counters[3], (unsigned long long)cnt.field);
+    if (COUNT) flush_counts(a, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// wavefront stage kernels
+// ---------------------------------------------------------------------------
+enum StageKind { ST_BVH_FULL = 0, ST_BVH_NEAR = 1, ST_BVH_FAR = 2, ST_FIELD_FULL = 3, ST_FIELD_SPLIT = 4 };
+
+struct StageArgs {
+    int32_t kind;
+    int32_t first;             // input = every query 0..n-1 (validity is checked here)
+    const int2* in_items;      // (query, flags) appended by the previous stage
+    const unsigned* in_count;
+    int2* out_items;           // null: last stage, a miss is final
+    unsigned* out_count;
+    unsigned* fetch;           // work counter of this stage
+    int32_t refill_min;
+};
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Load a query and the bounds of this stage's sub-interval.  Returns false
+// when the sub-interval is not part of the query (or the query is invalid).
+__device__ __forceinline__ bool stage_segment(const TraceArgs& a, int kind, int64_t q, float3& o, float3& d,
+                                              float& ta, float& tb, bool& invalid)
+{
+    const float4 r0 = __ldg(a.rays + 2 * q), r1 = __ldg(a.rays + 2 * q + 1);
+    o = make_float3(r0.x, r0.y, r0.z);
+    d = make_float3(r1.x, r1.y, r1.z);
+    const float tmin = r0.w, tmax = r1.w;
+    invalid = !valid_query(o, d, tmin, tmax);
+    if (invalid) return false;
+    if (kind == ST_BVH_FULL || kind == ST_FIELD_FULL) {
+        ta = tmin;
+        tb = tmax;
+        return true;
     }
+    const Split s = make_split(a, tmin, tmax);
+    if (kind == ST_BVH_NEAR) { ta = tmin; tb = s.t1; return s.near_bvh; }
+    if (kind == ST_BVH_FAR) { ta = s.t2; tb = tmax; return s.far_bvh; }
+    ta = s.t1;
+    tb = s.t2;
+    return s.field;
+}
+
+// Append the lanes with `fwd` set to the next stage's queue (one atomic per warp).
+__device__ __forceinline__ void forward(const StageArgs& st, bool fwd, int query, uint32_t flags)
+{
+    const unsigned m = __ballot_sync(kFull, fwd);
+    if (m == 0) return;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane_id() == (unsigned)leader) base = atomicAdd(st.out_count, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (fwd) st.out_items[base + __popc(m & ((1u << lane_id()) - 1u))] = make_int2(query, (int)flags);
+}
+
+// Take new queries for the idle lanes when enough of them are idle (or all are).
+// Sets `got` for the lanes that received query `slot`.
+__device__ __forceinline__ void refill(const StageArgs& st, unsigned n_in, bool idle, bool& drained, bool& got,
+                                       unsigned& slot)
+{
+    got = false;
+    const unsigned want = __ballot_sync(kFull, idle && !drained);
+    const unsigned busy = __ballot_sync(kFull, !idle);
+    if (want == 0 || (__popc(want) < st.refill_min && busy != 0)) return;
+    const int leader = __ffs(want) - 1;
+    unsigned base = 0;
+    if (lane_id() == (unsigned)leader) base = atomicAdd(st.fetch, (unsigned)__popc(want));
+    base = __shfl_sync(kFull, base, leader);
+    if (idle && !drained) {
+        const unsigned k = base + __popc(want & ((1u << lane_id()) - 1u));
+        if (k < n_in) {
+            got = true;
+            slot = k;
+        } else {
+            drained = true;
+        }
+    }
+}
+
+template <bool COUNT>
+__global__ void k_stage_bvh(const TraceArgs a, const StageArgs st)
+{
+    const unsigned n_in = st.first ? (unsigned)a.n : *st.in_count;
+    const bool any_hit = a.any_hit != 0;
+    int stack[RT_STACK_DEPTH];
+    Counts cnt = {0, 0, 0, 0};
+    bool drained = false, live = false;
+    int query = -1;
+    uint32_t flags = 0;
+    BvhRay r;
+    Trav s;
+    Hit best;
+    for (;;) {
+        bool got;
+        unsigned slot = 0;
+        refill(st, n_in, !live, drained, got, slot);
+        bool done = false, found = false, final_miss = false;
+        if (got) {
+            int2 item = st.first ? make_int2((int)slot, 0) : st.in_items[slot];
+            query = item.x;
+            flags = (uint32_t)item.y;
+            float3 o, d;
+            float ta, tb;
+            bool invalid;
+            bool active = stage_segment(a, st.kind, query, o, d, ta, tb, invalid);
+            if (active && ta <= tb && a.root != INT32_MIN) {
+                r = bvh_ray(o, d);
+                s = trav_begin(a.root, ta, tb);
+                best.prim = -1;
+                live = true;
+            } else {
+                done = true;
+                final_miss = invalid;
+            }
+        } else if (live) {
+            if (trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt)) {
+                done = true;
+                found = s.found;
+                live = false;
+            }
+        }
+        const bool fwd = done && !found && !final_miss && st.out_items != nullptr;
+        forward(st, fwd, query, flags);
+        if (done && !fwd) {
+            if (found) store_hit(a.hits + query, best.t, best.prim, best.u, best.v, RT_TRACER_BVH, flags);
+            else store_hit(a.hits + query, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
+        }
+        if (__ballot_sync(kFull, live || (!drained)) == 0) break;
+    }
+    if (COUNT) flush_counts(a, cnt);
+}
+
+template <bool COUNT>
+__global__ void k_stage_field(const TraceArgs a, const StageArgs st)
+{
+    const unsigned n_in = st.first ? (unsigned)a.n : *st.in_count;
+    Counts cnt = {0, 0, 0, 0};
+    bool drained = false, live = false;
+    int query = -1;
+    uint32_t flags = 0;
+    float3 o = make_float3(0.f, 0.f, 0.f), d = o;
+    float t = 0.f, tb = 0.f, t_prev = 0.f;
+    int k = 0;
+    for (;;) {
+        bool got;
+        unsigned slot = 0;
+        refill(st, n_in, !live, drained, got, slot);
+        bool done = false, found = false, final_miss = false;
+        if (got) {
+            int2 item = st.first ? make_int2((int)slot, 0) : st.in_items[slot];
+            query = item.x;
+            flags = (uint32_t)item.y;
+            float ta;
+            bool invalid;
+            bool active = stage_segment(a, st.kind, query, o, d, ta, tb, invalid);
+            if (active && clip_grid(a, o, d, ta, tb)) {
+                if (COUNT) ++cnt.field;
+                t = ta;
+                t_prev = __int_as_float(0x7fc00000);
+                k = 0;
+                live = true;
+            } else {
+                done = true;
+                final_miss = invalid;
+            }
+        } else if (live) {
+            if (COUNT) ++cnt.steps;
+            const int res = march_step(a, o, d, t, tb, t_prev);
+            ++k;
+            if (res == 1) {
+                done = true;
+                found = true;
+            } else if (res == 2) {
+                done = true;
+            } else if (k >= a.max_steps) {
+                flags |= RT_FLAG_STEP_LIMIT;
+                done = true;
+            }
+            if (done) live = false;
+        }
+        const bool fwd = done && !found && !final_miss && st.out_items != nullptr;
+        forward(st, fwd, query, flags);
+        if (done && !fwd) {
+            if (found) {
+                const float th = (a.refine_root && !isnan(t_prev)) ? refine(a, o, d, t_prev, t) : t;
+                store_hit(a.hits + query, th, -1, 0.f, 0.f, RT_TRACER_SDF, flags);
+            } else {
+                store_hit(a.hits + query, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
+            }
+        }
+        if (__ballot_sync(kFull, live || (!drained)) == 0) break;
+    }
+    if (COUNT) flush_counts(a, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct DeviceInfo {
+    int sms = 0;
+    cudaMemPool_t pool = nullptr;
+};
+
+std::mutex g_mu;
+DeviceInfo g_dev[64];
+
+rt_status device_info(DeviceInfo*& out)
+{
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return rt_fail(RT_ERR_INVALID_ARG, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceInfo& d = g_dev[dev];
+    if (d.sms == 0) {
+        RT_CUDA_TRY(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        RT_CUDA_TRY(cudaMemPoolCreate(&d.pool, &props));
+        // keep freed scratch in the pool between calls instead of returning it
+        uint64_t keep = ~0ull;
+        RT_CUDA_TRY(cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    out = &d;
+    return RT_OK;
+}
+
+template <class K>
+int persistent_blocks(K kernel, int block, const rt_tuning& tu, int sms)
+{
+    int per_sm = tu.blocks_per_sm;
+    if (per_sm <= 0) {
+        int fit = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, block, 0) != cudaSuccess || fit < 1) fit = 1;
+        per_sm = fit;
+    }
+    return sms * per_sm;
+}
+
+template <bool COUNT>
+rt_status launch_stage(const TraceArgs& a, const StageArgs& st, const rt_tuning& tu, int sms, cudaStream_t s)
+{
+    const bool field = st.kind == ST_FIELD_FULL || st.kind == ST_FIELD_SPLIT;
+    if (field) {
+        int blocks = persistent_blocks(k_stage_field<COUNT>, tu.block, tu, sms);
+        k_stage_field<COUNT><<<blocks, tu.block, 0, s>>>(a, st);
+    } else {
+        int blocks = persistent_blocks(k_stage_bvh<COUNT>, tu.block, tu, sms);
+        k_stage_bvh<COUNT><<<blocks, tu.block, 0, s>>>(a, st);
+    }
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+// the sub-interval kinds of a query, in the order Section 2 processes them
+int stage_program(const TraceArgs& a, int kinds[3])
+{
+    switch (a.mode) {
+    case RT_MODE_BVH: kinds[0] = ST_BVH_FULL; return 1;
+    case RT_MODE_SDF: kinds[0] = ST_FIELD_FULL; return 1;
+    case RT_MODE_SPLIT1:
+        if (a.any_hit) { kinds[0] = ST_FIELD_SPLIT; kinds[1] = ST_BVH_NEAR; }
+        else { kinds[0] = ST_BVH_NEAR; kinds[1] = ST_FIELD_SPLIT; }
+        return 2;
+    default:
+        if (a.any_hit) { kinds[0] = ST_FIELD_SPLIT; kinds[1] = ST_BVH_NEAR; }
+        else { kinds[0] = ST_BVH_NEAR; kinds[1] = ST_FIELD_SPLIT; }
+        kinds[2] = ST_BVH_FAR;
+        return 3;
+    }
+}
+
+int32_t public_kind(int k)
+{
+    switch (k) {
+    case ST_BVH_FULL: return RT_STAGE_BVH_FULL;
+    case ST_BVH_NEAR: return RT_STAGE_BVH_NEAR;
+    case ST_BVH_FAR: return RT_STAGE_BVH_FAR;
+    case ST_FIELD_FULL: return RT_STAGE_FIELD_FULL;
+    default: return RT_STAGE_FIELD_SPLIT;
+    }
+}
+
+template <bool COUNT>
+rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s, StageTiming* timing)
+{
+    DeviceInfo* dev = nullptr;
+    rt_status st = device_info(dev);
+    if (st != RT_OK) return st;
+    if (a.n > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "at most 2^31-1 queries per call");
+    int kinds[3];
+    const int n_st = stage_program(a, kinds);
+    // scratch: counters (fetch x3, queue sizes x2) and two ping-pong queues
+    const size_t counters_bytes = 256;
+    const size_t queue_bytes = n_st > 1 ? (size_t)a.n * sizeof(int2) : 0;
+    const size_t total = counters_bytes + (n_st > 1 ? queue_bytes : 0) + (n_st > 2 ? queue_bytes : 0);
+    void* scratch = nullptr;
+    RT_CUDA_TRY(cudaMallocFromPoolAsync(&scratch, total, dev->pool, s));
+    unsigned* ctr = static_cast<unsigned*>(scratch);
+    int2* q[2] = {reinterpret_cast<int2*>(static_cast<char*>(scratch) + counters_bytes),
+                  reinterpret_cast<int2*>(static_cast<char*>(scratch) + counters_bytes + queue_bytes)};
+    rt_status rs = RT_OK;
+    cudaError_t e = cudaMemsetAsync(ctr, 0, counters_bytes, s);
+    if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaMemsetAsync");
+    for (int k = 0; k < n_st && rs == RT_OK; ++k) {
+        StageArgs sa;
+        sa.kind = kinds[k];
+        sa.first = k == 0;
+        sa.in_items = k > 0 ? q[(k - 1) & 1] : nullptr;
+        sa.in_count = k > 0 ? &ctr[3 + ((k - 1) & 1)] : nullptr;
+        sa.out_items = k + 1 < n_st ? q[k & 1] : nullptr;
+        sa.out_count = k + 1 < n_st ? &ctr[3 + (k & 1)] : nullptr;
+        sa.fetch = &ctr[k];
+        sa.refill_min = tu.refill_min;
+        if (timing) {
+            e = cudaEventRecord(timing->events[k], s);
+            if (e != cudaSuccess) { rs = rt_cuda_fail(e, "cudaEventRecord"); break; }
+            timing->kinds[k] = public_kind(kinds[k]);
+        }
+        rs = launch_stage<COUNT>(a, sa, tu, dev->sms, s);
+    }
+    if (timing && rs == RT_OK) {
+        e = cudaEventRecord(timing->events[n_st], s);
+        if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaEventRecord");
+        timing->n_launches = n_st;
+    }
+    e = cudaFreeAsync(scratch, s);
+    if (rs == RT_OK && e != cudaSuccess) rs = rt_cuda_fail(e, "cudaFreeAsync");
+    return rs;
 }
 
 }  // namespace
 
-rt_status rt_launch_trace(const TraceArgs& a, bool counted, cudaStream_t s)
+rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, StageTiming* timing)
 {
-    const int64_t blocks = (a.n + kTraceBlock - 1) / kTraceBlock;
+    const rt_tuning& tu = rt_current_tuning();
+    TraceArgs a = a0;
+    if (tu.grid_layout == RT_LAYOUT_PLAIN) a.cells = nullptr;
+    if (tu.kernel == RT_KERNEL_WAVEFRONT)
+        return counted ? run_wavefront<true>(a, tu, s, timing) : run_wavefront<false>(a, tu, s, timing);
+    const int64_t blocks = (a.n + tu.block - 1) / tu.block;
     if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "too many rays");
-    if (counted) k_trace<true><<<(unsigned)blocks, kTraceBlock, 0, s>>>(a);
-    else k_trace<false><<<(unsigned)blocks, kTraceBlock, 0, s>>>(a);
+    if (timing) {
+        RT_CUDA_TRY(cudaEventRecord(timing->events[0], s));
+        timing->kinds[0] = RT_STAGE_ALL;
+    }
+    if (counted) k_trace<true><<<(unsigned)blocks, tu.block, 0, s>>>(a);
+    else k_trace<false><<<(unsigned)blocks, tu.block, 0, s>>>(a);
     RT_CUDA_TRY(cudaGetLastError());
+    if (timing) {
+        RT_CUDA_TRY(cudaEventRecord(timing->events[1], s));
+        timing->n_launches = 1;
+    }
     return RT_OK;
 }

@@ -22,6 +22,14 @@ __device__ __forceinline__ float sel3(float x, float y, float z, int k) { return
 
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 
+// 32-byte read-only vector load (sm_100 family); p must be 32-byte aligned
+__device__ __forceinline__ void ldg8(const void* p, float v[8])
+{
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p));
+}
+
 // ---------------------------------------------------------------------------
 // Triangle segment: closest (or any) hit on [ta, tb] through the BVH, with
 // the watertight ray/triangle test of Woop, Benthin & Wald (JCGT 2013) in
@@ -30,17 +38,22 @@ __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 // evaluate that edge to exactly opposite values and no ray slips between
 // them.  Ties in t go to the smaller triangle index.
 // ---------------------------------------------------------------------------
-template <bool COUNT>
-__device__ __forceinline__ bool bvh_segment(const TraceArgs& a, float3 o, float3 d, float ta, float tb, bool any_hit,
-                                            Hit& best, uint32_t& flags, Counts& cnt)
+struct BvhRay {
+    float3 o, idir, ood;
+    float Sx, Sy, Sz;
+    int kx, ky, kz;
+};
+
+__device__ __forceinline__ BvhRay bvh_ray(float3 o, float3 d)
 {
-    if (a.root == INT32_MIN || !(ta <= tb)) return false;
+    BvhRay r;
+    r.o = o;
     // safe reciprocal: components below 2^-80 behave like 2^-80 (slabs stay finite)
     const float eps = 8.27180613e-25f;
-    float3 idir = make_float3(1.0f / (fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
-                              1.0f / (fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
-                              1.0f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
-    float3 ood = make_float3(o.x * idir.x, o.y * idir.y, o.z * idir.z);
+    r.idir = make_float3(1.0f / (fabsf(d.x) > eps ? d.x : copysignf(eps, d.x)),
+                         1.0f / (fabsf(d.y) > eps ? d.y : copysignf(eps, d.y)),
+                         1.0f / (fabsf(d.z) > eps ? d.z : copysignf(eps, d.z)));
+    r.ood = make_float3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
     // watertight set-up: dominant axis kz, shear constants
     int kz = 0;
     float az = fabsf(d.x);
@@ -50,84 +63,152 @@ __device__ __forceinline__ bool bvh_segment(const TraceArgs& a, float3 o, float3
     int ky = kx == 2 ? 0 : kx + 1;
     float dkz = sel3(d.x, d.y, d.z, kz);
     if (dkz < 0.f) { int s = kx; kx = ky; ky = s; }
-    const float Sx = __fdiv_rn(sel3(d.x, d.y, d.z, kx), dkz);
-    const float Sy = __fdiv_rn(sel3(d.x, d.y, d.z, ky), dkz);
-    const float Sz = __frcp_rn(dkz);
+    r.Sx = __fdiv_rn(sel3(d.x, d.y, d.z, kx), dkz);
+    r.Sy = __fdiv_rn(sel3(d.x, d.y, d.z, ky), dkz);
+    r.Sz = __frcp_rn(dkz);
+    r.kx = kx;
+    r.ky = ky;
+    r.kz = kz;
+    return r;
+}
 
-    int stack[RT_STACK_DEPTH];
-    int sp = 0;
-    int node = a.root;
-    float tbest = tb;
-    bool found = false;
-    // a tree visit never exceeds 2n-1 nodes; the guard only stops a corrupt structure
-    for (uint32_t guard = 0;; ++guard) {
-        if (guard > (1u << 26)) {
-            flags |= RT_FLAG_ITER_LIMIT;
-            break;
-        }
-        if (node >= 0) {
-            const float4* np = reinterpret_cast<const float4*>(a.nodes + node);
-            float4 na = ldg4(np), nb = ldg4(np + 1), nc = ldg4(np + 2);
-            int4 nd = __ldg(reinterpret_cast<const int4*>(np + 3));
-            if (COUNT) ++cnt.nodes;
-            float x0 = fmaf(na.x, idir.x, -ood.x), x1 = fmaf(na.y, idir.x, -ood.x);
-            float y0 = fmaf(na.z, idir.y, -ood.y), y1 = fmaf(na.w, idir.y, -ood.y);
-            float z0 = fmaf(nc.x, idir.z, -ood.z), z1 = fmaf(nc.y, idir.z, -ood.z);
-            float tn0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), ta));
-            float tf0 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tbest));
-            x0 = fmaf(nb.x, idir.x, -ood.x); x1 = fmaf(nb.y, idir.x, -ood.x);
-            y0 = fmaf(nb.z, idir.y, -ood.y); y1 = fmaf(nb.w, idir.y, -ood.y);
-            z0 = fmaf(nc.z, idir.z, -ood.z); z1 = fmaf(nc.w, idir.z, -ood.z);
-            float tn1 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), ta));
-            float tf1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tbest));
-            bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
-            if (h0 && h1) {
-                int nearc = nd.x, farc = nd.y;
-                if (tn1 < tn0) { nearc = nd.y; farc = nd.x; }
-                if (sp < RT_STACK_DEPTH) stack[sp++] = farc;
-                else flags |= RT_FLAG_STACK_OVERFLOW;
-                node = nearc;
-                continue;
-            }
-            if (h0) { node = nd.x; continue; }
-            if (h1) { node = nd.y; continue; }
-        } else {
-            const int tri = ~node;
-            if (COUNT) ++cnt.tris;
-            const float4* tp = a.tris + 3 * (int64_t)tri;
-            float4 v0 = ldg4(tp), v1 = ldg4(tp + 1), v2 = ldg4(tp + 2);
-            float A0 = v0.x - o.x, A1 = v0.y - o.y, A2 = v0.z - o.z;
-            float B0 = v1.x - o.x, B1 = v1.y - o.y, B2 = v1.z - o.z;
-            float C0 = v2.x - o.x, C1 = v2.y - o.y, C2 = v2.z - o.z;
-            float Akz = sel3(A0, A1, A2, kz), Bkz = sel3(B0, B1, B2, kz), Ckz = sel3(C0, C1, C2, kz);
-            float Ax = __fmaf_rn(-Sx, Akz, sel3(A0, A1, A2, kx)), Ay = __fmaf_rn(-Sy, Akz, sel3(A0, A1, A2, ky));
-            float Bx = __fmaf_rn(-Sx, Bkz, sel3(B0, B1, B2, kx)), By = __fmaf_rn(-Sy, Bkz, sel3(B0, B1, B2, ky));
-            float Cx = __fmaf_rn(-Sx, Ckz, sel3(C0, C1, C2, kx)), Cy = __fmaf_rn(-Sy, Ckz, sel3(C0, C1, C2, ky));
-            float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
-            float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
-            float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
-            bool inside = !((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f));
-            float det = U + V + W;
-            if (inside && det != 0.f) {
-                float T = fmaf(U, Sz * Akz, fmaf(V, Sz * Bkz, W * (Sz * Ckz)));
-                float t = __fdiv_rn(T, det);
-                int prim = __float_as_int(v0.w);
-                if (t >= ta && t <= tbest && (!found || t < tbest || prim < best.prim)) {
-                    float rd = __frcp_rn(det);
-                    tbest = t;
-                    best.t = t;
-                    best.prim = prim;
-                    best.u = V * rd;
-                    best.v = W * rd;
-                    found = true;
-                    if (any_hit) break;
-                }
-            }
-        }
-        if (sp == 0) break;
-        node = stack[--sp];
+// Slab tests of both children of one node against [ta, tf]; 64-byte node read
+// as two 32-byte vectors.
+struct NodeHit {
+    int nearc, farc;
+    bool h0, h1;
+};
+
+__device__ __forceinline__ NodeHit visit_node(const BNode* nodes, int node, const BvhRay& r, float ta, float tf)
+{
+    float v[8], w[8];
+    const float* np = reinterpret_cast<const float*>(nodes + node);
+    ldg8(np, v);
+    ldg8(np + 8, w);
+    // v = a (c0 x/y), b (c1 x/y); w = c (z of both), d (children)
+    float x0 = fmaf(v[0], r.idir.x, -r.ood.x), x1 = fmaf(v[1], r.idir.x, -r.ood.x);
+    float y0 = fmaf(v[2], r.idir.y, -r.ood.y), y1 = fmaf(v[3], r.idir.y, -r.ood.y);
+    float z0 = fmaf(w[0], r.idir.z, -r.ood.z), z1 = fmaf(w[1], r.idir.z, -r.ood.z);
+    float tn0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), ta));
+    float tf0 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tf));
+    x0 = fmaf(v[4], r.idir.x, -r.ood.x); x1 = fmaf(v[5], r.idir.x, -r.ood.x);
+    y0 = fmaf(v[6], r.idir.y, -r.ood.y); y1 = fmaf(v[7], r.idir.y, -r.ood.y);
+    z0 = fmaf(w[2], r.idir.z, -r.ood.z); z1 = fmaf(w[3], r.idir.z, -r.ood.z);
+    float tn1 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), ta));
+    float tf1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tf));
+    NodeHit h;
+    h.h0 = tn0 <= tf0;
+    h.h1 = tn1 <= tf1;
+    int c0 = __float_as_int(w[4]), c1 = __float_as_int(w[5]);
+    bool swap = h.h0 && h.h1 && tn1 < tn0;
+    h.nearc = swap ? c1 : c0;
+    h.farc = swap ? c0 : c1;
+    return h;
+}
+
+// Watertight test of triangle `tri` (leaf order); on acceptance updates best/tbest.
+__device__ __forceinline__ bool test_triangle(const float4* tris, int tri, const BvhRay& r, float ta, float& tbest,
+                                              bool found, Hit& best)
+{
+    const float4* tp = tris + 3 * (int64_t)tri;
+    float4 v0 = ldg4(tp), v1 = ldg4(tp + 1), v2 = ldg4(tp + 2);
+    const float3 o = r.o;
+    float A0 = v0.x - o.x, A1 = v0.y - o.y, A2 = v0.z - o.z;
+    float B0 = v1.x - o.x, B1 = v1.y - o.y, B2 = v1.z - o.z;
+    float C0 = v2.x - o.x, C1 = v2.y - o.y, C2 = v2.z - o.z;
+    const int kx = r.kx, ky = r.ky, kz = r.kz;
+    float Akz = sel3(A0, A1, A2, kz), Bkz = sel3(B0, B1, B2, kz), Ckz = sel3(C0, C1, C2, kz);
+    float Ax = __fmaf_rn(-r.Sx, Akz, sel3(A0, A1, A2, kx)), Ay = __fmaf_rn(-r.Sy, Akz, sel3(A0, A1, A2, ky));
+    float Bx = __fmaf_rn(-r.Sx, Bkz, sel3(B0, B1, B2, kx)), By = __fmaf_rn(-r.Sy, Bkz, sel3(B0, B1, B2, ky));
+    float Cx = __fmaf_rn(-r.Sx, Ckz, sel3(C0, C1, C2, kx)), Cy = __fmaf_rn(-r.Sy, Ckz, sel3(C0, C1, C2, ky));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    bool inside = !((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f));
+    float det = U + V + W;
+    if (!inside || det == 0.f) return false;
+    float T = fmaf(U, r.Sz * Akz, fmaf(V, r.Sz * Bkz, W * (r.Sz * Ckz)));
+    float t = __fdiv_rn(T, det);
+    int prim = __float_as_int(v0.w);
+    if (t >= ta && t <= tbest && (!found || t < tbest || prim < best.prim)) {
+        float rd = __frcp_rn(det);
+        tbest = t;
+        best.t = t;
+        best.prim = prim;
+        best.u = V * rd;
+        best.v = W * rd;
+        return true;
     }
-    return found;
+    return false;
+}
+
+// Resumable traversal state of one segment.
+struct Trav {
+    int node;
+    int sp;
+    float ta, tbest;
+    bool found;
+    uint32_t guard;
+};
+
+__device__ __forceinline__ Trav trav_begin(int root, float ta, float tb)
+{
+    Trav s;
+    s.node = root;
+    s.sp = 0;
+    s.ta = ta;
+    s.tbest = tb;
+    s.found = false;
+    s.guard = 0;
+    return s;
+}
+
+// One trip of the while-while loop: descend through internal nodes to the next
+// leaf, test it, and pop the next subtree.  Returns true when the segment is done.
+template <bool COUNT>
+__device__ __forceinline__ bool trav_trip(const TraceArgs& a, const BvhRay& r, Trav& s, int* stack, bool any_hit,
+                                          Hit& best, uint32_t& flags, Counts& cnt)
+{
+    while (s.node >= 0) {
+        if (++s.guard > (1u << 26)) {  // a tree visit is bounded by 2n-1 nodes; stops only a corrupt structure
+            flags |= RT_FLAG_ITER_LIMIT;
+            return true;
+        }
+        if (COUNT) ++cnt.nodes;
+        NodeHit h = visit_node(a.nodes, s.node, r, s.ta, s.tbest);
+        if (h.h0 && h.h1) {
+            if (s.sp < RT_STACK_DEPTH) stack[s.sp++] = h.farc;
+            else flags |= RT_FLAG_STACK_OVERFLOW;
+            s.node = h.nearc;
+        } else if (h.h0 || h.h1) {
+            s.node = h.h0 ? h.nearc : h.farc;
+        } else {
+            if (s.sp == 0) return true;
+            s.node = stack[--s.sp];
+        }
+    }
+    if (COUNT) ++cnt.tris;
+    if (test_triangle(a.tris, ~s.node, r, s.ta, s.tbest, s.found, best)) {
+        s.found = true;
+        if (any_hit) return true;
+    }
+    if (s.sp == 0) return true;
+    s.node = stack[--s.sp];
+    return false;
+}
+
+// Whole triangle segment in one call (used by the one-thread-per-query kernel).
+template <bool COUNT>
+__device__ __forceinline__ bool bvh_segment(const TraceArgs& a, float3 o, float3 d, float ta, float tb, bool any_hit,
+                                            Hit& best, uint32_t& flags, Counts& cnt)
+{
+    if (a.root == INT32_MIN || !(ta <= tb)) return false;
+    const BvhRay r = bvh_ray(o, d);
+    int stack[RT_STACK_DEPTH];
+    Trav s = trav_begin(a.root, ta, tb);
+    while (!trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt)) {
+    }
+    return s.found;
 }
 
 // ---------------------------------------------------------------------------
@@ -147,7 +228,7 @@ __device__ __forceinline__ float grid_at(const TraceArgs& a, int64_t i)
 }
 
 struct Cell {
-    int64_t base;
+    int i0[3];
     float f[3];
     bool clamped[3];
 };
@@ -165,11 +246,50 @@ __device__ __forceinline__ Cell locate(const TraceArgs& a, float px, float py, f
         int ii = (int)floorf(u);
         if (ii > a.gn[k] - 2) ii = a.gn[k] - 2;
         c.f[k] = __fsub_rn(u, (float)ii);
-        if (k == 0) c.base = ii;
-        else if (k == 1) c.base += (int64_t)a.gn[0] * ii;
-        else c.base += (int64_t)a.gn[0] * a.gn[1] * ii;
+        c.i0[k] = ii;
     }
     return c;
+}
+
+__device__ __forceinline__ int64_t grid_base(const TraceArgs& a, const Cell& c)
+{
+    return c.i0[0] + (int64_t)a.gn[0] * (c.i0[1] + (int64_t)a.gn[1] * c.i0[2]);
+}
+
+__device__ __forceinline__ int64_t cell_index(const TraceArgs& a, const Cell& c)
+{
+    return c.i0[0] + (int64_t)(a.gn[0] - 1) * (c.i0[1] + (int64_t)(a.gn[1] - 1) * c.i0[2]);
+}
+
+// the 8 corner values of the cell, order v000 v100 v010 v110 v001 v101 v011 v111
+__device__ __forceinline__ void corners(const TraceArgs& a, const Cell& c, float v[8])
+{
+    if (a.cells) {
+        const int64_t ci = cell_index(a, c);
+        if (a.grid_f16) {
+            uint4 q = __ldg(reinterpret_cast<const uint4*>(a.cells) + ci);
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                __half2 h2 = *reinterpret_cast<const __half2*>(&w[k]);
+                v[2 * k] = __low2float(h2);
+                v[2 * k + 1] = __high2float(h2);
+            }
+        } else {
+            ldg8(reinterpret_cast<const float*>(a.cells) + 8 * ci, v);
+        }
+        return;
+    }
+    const int64_t b = grid_base(a, c);
+    const int64_t sy = a.gn[0], sz = (int64_t)a.gn[0] * a.gn[1];
+    v[0] = grid_at(a, b);
+    v[1] = grid_at(a, b + 1);
+    v[2] = grid_at(a, b + sy);
+    v[3] = grid_at(a, b + sy + 1);
+    v[4] = grid_at(a, b + sz);
+    v[5] = grid_at(a, b + sz + 1);
+    v[6] = grid_at(a, b + sz + sy);
+    v[7] = grid_at(a, b + sz + sy + 1);
 }
 
 __device__ __forceinline__ float lerp_rn(float f, float x, float y) { return __fmaf_rn(f, __fsub_rn(y, x), x); }
@@ -177,15 +297,12 @@ __device__ __forceinline__ float lerp_rn(float f, float x, float y) { return __f
 __device__ __forceinline__ float trilinear(const TraceArgs& a, float px, float py, float pz)
 {
     Cell c = locate(a, px, py, pz);
-    const int64_t sy = a.gn[0], sz = (int64_t)a.gn[0] * a.gn[1];
-    float v000 = grid_at(a, c.base), v100 = grid_at(a, c.base + 1);
-    float v010 = grid_at(a, c.base + sy), v110 = grid_at(a, c.base + sy + 1);
-    float v001 = grid_at(a, c.base + sz), v101 = grid_at(a, c.base + sz + 1);
-    float v011 = grid_at(a, c.base + sz + sy), v111 = grid_at(a, c.base + sz + sy + 1);
-    float c00 = lerp_rn(c.f[0], v000, v100);
-    float c10 = lerp_rn(c.f[0], v010, v110);
-    float c01 = lerp_rn(c.f[0], v001, v101);
-    float c11 = lerp_rn(c.f[0], v011, v111);
+    float v[8];
+    corners(a, c, v);
+    float c00 = lerp_rn(c.f[0], v[0], v[1]);
+    float c10 = lerp_rn(c.f[0], v[2], v[3]);
+    float c01 = lerp_rn(c.f[0], v[4], v[5]);
+    float c11 = lerp_rn(c.f[0], v[6], v[7]);
     float c0 = lerp_rn(c.f[1], c00, c10);
     float c1 = lerp_rn(c.f[1], c01, c11);
     return lerp_rn(c.f[2], c0, c1);
@@ -216,6 +333,17 @@ struct March {
     float t, t_prev;
 };
 
+// One march step at t; returns 0 to continue, 1 on a hit, 2 on leaving [.., tb].
+__device__ __forceinline__ int march_step(const TraceArgs& a, float3 o, float3 d, float& t, float tb, float& t_prev)
+{
+    float px = __fmaf_rn(t, d.x, o.x), py = __fmaf_rn(t, d.y, o.y), pz = __fmaf_rn(t, d.z, o.z);
+    float phi = trilinear(a, px, py, pz);
+    if (phi < a.eps_hit) return 1;
+    t_prev = t;
+    t = __fadd_rn(t, fmaxf(phi, a.eps_min));
+    return t > tb ? 2 : 0;
+}
+
 template <bool COUNT>
 __device__ __forceinline__ March sdf_march(const TraceArgs& a, float3 o, float3 d, float ta, float tb,
                                            uint32_t& flags, Counts& cnt)
@@ -225,17 +353,14 @@ __device__ __forceinline__ March sdf_march(const TraceArgs& a, float3 o, float3 
     if (COUNT) ++cnt.field;
     float t = ta;
     for (int k = 0; k < a.max_steps; ++k) {
-        float px = __fmaf_rn(t, d.x, o.x), py = __fmaf_rn(t, d.y, o.y), pz = __fmaf_rn(t, d.z, o.z);
-        float phi = trilinear(a, px, py, pz);
         if (COUNT) ++cnt.steps;
-        if (phi < a.eps_hit) {
+        int r = march_step(a, o, d, t, tb, m.t_prev);
+        if (r == 1) {
             m.hit = true;
             m.t = t;
             return m;
         }
-        m.t_prev = t;
-        t = __fadd_rn(t, fmaxf(phi, a.eps_min));
-        if (t > tb) return m;
+        if (r == 2) return m;
     }
     flags |= RT_FLAG_STEP_LIMIT;
     return m;
@@ -275,6 +400,21 @@ __device__ __forceinline__ Split make_split(const TraceArgs& a, float tmin, floa
         s.far_bvh = a.m_far > 0.f;
     }
     return s;
+}
+
+// Eq. 1 is defined for real o, d and t_min <= t_max; anything else has no intersection
+__device__ __forceinline__ bool valid_query(float3 o, float3 d, float tmin, float tmax)
+{
+    return !(isnan(o.x) || isnan(o.y) || isnan(o.z) || isnan(d.x) || isnan(d.y) || isnan(d.z)) && (tmin <= tmax);
+}
+
+__device__ __forceinline__ void store_hit(rt_hit* out, float t, int32_t prim, float u, float v, int32_t tracer,
+                                          uint32_t flags)
+{
+    float2* p = reinterpret_cast<float2*>(out);
+    p[0] = make_float2(t, __int_as_float(prim));
+    p[1] = make_float2(u, v);
+    p[2] = make_float2(__int_as_float(tracer), __uint_as_float(flags));
 }
 
 }  // namespace rtdev

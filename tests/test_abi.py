@@ -45,6 +45,22 @@ def test_struct_sizes_match_header():
     import paper_2305_07253_gb300 as rq
     assert ctypes.sizeof(rq.rt_split_params) == 32
     assert ctypes.sizeof(rq.rt_scene_info) == 8 * 3 + 4 * 2 + 4 * 6 + 8
+    assert ctypes.sizeof(rq.rt_tuning) == 20
+
+
+def test_tuning_roundtrip_and_validation(rtlib):
+    import paper_2305_07253_gb300 as rq
+    prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE, block=256, refill_min=4)
+    try:
+        t = rq.rt_get_tuning()
+        assert (t.kernel, t.block, t.refill_min) == (rq.KERNEL_SIMPLE, 256, 4)
+        for bad in (dict(block=48), dict(block=0), dict(refill_min=0), dict(refill_min=33), dict(kernel=7),
+                    dict(grid_layout=5), dict(blocks_per_sm=-1)):
+            with pytest.raises(rq.RtError):
+                rq.rt_set_tuning(**bad)
+        assert rq.rt_get_tuning().block == 256  # a rejected call changes nothing
+    finally:
+        rq.rt_set_tuning(prev)
 
 
 def test_argument_errors_without_a_gpu(rtlib):

@@ -48,9 +48,29 @@ class World:
             self.sdf = rq.rt_sdf_create(self.gridt, s.lo, s.hi)
 
 
+TUNINGS = {
+    "wavefront-cells": dict(kernel=0, grid_layout=0),
+    "wavefront-plain": dict(kernel=0, grid_layout=1),
+    "simple-cells": dict(kernel=1, grid_layout=0),
+    "simple-plain": dict(kernel=1, grid_layout=1),
+    "wavefront-refill1-b64": dict(kernel=0, grid_layout=0, refill_min=1, block=64),
+    "wavefront-refill32-b256": dict(kernel=0, grid_layout=0, refill_min=32, block=256, blocks_per_sm=2),
+}
+
+
+@pytest.fixture(params=list(TUNINGS))
+def tuning(request):
+    import paper_2305_07253_gb300 as rq
+    prev = rq.rt_set_tuning(**TUNINGS[request.param])
+    yield request.param
+    rq.rt_set_tuning(prev)
+
+
 @pytest.fixture(scope="module")
 def tiny():
-    return World("tiny", 32, 4096)
+    w = World("tiny", 32, 4096)
+    w.rq.rt_sdf_prepare(w.sdf)
+    return w
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +89,7 @@ def test_scene_build_info(tiny, medium):
 
 @pytest.mark.parametrize("which", ["tiny", "medium"])
 @pytest.mark.parametrize("any_hit", [False, True])
-def test_bvh_parity(which, any_hit, tiny, medium):
+def test_bvh_parity(which, any_hit, tiny, medium, tuning):
     w = tiny if which == "tiny" else medium
     g = gpu_hits_to_numpy(w.rq.rt_trace_bvh(w.scene, w.rays_d, any_hit=any_hit))
     o = w.bvh.trace(w.rays)
@@ -124,7 +144,7 @@ def test_bake_parity_medium_sampled(medium):
     assert torch.equal(gh, gt.half())
 
 
-def test_sdf_trace_matches_float_march(tiny):
+def test_sdf_trace_matches_float_march(tiny, tuning):
     rq = tiny.rq
     p = rq.split_params(mode=rq.MODE_SDF)
     g = gpu_hits_to_numpy(rq.rt_trace_sdf(tiny.sdf, tiny.rays_d, p))
@@ -136,7 +156,7 @@ def test_sdf_trace_matches_float_march(tiny):
 
 
 @pytest.mark.parametrize("m", [0.0, 1.0, 2.0, 4.0, math.inf])
-def test_combined_one_split(tiny, m):
+def test_combined_one_split(tiny, m, tuning):
     rq = tiny.rq
     p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
     g = gpu_hits_to_numpy(rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p))
@@ -147,7 +167,7 @@ def test_combined_one_split(tiny, m):
     check_sdf_resolved(g, o, sel=same)
 
 
-def test_endpoint_identities(tiny):
+def test_endpoint_identities(tiny, tuning):
     """A multiplier of 0 is the pure field trace and +inf the pure triangle trace, bit for bit."""
     rq = tiny.rq
     for mode in (rq.MODE_SPLIT1, rq.MODE_SPLIT2):
@@ -178,7 +198,7 @@ def _shadow_rays(s, n, seed):
 
 
 @pytest.mark.parametrize("any_hit", [True, False])
-def test_combined_two_split_shadow(tiny, any_hit):
+def test_combined_two_split_shadow(tiny, any_hit, tuning):
     rq = tiny.rq
     rays = _shadow_rays(tiny.s, 3000, 8)
     p = rq.split_params(mode=rq.MODE_SPLIT2, any_hit=any_hit, m_near=2.0, m_far=2.0)
@@ -192,12 +212,13 @@ def test_combined_two_split_shadow(tiny, any_hit):
         check_bvh_resolved(g, o, rays, tiny.s.verts, tiny.s.tris, sel=(o["tracer"] == 1) & same)
 
 
-def test_fp16_grid_matches_float_march_on_rounded_values(tiny):
+def test_fp16_grid_matches_float_march_on_rounded_values(tiny, tuning):
     rq = tiny.rq
     s = tiny.s
     v16 = tiny.vals64.astype(np.float16)
     gt = _cuda(v16.reshape(32, 32, 32))
     sdf16 = rq.rt_sdf_create(gt, s.lo, s.hi)
+    rq.rt_sdf_prepare(sdf16)
     grid = O.Grid(s.lo, s.hi, tiny.n, values=v16.astype(np.float64))
     for mode, m in ((rq.MODE_SDF, 0.0), (rq.MODE_SPLIT1, 2.0)):
         p = rq.split_params(mode=mode, m_near=m)
@@ -209,7 +230,7 @@ def test_fp16_grid_matches_float_march_on_rounded_values(tiny):
         assert summ["exact"] >= 0.999
 
 
-def test_edge_cases(tiny):
+def test_edge_cases(tiny, tuning):
     rq = tiny.rq
     p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=2.0)
     # empty batch
@@ -234,7 +255,7 @@ def test_edge_cases(tiny):
         np.testing.assert_allclose(g["t"][hit], o["t"][hit], rtol=1e-4)
 
 
-def test_counted_variant_same_hits(tiny):
+def test_counted_variant_same_hits(tiny, tuning):
     rq = tiny.rq
     p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=2.0)
     a = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p)
@@ -262,12 +283,13 @@ def noisy(tiny):
     v32 = vals.astype(np.float32)
     gt = _cuda(v32.reshape(32, 32, 32))
     sdf = tiny.rq.rt_sdf_create(gt, s.lo, s.hi)
+    tiny.rq.rt_sdf_prepare(sdf)
     grid = O.Grid(s.lo, s.hi, tiny.n, values=v32.astype(np.float64))
     rays = R.gi_rays(s, 1024, 31, s.diagonal)
     return gt, sdf, grid, rays
 
 
-def test_backward_matches_oracle_adjoint(tiny, noisy):
+def test_backward_matches_oracle_adjoint(tiny, noisy, tuning):
     rq = tiny.rq
     gt, sdf, grid, rays = noisy
     p = rq.split_params(mode=rq.MODE_SDF, refine_root=True)
@@ -320,3 +342,63 @@ def test_autograd_function_matches_central_differences(tiny, noisy):
         m = fin & np.isfinite(tp) & np.isfinite(tm) & ok.cpu().numpy()
         fd = np.sum((tp[m] ** 2 - tm[m] ** 2)) / (2 * d)
         assert grad[vi] == pytest.approx(fd, rel=2e-2, abs=1e-3 * np.abs(grad).max())
+
+
+def test_tunings_give_identical_hits(tiny, medium):
+    """Results do not depend on the launch tuning: every kernel/layout/refill setting
+    returns the same hit records, bit for bit."""
+    rq = tiny.rq
+    for w in (tiny,):
+        for mode, m in ((rq.MODE_SPLIT1, 2.0), (rq.MODE_SPLIT2, 2.0), (rq.MODE_BVH, 0.0), (rq.MODE_SDF, 0.0)):
+            for any_hit in (False, True):
+                p = rq.split_params(mode=mode, m_near=m, m_far=m, any_hit=any_hit)
+                ref = None
+                for name, kw in TUNINGS.items():
+                    prev = rq.rt_set_tuning(**kw)
+                    try:
+                        h = rq.rt_trace_combined(w.scene, w.sdf, w.rays_d, p)
+                    finally:
+                        rq.rt_set_tuning(prev)
+                    if any_hit:
+                        h = h[:, 4] > 0  # which valid hit is reported may differ; hit/miss may not
+                    if ref is None:
+                        ref = h
+                    else:
+                        assert torch.equal(h, ref), (name, mode, any_hit)
+
+
+def test_sdf_prepare_tracks_grid_updates(tiny):
+    """The cell copy is what the traces read: after writing the grid, prepare refreshes it."""
+    rq = tiny.rq
+    s = tiny.s
+    g = tiny.gridt.clone()
+    sdf = rq.rt_sdf_create(g, s.lo, s.hi)
+    rq.rt_sdf_prepare(sdf)
+    p = rq.split_params(mode=rq.MODE_SDF)
+    a = rq.rt_trace_sdf(sdf, tiny.rays_d, p)
+    g.add_(0.05)
+    rq.rt_sdf_prepare(sdf)
+    b = rq.rt_trace_sdf(sdf, tiny.rays_d, p)
+    prev = rq.rt_set_tuning(grid_layout=rq.LAYOUT_PLAIN)
+    try:
+        c = rq.rt_trace_sdf(sdf, tiny.rays_d, p)
+    finally:
+        rq.rt_set_tuning(prev)
+    assert not torch.equal(a, b)
+    assert torch.equal(b, c)
+
+
+def test_timed_variant_reports_each_launch(tiny):
+    rq = tiny.rq
+    p = rq.split_params(mode=rq.MODE_SPLIT2, m_near=2.0, m_far=2.0)
+    a = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p)
+    b, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
+    assert torch.equal(a, b)
+    assert [x[0] for x in st] == ["bvh_near", "field_split", "bvh_far"]
+    assert all(ms > 0 for _, ms in st)
+    prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
+    try:
+        c, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
+    finally:
+        rq.rt_set_tuning(prev)
+    assert torch.equal(a, c) and [x[0] for x in st] == ["all"]
