@@ -21,6 +21,10 @@ using namespace rtdev;
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+#ifndef RT_TRIP_BUDGET
+#define RT_TRIP_BUDGET 8
+#endif
+constexpr int kTripBudget = RT_TRIP_BUDGET;  // traversal iterations between two refill checks
 
 // ---------------------------------------------------------------------------
 // simple kernel: one thread per query
@@ -209,7 +213,7 @@ __global__ void k_stage_bvh(const TraceArgs a, const StageArgs st)
                 final_miss = invalid;
             }
         } else if (live) {
-            if (trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt)) {
+            if (trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt, kTripBudget)) {
                 done = true;
                 found = s.found;
                 live = false;

@@ -22,12 +22,34 @@ __device__ __forceinline__ float sel3(float x, float y, float z, int k) { return
 
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 
-// 32-byte read-only vector load (sm_100 family); p must be 32-byte aligned
+// 32-byte read-only vector load (sm_100 family); p must be 32-byte aligned.
+// Not volatile: the load has no side effect, so the compiler may schedule it.
 __device__ __forceinline__ void ldg8(const void* p, float v[8])
 {
+#ifdef RT_LDG8_VOLATILE
     asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
                  : "l"(p));
+#else
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
+#endif
+}
+
+// a 64-byte node as two 32-byte vectors (default) or four 16-byte ones
+__device__ __forceinline__ void load_node(const BNode* nodes, int node, float v[8], float w[8])
+{
+    const float* np = reinterpret_cast<const float*>(nodes + node);
+#ifdef RT_NODE_LOAD128
+    const float4* q = reinterpret_cast<const float4*>(np);
+    float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    w[0] = c.x; w[1] = c.y; w[2] = c.z; w[3] = c.w; w[4] = d.x; w[5] = d.y; w[6] = d.z; w[7] = d.w;
+#else
+    ldg8(np, v);
+    ldg8(np + 8, w);
+#endif
 }
 
 // ---------------------------------------------------------------------------
@@ -82,9 +104,7 @@ struct NodeHit {
 __device__ __forceinline__ NodeHit visit_node(const BNode* nodes, int node, const BvhRay& r, float ta, float tf)
 {
     float v[8], w[8];
-    const float* np = reinterpret_cast<const float*>(nodes + node);
-    ldg8(np, v);
-    ldg8(np + 8, w);
+    load_node(nodes, node, v, w);
     // v = a (c0 x/y), b (c1 x/y); w = c (z of both), d (children)
     float x0 = fmaf(v[0], r.idir.x, -r.ood.x), x1 = fmaf(v[1], r.idir.x, -r.ood.x);
     float y0 = fmaf(v[2], r.idir.y, -r.ood.y), y1 = fmaf(v[3], r.idir.y, -r.ood.y);
@@ -163,37 +183,42 @@ __device__ __forceinline__ Trav trav_begin(int root, float ta, float tb)
     return s;
 }
 
-// One trip of the while-while loop: descend through internal nodes to the next
-// leaf, test it, and pop the next subtree.  Returns true when the segment is done.
+// Up to `budget` traversal iterations; each iteration visits one internal node
+// or tests one leaf (lanes at leaves and lanes at inner nodes share every
+// iteration, so none waits for the others to reach a leaf).  Returns true when
+// the segment is done.
 template <bool COUNT>
 __device__ __forceinline__ bool trav_trip(const TraceArgs& a, const BvhRay& r, Trav& s, int* stack, bool any_hit,
-                                          Hit& best, uint32_t& flags, Counts& cnt)
+                                          Hit& best, uint32_t& flags, Counts& cnt, int budget)
 {
-    while (s.node >= 0) {
+    for (int it = 0; it < budget; ++it) {
         if (++s.guard > (1u << 26)) {  // a tree visit is bounded by 2n-1 nodes; stops only a corrupt structure
             flags |= RT_FLAG_ITER_LIMIT;
             return true;
         }
-        if (COUNT) ++cnt.nodes;
-        NodeHit h = visit_node(a.nodes, s.node, r, s.ta, s.tbest);
-        if (h.h0 && h.h1) {
-            if (s.sp < RT_STACK_DEPTH) stack[s.sp++] = h.farc;
-            else flags |= RT_FLAG_STACK_OVERFLOW;
-            s.node = h.nearc;
-        } else if (h.h0 || h.h1) {
-            s.node = h.h0 ? h.nearc : h.farc;
+        if (s.node >= 0) {
+            if (COUNT) ++cnt.nodes;
+            NodeHit h = visit_node(a.nodes, s.node, r, s.ta, s.tbest);
+            if (h.h0 && h.h1) {
+                if (s.sp < RT_STACK_DEPTH) stack[s.sp++] = h.farc;
+                else flags |= RT_FLAG_STACK_OVERFLOW;
+                s.node = h.nearc;
+                continue;
+            }
+            if (h.h0 || h.h1) {
+                s.node = h.h0 ? h.nearc : h.farc;
+                continue;
+            }
         } else {
-            if (s.sp == 0) return true;
-            s.node = stack[--s.sp];
+            if (COUNT) ++cnt.tris;
+            if (test_triangle(a.tris, ~s.node, r, s.ta, s.tbest, s.found, best)) {
+                s.found = true;
+                if (any_hit) return true;
+            }
         }
+        if (s.sp == 0) return true;
+        s.node = stack[--s.sp];
     }
-    if (COUNT) ++cnt.tris;
-    if (test_triangle(a.tris, ~s.node, r, s.ta, s.tbest, s.found, best)) {
-        s.found = true;
-        if (any_hit) return true;
-    }
-    if (s.sp == 0) return true;
-    s.node = stack[--s.sp];
     return false;
 }
 
@@ -206,7 +231,7 @@ __device__ __forceinline__ bool bvh_segment(const TraceArgs& a, float3 o, float3
     const BvhRay r = bvh_ray(o, d);
     int stack[RT_STACK_DEPTH];
     Trav s = trav_begin(a.root, ta, tb);
-    while (!trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt)) {
+    while (!trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt, 1 << 30)) {
     }
     return s.found;
 }
