@@ -214,6 +214,29 @@ rt_status rt_trace_combined_timed(const rt_scene* scene, const rt_sdf* sdf, cons
                                   const rt_split_params* params, rt_hit* d_hits, float stage_ms[3],
                                   int32_t stage_kind[3], int32_t* n_stages, void* stream);
 
+/* The combined query of rt_trace_combined, for callers that cannot allocate
+ * device memory during the call: for example a renderer whose frame loop
+ * forbids allocation, or a host that hands the library a fixed device-memory
+ * budget and must not see it grow.  rt_trace_combined takes its per-call
+ * scratch (work counters and two ray queues) from a memory pool; this entry
+ * point allocates nothing and uses one fixed array compiled into the library
+ * instead.  The paper has no counterpart: this is a deployment variant.
+ *   - At most 1,048,576 queries per call (the array holds 16 MiB + 256 bytes
+ *     and every GPU that loads the library keeps it until the process ends);
+ *     a larger n is rejected with RT_ERR_INVALID_ARG before any work.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the one array.  Calls whose work overlaps on
+ *     the GPU (other streams, other threads) race and corrupt each other's
+ *     results: serialise them, e.g. on one stream.  The counters are cleared
+ *     on `stream` at the start of every call.
+ *   - Always runs the wavefront stage kernels (the tuning's block, residency,
+ *     refill and layout apply); results equal rt_trace_combined's.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+rt_status rt_trace_combined_noalloc(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
+                                    const rt_split_params* params, rt_hit* d_hits, void* stream);
+
 /* Adjoint of the field-resolved hit distance.  For each query whose hit
  * record (from a forward call with the same params, refine_root = 1) has
  * tracer == RT_TRACER_SDF, the root p* = o + t d of phi = eps satisfies

@@ -36,8 +36,8 @@ LAYOUT_CELLS, LAYOUT_PLAIN = 0, 1
 
 EXPORTS = ("rt_scene_build", "rt_scene_info_get", "rt_scene_destroy", "rt_sdf_create", "rt_sdf_destroy",
            "rt_sdf_prepare", "rt_sdf_bake", "rt_trace_bvh", "rt_trace_sdf", "rt_trace_combined",
-           "rt_trace_combined_counted", "rt_trace_combined_timed", "rt_trace_combined_backward", "rt_set_tuning",
-           "rt_get_tuning",
+           "rt_trace_combined_counted", "rt_trace_combined_timed", "rt_trace_combined_noalloc",
+           "rt_trace_combined_backward", "rt_set_tuning", "rt_get_tuning",
            "rt_last_error", "rt_version")
 
 
@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
             "rt_trace_combined": [P, P, P, i64, P, P, P],
             "rt_trace_combined_counted": [P, P, P, i64, P, P, P, P],
             "rt_trace_combined_timed": [P, P, P, i64, P, P, P, P, P, P],
+            "rt_trace_combined_noalloc": [P, P, P, i64, P, P, P],
             "rt_trace_combined_backward": [P, P, P, i64, P, P, P, P, P],
         }
         for name, args in sig.items():
@@ -269,6 +270,23 @@ def rt_trace_combined_counted(scene: Scene | None, sdf: Sdf | None, rays: torch.
                                            _dptr(rays), rays.shape[0], ctypes.byref(params), _dptr(hits),
                                            _dptr(counters), _stream(stream)))
     return hits, counters
+
+
+NOALLOC_MAX_RAYS = 1 << 20
+
+
+def rt_trace_combined_noalloc(scene: Scene | None, sdf: Sdf | None, rays: torch.Tensor, params: rt_split_params,
+                              hits: torch.Tensor, stream=None) -> torch.Tensor:
+    """rt_trace_combined without any device allocation (fixed in-library scratch,
+    at most NOALLOC_MAX_RAYS queries per call; concurrent calls race).  `hits`
+    must be preallocated by the caller."""
+    if hits is None:
+        raise ValueError("the caller provides the hit buffer")
+    hits = _rays_hits(rays, hits)
+    _check(lib().rt_trace_combined_noalloc(scene.handle if scene else None, sdf.handle if sdf else None,
+                                           _dptr(rays), rays.shape[0], ctypes.byref(params), _dptr(hits),
+                                           _stream(stream)))
+    return hits
 
 
 STAGE_NAMES = {0: "all", 1: "bvh_full", 2: "bvh_near", 3: "bvh_far", 4: "field_full", 5: "field_split"}

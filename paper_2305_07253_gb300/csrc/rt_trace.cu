@@ -455,3 +455,116 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
     }
     return RT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// rt_trace_combined_noalloc: the wavefront trace with its scratch (the stage
+// counters and the two queues) in one fixed device array of this file instead
+// of memory taken from the pool on every call.  The array is sized for
+// kNoAllocMaxRays queries and is part of the module: every device that loads
+// the library holds it until the process exits.  Host code reaches it only
+// through the address returned by cudaGetSymbolAddress (the array's name is a
+// host-side stand-in, not a device address).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxRays = (int64_t)1 << 20;
+constexpr size_t kNoAllocCounterBytes = 256;
+constexpr size_t kNoAllocQueueBytes = (size_t)kNoAllocMaxRays * sizeof(int2);
+constexpr size_t kNoAllocBytes = kNoAllocCounterBytes + 2 * kNoAllocQueueBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocDevice {
+    void* scratch = nullptr;  // device address of g_noalloc_scratch on this device
+    int sms = 0;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+
+// once per device, with that device current: look up the array's device address
+rt_status noalloc_setup(NoAllocDevice*& out)
+{
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return rt_fail(RT_ERR_INVALID_ARG, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.scratch) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return rt_cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return rt_cuda_fail(e, "cudaDeviceGetAttribute");
+        d.sms = sms;
+        d.scratch = p;
+    }
+    out = &d;
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" rt_status rt_trace_combined_noalloc(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
+                                               const rt_split_params* p, rt_hit* hits, void* stream)
+{
+    if (!p) return rt_fail(RT_ERR_INVALID_ARG, "params is null");
+    if (p->mode < 0 || p->mode > 3) return rt_fail(RT_ERR_INVALID_ARG, "mode %d not in 0..3", p->mode);
+    if (!(p->m_near >= 0.f) || !(p->m_far >= 0.f))
+        return rt_fail(RT_ERR_INVALID_ARG, "multipliers must be >= 0 (got %g, %g)", p->m_near, p->m_far);
+    if (p->max_steps < 1) return rt_fail(RT_ERR_INVALID_ARG, "max_steps must be >= 1");
+    if (!(p->hit_eps_vox >= 0.f) || !(p->min_step_vox > 0.f) || isinf(p->hit_eps_vox) || isinf(p->min_step_vox))
+        return rt_fail(RT_ERR_INVALID_ARG, "hit_eps_vox must be >= 0 and min_step_vox > 0, both finite");
+    if (p->any_hit != 0 && p->any_hit != 1) return rt_fail(RT_ERR_INVALID_ARG, "any_hit must be 0 or 1");
+    if (n < 0) return rt_fail(RT_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+    if (n > kNoAllocMaxRays)
+        return rt_fail(RT_ERR_INVALID_ARG,
+                       "rt_trace_combined_noalloc takes at most %lld queries per call (got %lld); split the batch "
+                       "or use rt_trace_combined", (long long)kNoAllocMaxRays, (long long)n);
+    if (p->mode != RT_MODE_SDF && !sc) return rt_fail(RT_ERR_INVALID_ARG, "mode %d needs a scene", p->mode);
+    if (p->mode != RT_MODE_BVH && !sdf) return rt_fail(RT_ERR_INVALID_ARG, "mode %d needs a grid", p->mode);
+    if (n == 0) return RT_OK;
+    if (!rays || !hits) return rt_fail(RT_ERR_INVALID_ARG, "null ray or hit buffer");
+    if (((uintptr_t)rays & 15u) != 0) return rt_fail(RT_ERR_INVALID_ARG, "ray buffer not 16-byte aligned");
+    if (((uintptr_t)hits & 7u) != 0) return rt_fail(RT_ERR_INVALID_ARG, "hit buffer not 8-byte aligned");
+    int cur = -1;
+    RT_CUDA_TRY(cudaGetDevice(&cur));
+    if (sc && sc->device != cur) return rt_fail(RT_ERR_INVALID_ARG, "scene belongs to device %d, current is %d",
+                                                sc->device, cur);
+    NoAllocDevice* dev = nullptr;
+    rt_status st = noalloc_setup(dev);
+    if (st != RT_OK) return st;
+
+    TraceArgs a;
+    rt_fill_trace_args(a, p->mode == RT_MODE_SDF ? nullptr : sc, p->mode == RT_MODE_BVH ? nullptr : sdf, p);
+    a.rays = reinterpret_cast<const float4*>(rays);
+    a.hits = hits;
+    a.n = n;
+    a.counters = nullptr;
+    const rt_tuning& tu = rt_current_tuning();
+    if (tu.grid_layout == RT_LAYOUT_PLAIN) a.cells = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    int kinds[3];
+    const int n_st = stage_program(a, kinds);
+    unsigned char* base = static_cast<unsigned char*>(dev->scratch);
+    unsigned* ctr = reinterpret_cast<unsigned*>(base);
+    int2* q[2] = {reinterpret_cast<int2*>(base + kNoAllocCounterBytes),
+                  reinterpret_cast<int2*>(base + kNoAllocCounterBytes + kNoAllocQueueBytes)};
+    // every call starts from zeroed counters (the array keeps the last call's contents)
+    RT_CUDA_TRY(cudaMemsetAsync(ctr, 0, kNoAllocCounterBytes, s));
+    for (int k = 0; k < n_st; ++k) {
+        StageArgs sa;
+        sa.kind = kinds[k];
+        sa.first = k == 0;
+        sa.in_items = k > 0 ? q[(k - 1) & 1] : nullptr;
+        sa.in_count = k > 0 ? &ctr[3 + ((k - 1) & 1)] : nullptr;
+        sa.out_items = k + 1 < n_st ? q[k & 1] : nullptr;
+        sa.out_count = k + 1 < n_st ? &ctr[3 + (k & 1)] : nullptr;
+        sa.fetch = &ctr[k];
+        sa.refill_min = tu.refill_min;
+        st = launch_stage<false>(a, sa, tu, dev->sms, s);
+        if (st != RT_OK) return st;
+    }
+    return RT_OK;
+}
