@@ -15,6 +15,7 @@ namespace {
 
 constexpr int kBwdBlock = 128;
 
+template <int L>
 __global__ void __launch_bounds__(kBwdBlock) k_backward(const TraceArgs a, const float* __restrict__ grad_t,
                                                         float* __restrict__ grad_grid)
 {
@@ -34,9 +35,9 @@ __global__ void __launch_bounds__(kBwdBlock) k_backward(const TraceArgs a, const
     }
     uint32_t flags = 0;
     Counts cnt = {0, 0, 0, 0};
-    March m = sdf_march<false>(a, o, d, ts, te, flags, cnt);
+    March m = sdf_march<false, L>(a, o, d, ts, te, flags, cnt);
     if (!m.hit || isnan(m.t_prev)) return;  // a hit at the first sample has no bracket
-    const float t = refine(a, o, d, m.t_prev, m.t);
+    const float t = refine<L>(a, o, d, m.t_prev, m.t);
     const float px = __fmaf_rn(t, d.x, o.x), py = __fmaf_rn(t, d.y, o.y), pz = __fmaf_rn(t, d.z, o.z);
     Cell c = locate(a, px, py, pz);
     const int64_t base = grid_base(a, c);
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(kBwdBlock) k_backward(const TraceArgs a, const
     const int64_t off[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
     float v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = grid_at(a, base + off[k]);
+    for (int k = 0; k < 8; ++k) v[k] = grid_at<GL_PLAIN_F32>(a, base + off[k]);
     const float fx = c.f[0], fy = c.f[1], fz = c.f[2];
     const float gx = c.clamped[0] ? 0.f
         : ((v[1] - v[0]) * (1 - fy) * (1 - fz) + (v[3] - v[2]) * fy * (1 - fz) + (v[5] - v[4]) * (1 - fy) * fz +
@@ -71,7 +72,9 @@ rt_status rt_launch_backward(const TraceArgs& a, const float* grad_t, float* gra
 {
     const int64_t blocks = (a.n + kBwdBlock - 1) / kBwdBlock;
     if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "too many rays");
-    k_backward<<<(unsigned)blocks, kBwdBlock, 0, s>>>(a, grad_t, grad_grid);
+    // float32 grids only (checked by the caller); the march reads the cell copy when present
+    if (a.cells) k_backward<GL_CELLS_F32><<<(unsigned)blocks, kBwdBlock, 0, s>>>(a, grad_t, grad_grid);
+    else k_backward<GL_PLAIN_F32><<<(unsigned)blocks, kBwdBlock, 0, s>>>(a, grad_t, grad_grid);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }

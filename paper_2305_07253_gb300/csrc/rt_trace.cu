@@ -25,11 +25,15 @@ constexpr unsigned kFull = 0xffffffffu;
 #define RT_TRIP_BUDGET 8
 #endif
 constexpr int kTripBudget = RT_TRIP_BUDGET;  // traversal iterations between two refill checks
+#ifndef RT_FIELD_BUDGET
+#define RT_FIELD_BUDGET 4
+#endif
+constexpr int kFieldBudget = RT_FIELD_BUDGET;  // march steps between two refill checks
 
 // ---------------------------------------------------------------------------
 // simple kernel: one thread per query
 // ---------------------------------------------------------------------------
-template <bool COUNT>
+template <bool COUNT, int L>
 __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts& cnt)
 {
     const float4 r0 = __ldg(a.rays + 2 * i), r1 = __ldg(a.rays + 2 * i + 1);
@@ -43,19 +47,19 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
     } else if (a.mode == RT_MODE_BVH) {
         if (bvh_segment<COUNT>(a, o, d, tmin, tmax, a.any_hit, h, flags, cnt)) tracer = RT_TRACER_BVH;
     } else if (a.mode == RT_MODE_SDF) {
-        March m = sdf_march<COUNT>(a, o, d, tmin, tmax, flags, cnt);
+        March m = sdf_march<COUNT, L>(a, o, d, tmin, tmax, flags, cnt);
         if (m.hit) {
             tracer = RT_TRACER_SDF;
-            h.t = (a.refine_root && !isnan(m.t_prev)) ? refine(a, o, d, m.t_prev, m.t) : m.t;
+            h.t = (a.refine_root && !isnan(m.t_prev)) ? refine<L>(a, o, d, m.t_prev, m.t) : m.t;
         }
     } else {
         const Split s = make_split(a, tmin, tmax);
         if (a.any_hit) {
             if (s.field) {
-                March m = sdf_march<COUNT>(a, o, d, s.t1, s.t2, flags, cnt);
+                March m = sdf_march<COUNT, L>(a, o, d, s.t1, s.t2, flags, cnt);
                 if (m.hit) {
                     tracer = RT_TRACER_SDF;
-                    h.t = (a.refine_root && !isnan(m.t_prev)) ? refine(a, o, d, m.t_prev, m.t) : m.t;
+                    h.t = (a.refine_root && !isnan(m.t_prev)) ? refine<L>(a, o, d, m.t_prev, m.t) : m.t;
                 }
             }
             if (tracer == RT_TRACER_MISS && s.near_bvh && bvh_segment<COUNT>(a, o, d, tmin, s.t1, true, h, flags, cnt))
@@ -65,10 +69,10 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
         } else {
             if (s.near_bvh && bvh_segment<COUNT>(a, o, d, tmin, s.t1, false, h, flags, cnt)) tracer = RT_TRACER_BVH;
             if (tracer == RT_TRACER_MISS && s.field) {
-                March m = sdf_march<COUNT>(a, o, d, s.t1, s.t2, flags, cnt);
+                March m = sdf_march<COUNT, L>(a, o, d, s.t1, s.t2, flags, cnt);
                 if (m.hit) {
                     tracer = RT_TRACER_SDF;
-                    h.t = (a.refine_root && !isnan(m.t_prev)) ? refine(a, o, d, m.t_prev, m.t) : m.t;
+                    h.t = (a.refine_root && !isnan(m.t_prev)) ? refine<L>(a, o, d, m.t_prev, m.t) : m.t;
                 }
             }
             if (tracer == RT_TRACER_MISS && s.far_bvh && bvh_segment<COUNT>(a, o, d, s.t2, tmax, false, h, flags, cnt))
@@ -90,12 +94,12 @@ __device__ __forceinline__ void flush_counts(const TraceArgs& a, const Counts& c
     if (cnt.field) atomicAdd(&a.counters[3], (unsigned long long)cnt.field);
 }
 
-template <bool COUNT>
+template <bool COUNT, int L>
 __global__ void k_trace(const TraceArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     Counts cnt = {0, 0, 0, 0};
-    if (i < a.n) trace_one<COUNT>(a, i, cnt);
+    if (i < a.n) trace_one<COUNT, L>(a, i, cnt);
     if (COUNT) flush_counts(a, cnt);
 }
 
@@ -230,7 +234,7 @@ __global__ void k_stage_bvh(const TraceArgs a, const StageArgs st)
     if (COUNT) flush_counts(a, cnt);
 }
 
-template <bool COUNT>
+template <bool COUNT, int L>
 __global__ void k_stage_field(const TraceArgs a, const StageArgs st)
 {
     const unsigned n_in = st.first ? (unsigned)a.n : *st.in_count;
@@ -264,17 +268,21 @@ __global__ void k_stage_field(const TraceArgs a, const StageArgs st)
                 final_miss = invalid;
             }
         } else if (live) {
-            if (COUNT) ++cnt.steps;
-            const int res = march_step(a, o, d, t, tb, t_prev);
-            ++k;
-            if (res == 1) {
-                done = true;
-                found = true;
-            } else if (res == 2) {
-                done = true;
-            } else if (k >= a.max_steps) {
-                flags |= RT_FLAG_STEP_LIMIT;
-                done = true;
+            // several march steps between two refill checks
+            for (int it = 0; it < kFieldBudget; ++it) {
+                if (COUNT) ++cnt.steps;
+                const int res = march_step<L>(a, o, d, t, tb, t_prev);
+                ++k;
+                if (res == 1) {
+                    done = true;
+                    found = true;
+                } else if (res == 2) {
+                    done = true;
+                } else if (k >= a.max_steps) {
+                    flags |= RT_FLAG_STEP_LIMIT;
+                    done = true;
+                }
+                if (done) break;
             }
             if (done) live = false;
         }
@@ -282,7 +290,7 @@ __global__ void k_stage_field(const TraceArgs a, const StageArgs st)
         forward(st, fwd, query, flags);
         if (done && !fwd) {
             if (found) {
-                const float th = (a.refine_root && !isnan(t_prev)) ? refine(a, o, d, t_prev, t) : t;
+                const float th = (a.refine_root && !isnan(t_prev)) ? refine<L>(a, o, d, t_prev, t) : t;
                 store_hit(a.hits + query, th, -1, 0.f, 0.f, RT_TRACER_SDF, flags);
             } else {
                 store_hit(a.hits + query, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
@@ -344,8 +352,19 @@ rt_status launch_stage(const TraceArgs& a, const StageArgs& st, const rt_tuning&
 {
     const bool field = st.kind == ST_FIELD_FULL || st.kind == ST_FIELD_SPLIT;
     if (field) {
-        int blocks = persistent_blocks(k_stage_field<COUNT>, tu.block, tu, sms);
-        k_stage_field<COUNT><<<blocks, tu.block, 0, s>>>(a, st);
+        switch (grid_layout_of(a)) {
+#define RT_FIELD_CASE(LL)                                                                  \
+    case LL: {                                                                             \
+        int blocks = persistent_blocks(k_stage_field<COUNT, LL>, tu.block, tu, sms);       \
+        k_stage_field<COUNT, LL><<<blocks, tu.block, 0, s>>>(a, st);                       \
+        break;                                                                             \
+    }
+            RT_FIELD_CASE(GL_PLAIN_F32)
+            RT_FIELD_CASE(GL_PLAIN_F16)
+            RT_FIELD_CASE(GL_CELLS_F32)
+            RT_FIELD_CASE(GL_CELLS_F16)
+#undef RT_FIELD_CASE
+        }
     } else {
         int blocks = persistent_blocks(k_stage_bvh<COUNT>, tu.block, tu, sms);
         k_stage_bvh<COUNT><<<blocks, tu.block, 0, s>>>(a, st);
@@ -446,8 +465,16 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
         RT_CUDA_TRY(cudaEventRecord(timing->events[0], s));
         timing->kinds[0] = RT_STAGE_ALL;
     }
-    if (counted) k_trace<true><<<(unsigned)blocks, tu.block, 0, s>>>(a);
-    else k_trace<false><<<(unsigned)blocks, tu.block, 0, s>>>(a);
+    switch (grid_layout_of(a) + (counted ? 4 : 0)) {
+    case 0: k_trace<false, GL_PLAIN_F32><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
+    case 1: k_trace<false, GL_PLAIN_F16><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
+    case 2: k_trace<false, GL_CELLS_F32><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
+    case 3: k_trace<false, GL_CELLS_F16><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
+    case 4: k_trace<true, GL_PLAIN_F32><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
+    case 5: k_trace<true, GL_PLAIN_F16><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
+    case 6: k_trace<true, GL_CELLS_F32><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
+    default: k_trace<true, GL_CELLS_F16><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
+    }
     RT_CUDA_TRY(cudaGetLastError());
     if (timing) {
         RT_CUDA_TRY(cudaEventRecord(timing->events[1], s));

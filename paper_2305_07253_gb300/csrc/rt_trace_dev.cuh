@@ -246,9 +246,20 @@ __device__ __forceinline__ bool bvh_segment(const TraceArgs& a, float3 o, float3
 // trilinear: u = (p - lo) * (1/h), clamped to [0, n-1]; i0 = min(floor(u), n-2);
 // f = u - i0; lerp(a, b, f) = fma(f, b - a, a) along x, then y, then z.
 // ---------------------------------------------------------------------------
+// Grid storage seen by the march, fixed at compile time so that a step has no
+// layout or type branches: the caller's plain grid (float32 / float16) or the
+// library's cell-corner copy (float32 / float16).
+enum GridLayout { GL_PLAIN_F32 = 0, GL_PLAIN_F16 = 1, GL_CELLS_F32 = 2, GL_CELLS_F16 = 3 };
+
+__host__ __device__ __forceinline__ int grid_layout_of(const TraceArgs& a)
+{
+    return (a.cells ? 2 : 0) + (a.grid_f16 ? 1 : 0);
+}
+
+template <int L>
 __device__ __forceinline__ float grid_at(const TraceArgs& a, int64_t i)
 {
-    if (a.grid_f16) return __half2float(__ldg(reinterpret_cast<const __half*>(a.grid) + i));
+    if (L == GL_PLAIN_F16 || L == GL_CELLS_F16) return __half2float(__ldg(reinterpret_cast<const __half*>(a.grid) + i));
     return __ldg(reinterpret_cast<const float*>(a.grid) + i);
 }
 
@@ -287,43 +298,44 @@ __device__ __forceinline__ int64_t cell_index(const TraceArgs& a, const Cell& c)
 }
 
 // the 8 corner values of the cell, order v000 v100 v010 v110 v001 v101 v011 v111
+template <int L>
 __device__ __forceinline__ void corners(const TraceArgs& a, const Cell& c, float v[8])
 {
-    if (a.cells) {
-        const int64_t ci = cell_index(a, c);
-        if (a.grid_f16) {
-            uint4 q = __ldg(reinterpret_cast<const uint4*>(a.cells) + ci);
-            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    if (L == GL_CELLS_F16) {
+        uint4 q = __ldg(reinterpret_cast<const uint4*>(a.cells) + cell_index(a, c));
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                __half2 h2 = *reinterpret_cast<const __half2*>(&w[k]);
-                v[2 * k] = __low2float(h2);
-                v[2 * k + 1] = __high2float(h2);
-            }
-        } else {
-            ldg8(reinterpret_cast<const float*>(a.cells) + 8 * ci, v);
+        for (int k = 0; k < 4; ++k) {
+            __half2 h2 = *reinterpret_cast<const __half2*>(&w[k]);
+            v[2 * k] = __low2float(h2);
+            v[2 * k + 1] = __high2float(h2);
         }
+        return;
+    }
+    if (L == GL_CELLS_F32) {
+        ldg8(reinterpret_cast<const float*>(a.cells) + 8 * cell_index(a, c), v);
         return;
     }
     const int64_t b = grid_base(a, c);
     const int64_t sy = a.gn[0], sz = (int64_t)a.gn[0] * a.gn[1];
-    v[0] = grid_at(a, b);
-    v[1] = grid_at(a, b + 1);
-    v[2] = grid_at(a, b + sy);
-    v[3] = grid_at(a, b + sy + 1);
-    v[4] = grid_at(a, b + sz);
-    v[5] = grid_at(a, b + sz + 1);
-    v[6] = grid_at(a, b + sz + sy);
-    v[7] = grid_at(a, b + sz + sy + 1);
+    v[0] = grid_at<L>(a, b);
+    v[1] = grid_at<L>(a, b + 1);
+    v[2] = grid_at<L>(a, b + sy);
+    v[3] = grid_at<L>(a, b + sy + 1);
+    v[4] = grid_at<L>(a, b + sz);
+    v[5] = grid_at<L>(a, b + sz + 1);
+    v[6] = grid_at<L>(a, b + sz + sy);
+    v[7] = grid_at<L>(a, b + sz + sy + 1);
 }
 
 __device__ __forceinline__ float lerp_rn(float f, float x, float y) { return __fmaf_rn(f, __fsub_rn(y, x), x); }
 
+template <int L>
 __device__ __forceinline__ float trilinear(const TraceArgs& a, float px, float py, float pz)
 {
     Cell c = locate(a, px, py, pz);
     float v[8];
-    corners(a, c, v);
+    corners<L>(a, c, v);
     float c00 = lerp_rn(c.f[0], v[0], v[1]);
     float c10 = lerp_rn(c.f[0], v[2], v[3]);
     float c01 = lerp_rn(c.f[0], v[4], v[5]);
@@ -359,17 +371,18 @@ struct March {
 };
 
 // One march step at t; returns 0 to continue, 1 on a hit, 2 on leaving [.., tb].
+template <int L>
 __device__ __forceinline__ int march_step(const TraceArgs& a, float3 o, float3 d, float& t, float tb, float& t_prev)
 {
     float px = __fmaf_rn(t, d.x, o.x), py = __fmaf_rn(t, d.y, o.y), pz = __fmaf_rn(t, d.z, o.z);
-    float phi = trilinear(a, px, py, pz);
+    float phi = trilinear<L>(a, px, py, pz);
     if (phi < a.eps_hit) return 1;
     t_prev = t;
     t = __fadd_rn(t, fmaxf(phi, a.eps_min));
     return t > tb ? 2 : 0;
 }
 
-template <bool COUNT>
+template <bool COUNT, int L>
 __device__ __forceinline__ March sdf_march(const TraceArgs& a, float3 o, float3 d, float ta, float tb,
                                            uint32_t& flags, Counts& cnt)
 {
@@ -379,7 +392,7 @@ __device__ __forceinline__ March sdf_march(const TraceArgs& a, float3 o, float3 
     float t = ta;
     for (int k = 0; k < a.max_steps; ++k) {
         if (COUNT) ++cnt.steps;
-        int r = march_step(a, o, d, t, tb, m.t_prev);
+        int r = march_step<L>(a, o, d, t, tb, m.t_prev);
         if (r == 1) {
             m.hit = true;
             m.t = t;
@@ -392,12 +405,13 @@ __device__ __forceinline__ March sdf_march(const TraceArgs& a, float3 o, float3 
 }
 
 // root of phi(o + s d) = eps_hit inside the last step [t_prev, t] (24 halvings)
+template <int L>
 __device__ __forceinline__ float refine(const TraceArgs& a, float3 o, float3 d, float t_prev, float t)
 {
     float lo = t_prev, hi = t;
     for (int it = 0; it < 24; ++it) {
         float mid = 0.5f * (lo + hi);
-        float phi = trilinear(a, __fmaf_rn(mid, d.x, o.x), __fmaf_rn(mid, d.y, o.y), __fmaf_rn(mid, d.z, o.z));
+        float phi = trilinear<L>(a, __fmaf_rn(mid, d.x, o.x), __fmaf_rn(mid, d.y, o.y), __fmaf_rn(mid, d.z, o.z));
         if (phi < a.eps_hit) hi = mid; else lo = mid;
     }
     return 0.5f * (lo + hi);
