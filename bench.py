@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="set up, then run only warmup+steps launches of the --only traces (for ncu); prints timings")
     ap.add_argument("--only", default="all", choices=["all", "combined", "bvh", "sdf"])
+    ap.add_argument("--workload", default="frame", choices=["frame", "batching"],
+                    help="frame: the 1080p GI headline; batching: 8 frames of mixed primary/shadow/AO/GI batches")
+    ap.add_argument("--frames", type=int, default=8)
     return ap.parse_args()
 
 
@@ -410,10 +413,139 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def make_frame_batches(s, frame: int, seed: int = 2305):
+    """One frame of the mixed workload (Section 3's query kinds): primary rays,
+    1-4 AO rays per pixel (t_max 0.5 m, one split), one GI ray per pixel (t_max
+    30 m, one split) and shadow rays to 4 random point lights (two splits, any
+    hit), their count drawn from [0.5 M, 2.07 M]."""
+    from synth import rng as RNG
+    n_px = 1920 * 1080
+    fs = seed * 1000 + frame
+    prim = R.primary_rays(s)
+    p, nn = R.surface_points(s, n_px, fs)
+    bias = 1e-3 * s.diagonal
+    u = RNG.uniform(fs, 901, n_px + 2)
+    per_pt = 1 + (u[:n_px] * 4).astype(np.int64)
+    ao = R.ao_rays(p, nn, per_pt, fs, 0.5, bias)
+    gi = R.ao_rays(p, nn, np.ones(n_px, dtype=np.int64), fs + 7, 30.0, bias)
+    n_sh = int(500_000 + u[n_px] * (n_px - 500_000))
+    lights = 0.5 + RNG.uniform(fs, 902, 12).reshape(4, 3) * (np.array(s.room) - 1.0)
+    sh = R.shadow_rays(p[:n_sh], nn[:n_sh], lights, fs, bias)
+    return [("primary", prim, dict(mode=0)), ("ao", ao, dict(mode=1, m_near=M_MIDDLE)),
+            ("gi", gi, dict(mode=1, m_near=M_MIDDLE)),
+            ("shadow", sh, dict(mode=2, m_near=M_MIDDLE, m_far=M_MIDDLE, any_hit=True))]
+
+
+def run_batching(args):
+    import torch
+
+    import paper_2305_07253_gb300 as rq
+    from paper_2305_07253_gb300 import autotune
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = S.make_scene("frame")
+    n = s.spec.grid_n
+    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
+    grid = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    sdf = rq.rt_sdf_create(grid, s.lo, s.hi)
+    rq.rt_sdf_bake(scene, sdf, rq.BAKE_BVH)
+    frames = []
+    t0 = time.perf_counter()
+    for f in range(args.frames):
+        fb = []
+        for name, rays, kw in make_frame_batches(s, f):
+            rd = torch.from_numpy(rays).to(dev)
+            fb.append((name, rd, rq.split_params(**kw), torch.empty((rd.shape[0], 6), dtype=torch.int32, device=dev)))
+        frames.append(fb)
+    gen_s = time.perf_counter() - t0
+    n_total = sum(b[1].shape[0] for fb in frames for b in fb)
+    sizes = [{b[0]: int(b[1].shape[0]) for b in fb} for fb in frames]
+
+    def per_batch():
+        for fb in frames:
+            for _, rd, p, h in fb:
+                rq.rt_trace_combined(scene, sdf, rd, p, h)
+
+    def batched():
+        for fb in frames:
+            rq.rt_trace_batches(scene, sdf, [(rd, p, h) for _, rd, p, h in fb])
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(1, args.steps // 50)
+    default = rq.rt_get_tuning().as_dict()
+    ms_per_batch_default = timed(per_batch, reps)
+    ms_batched_default = timed(batched, reps)
+    # autotune the batched form on the first frame
+    f0 = [(rd, p, h) for _, rd, p, h in frames[0]]
+    best, results = autotune.autotune(lambda: rq.rt_trace_batches(scene, sdf, f0), reps=3, warmup=1)
+    ms_per_batch = timed(per_batch, reps)
+    ms_batched = timed(batched, reps)
+    # one CUDA graph per frame
+    graphs = []
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        for fb in frames:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=st):
+                rq.rt_trace_batches(scene, sdf, [(rd, p, h) for _, rd, p, h in fb], stream=st)
+            graphs.append(g)
+    torch.cuda.current_stream().wait_stream(st)
+
+    def replay():
+        for g in graphs:
+            g.replay()
+
+    ms_graph = timed(replay, reps)
+    # the same frames with a float16 grid
+    g16 = grid.half()
+    sdf16 = rq.rt_sdf_create(g16, s.lo, s.hi)
+    rq.rt_sdf_prepare(sdf16)
+
+    def batched16():
+        for fb in frames:
+            rq.rt_trace_batches(scene, sdf16, [(rd, p, h) for _, rd, p, h in fb])
+
+    ms_batched16 = timed(batched16, reps)
+    rate = lambda ms: n_total / (ms * 1e-3)  # noqa: E731
+    line = {
+        "metric": "mixed-batch rays/s (primary, shadow, AO, GI per frame)", "value": rate(ms_graph),
+        "unit": UNIT, "n_gpus": 1, "frames": args.frames, "rays_total": n_total, "higher_is_better": True,
+        "data": "synthetic (seeded procedural scene and rays)", "dtype": "f32",
+        "config": {"workload": "frame-mixed-batches", "scene": "frame", "n_tris": int(s.n_tris),
+                   "grid": [n, n, n], "batch_sizes_per_frame": sizes, "input_generation_s": gen_s},
+        "forms": {
+            "one_call_per_batch_default_tuning": {"ms_total": ms_per_batch_default, "value": rate(ms_per_batch_default)},
+            "batched_default_tuning": {"ms_total": ms_batched_default, "value": rate(ms_batched_default)},
+            "one_call_per_batch_autotuned": {"ms_total": ms_per_batch, "value": rate(ms_per_batch)},
+            "batched_autotuned": {"ms_total": ms_batched, "value": rate(ms_batched)},
+            "batched_autotuned_cuda_graph": {"ms_total": ms_graph, "value": rate(ms_graph)},
+            "batched_autotuned_f16_grid": {"ms_total": ms_batched16, "value": rate(ms_batched16)},
+        },
+        "tuning_default": default, "tuning_autotuned": best,
+        "autotune_top5": sorted(([r[1], r[0]] for r in results), key=lambda x: x[0])[:5],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batching":
+        run_batching(args)
     else:
         run_ours(args)
 

@@ -237,6 +237,34 @@ rt_status rt_trace_combined_timed(const rt_scene* scene, const rt_sdf* sdf, cons
 rt_status rt_trace_combined_noalloc(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
                                     const rt_split_params* params, rt_hit* d_hits, void* stream);
 
+/* One batch of queries for rt_trace_batches: its rays, its hit records, its
+ * split parameters. */
+typedef struct {
+    const rt_ray* d_rays;
+    rt_hit* d_hits;
+    int64_t n;
+    rt_split_params params;
+} rt_batch;
+
+enum { RT_MAX_BATCHES = 16 };
+
+/* Several batches of queries in one call, for example the primary, shadow, AO
+ * and GI rays of one frame (Section 3 uses one split for AO and GI rays and two
+ * splits with any-hit for shadow rays).  The result equals one
+ * rt_trace_combined per batch.  All batches run through one pipeline of three
+ * persistent stage launches (triangles, field, triangles): every query follows
+ * its own batch's sub-interval program through it, so uneven batches share the
+ * kernels instead of each paying its own launches and tails, and a frame is a
+ * fixed sequence of launches that can be captured in a CUDA graph.
+ *   - at most RT_MAX_BATCHES batches, at most 2^31-1 queries in total;
+ *   - mode, any_hit, m_near and m_far may differ per batch; max_steps,
+ *     hit_eps_vox, min_step_vox and refine_root must be equal in all batches;
+ *   - always uses the wavefront stage kernels; the tuning's block, residency,
+ *     refill and layout apply.
+ * Errors: RT_ERR_INVALID_ARG before any work for bad batches. */
+rt_status rt_trace_batches(const rt_scene* scene, const rt_sdf* sdf, const rt_batch* batches, int32_t n_batches,
+                           void* stream);
+
 /* Adjoint of the field-resolved hit distance.  For each query whose hit
  * record (from a forward call with the same params, refine_root = 1) has
  * tracer == RT_TRACER_SDF, the root p* = o + t d of phi = eps satisfies

@@ -37,7 +37,7 @@ LAYOUT_CELLS, LAYOUT_PLAIN = 0, 1
 EXPORTS = ("rt_scene_build", "rt_scene_info_get", "rt_scene_destroy", "rt_sdf_create", "rt_sdf_destroy",
            "rt_sdf_prepare", "rt_sdf_bake", "rt_trace_bvh", "rt_trace_sdf", "rt_trace_combined",
            "rt_trace_combined_counted", "rt_trace_combined_timed", "rt_trace_combined_noalloc",
-           "rt_trace_combined_backward", "rt_set_tuning", "rt_get_tuning",
+           "rt_trace_combined_backward", "rt_trace_batches", "rt_set_tuning", "rt_get_tuning",
            "rt_last_error", "rt_version")
 
 
@@ -59,6 +59,14 @@ class rt_tuning(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class rt_batch(ctypes.Structure):
+    _fields_ = [("d_rays", ctypes.c_void_p), ("d_hits", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("params", rt_split_params)]
+
+
+MAX_BATCHES = 16
 
 
 class rt_scene_info(ctypes.Structure):
@@ -98,6 +106,7 @@ def lib() -> ctypes.CDLL:
             "rt_trace_combined_counted": [P, P, P, i64, P, P, P, P],
             "rt_trace_combined_timed": [P, P, P, i64, P, P, P, P, P, P],
             "rt_trace_combined_noalloc": [P, P, P, i64, P, P, P],
+            "rt_trace_batches": [P, P, P, i32, P],
             "rt_trace_combined_backward": [P, P, P, i64, P, P, P, P, P],
         }
         for name, args in sig.items():
@@ -287,6 +296,26 @@ def rt_trace_combined_noalloc(scene: Scene | None, sdf: Sdf | None, rays: torch.
                                            _dptr(rays), rays.shape[0], ctypes.byref(params), _dptr(hits),
                                            _stream(stream)))
     return hits
+
+
+def rt_trace_batches(scene: Scene | None, sdf: Sdf | None, batches, stream=None) -> list:
+    """batches: sequence of (rays, params) or (rays, params, hits); returns the hit tensors.
+    One pipeline of persistent stage launches serves all batches (graph-capturable)."""
+    if len(batches) > MAX_BATCHES:
+        raise ValueError(f"at most {MAX_BATCHES} batches")
+    arr = (rt_batch * max(1, len(batches)))()
+    outs = []
+    for k, bt in enumerate(batches):
+        rays, params = bt[0], bt[1]
+        hits = _rays_hits(rays, bt[2] if len(bt) > 2 else None)
+        outs.append(hits)
+        arr[k].d_rays = rays.data_ptr() if rays.numel() else None
+        arr[k].d_hits = hits.data_ptr() if hits.numel() else None
+        arr[k].n = rays.shape[0]
+        arr[k].params = params
+    _check(lib().rt_trace_batches(scene.handle if scene else None, sdf.handle if sdf else None, arr, len(batches),
+                                  _stream(stream)))
+    return outs
 
 
 STAGE_NAMES = {0: "all", 1: "bvh_full", 2: "bvh_near", 3: "bvh_far", 4: "field_full", 5: "field_split"}

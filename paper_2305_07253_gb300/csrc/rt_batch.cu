@@ -1,0 +1,440 @@
+// Mixed batches in one wavefront pipeline (rt_trace_batches).
+//
+// Each query follows the sub-interval program of its batch (Section 2: closest
+// hit in order with early exit, any hit field first; Section 3: one split for
+// AO/GI rays, two splits for shadow rays):
+//   mode 0            : triangles [t_min, t_max]
+//   mode 3            : field [t_min, t_max]
+//   mode 1, closest   : triangles near, field
+//   mode 1, any hit   : field, triangles near
+//   mode 2, closest   : triangles near, field, triangles far
+//   mode 2, any hit   : field, then triangles near and far
+// The pipeline is three persistent launches -- triangles, field, triangles --
+// which covers every program above.  A query whose next sub-interval is not of
+// a launch's kind passes through it to the next launch's queue.
+#include <mutex>
+
+#include "rt_trace_dev.cuh"
+
+using namespace rtdev;
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBatchTrip = 8;   // traversal iterations between refill checks
+constexpr int kBatchSteps = 4;  // march steps between refill checks
+
+enum Seg { SEG_NONE = 0, SEG_B_FULL, SEG_F_FULL, SEG_B_NEAR, SEG_F_SPLIT, SEG_B_FAR, SEG_B_NEAR_FAR };
+
+struct BatchEntry {
+    const float4* rays;
+    rt_hit* hits;
+    int64_t offset;
+    int32_t mode, any_hit;
+    float m_near, m_far;
+};
+
+struct BatchTable {
+    BatchEntry e[RT_MAX_BATCHES];
+    int32_t count;
+};
+
+struct Pipe {
+    const int2* in_items;     // null: first launch, every query
+    const unsigned* in_count;
+    unsigned n_first;         // total queries (first launch)
+    int2* out_items;          // null: last launch
+    unsigned* out_count;
+    unsigned* fetch;
+    int32_t refill_min;
+};
+
+__device__ __forceinline__ unsigned lane() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ int seg_at(int mode, int any_hit, int p)
+{
+    switch (mode) {
+    case RT_MODE_BVH: return p == 0 ? SEG_B_FULL : SEG_NONE;
+    case RT_MODE_SDF: return p == 0 ? SEG_F_FULL : SEG_NONE;
+    case RT_MODE_SPLIT1:
+        if (any_hit) return p == 0 ? SEG_F_SPLIT : (p == 1 ? SEG_B_NEAR : SEG_NONE);
+        return p == 0 ? SEG_B_NEAR : (p == 1 ? SEG_F_SPLIT : SEG_NONE);
+    default:
+        if (any_hit) return p == 0 ? SEG_F_SPLIT : (p == 1 ? SEG_B_NEAR_FAR : SEG_NONE);
+        return p == 0 ? SEG_B_NEAR : (p == 1 ? SEG_F_SPLIT : (p == 2 ? SEG_B_FAR : SEG_NONE));
+    }
+}
+
+__device__ __forceinline__ bool seg_is_field(int s) { return s == SEG_F_FULL || s == SEG_F_SPLIT; }
+
+__device__ __forceinline__ int find_batch(const BatchTable& tb, int64_t g)
+{
+    int b = 0;
+#pragma unroll
+    for (int k = 1; k < RT_MAX_BATCHES; ++k)
+        if (k < tb.count && tb.e[k].offset <= g) b = k;
+    return b;
+}
+
+// the split of Eq. 2 for this batch's multipliers
+__device__ __forceinline__ Split batch_split(const TraceArgs& a, const BatchEntry& e, float tmin, float tmax)
+{
+    TraceArgs b = a;
+    b.mode = e.mode;
+    b.m_near = e.m_near;
+    b.m_far = e.m_far;
+    return make_split(b, tmin, tmax);
+}
+
+__device__ __forceinline__ void forward_item(const Pipe& pp, bool fwd, int2 item)
+{
+    const unsigned m = __ballot_sync(kFull, fwd);
+    if (m == 0) return;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane() == (unsigned)leader) base = atomicAdd(pp.out_count, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (fwd) pp.out_items[base + __popc(m & ((1u << lane()) - 1u))] = item;
+}
+
+__device__ __forceinline__ void take(const Pipe& pp, unsigned n_in, bool idle, bool& drained, bool& got, unsigned& slot)
+{
+    got = false;
+    const unsigned want = __ballot_sync(kFull, idle && !drained);
+    const unsigned busy = __ballot_sync(kFull, !idle);
+    if (want == 0 || (__popc(want) < pp.refill_min && busy != 0)) return;
+    const int leader = __ffs(want) - 1;
+    unsigned base = 0;
+    if (lane() == (unsigned)leader) base = atomicAdd(pp.fetch, (unsigned)__popc(want));
+    base = __shfl_sync(kFull, base, leader);
+    if (idle && !drained) {
+        const unsigned k = base + __popc(want & ((1u << lane()) - 1u));
+        if (k < n_in) { got = true; slot = k; } else drained = true;
+    }
+}
+
+// queue item: x = global query index, y = flags | (program position << 8)
+__device__ __forceinline__ int2 pack_item(int g, uint32_t flags, int p) { return make_int2(g, (int)(flags | (p << 8))); }
+
+template <bool COUNT>
+__global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe pp)
+{
+    const unsigned n_in = pp.in_items ? *pp.in_count : pp.n_first;
+    int stack[RT_STACK_DEPTH];
+    Counts cnt = {0, 0, 0, 0};
+    bool drained = false, live = false;
+    int g = -1, p = 0, b = 0;
+    int64_t qi = 0;
+    uint32_t flags = 0;
+    bool any_hit = false, far_next = false;
+    float far_a = 0.f, far_b = 0.f;
+    BvhRay r;
+    Trav s;
+    Hit best;
+    for (;;) {
+        bool got;
+        unsigned slot = 0;
+        take(pp, n_in, !live, drained, got, slot);
+        bool done = false, found = false, pass = false;
+        if (got) {
+            const int2 item = pp.in_items ? pp.in_items[slot] : make_int2((int)slot, 0);
+            g = item.x;
+            flags = (uint32_t)item.y & 0xffu;
+            p = (item.y >> 8) & 0xff;
+            b = find_batch(tb, g);
+            const BatchEntry& e = tb.e[b];
+            qi = g - e.offset;
+            const int seg = seg_at(e.mode, e.any_hit, p);
+            const float4 r0 = __ldg(e.rays + 2 * qi), r1 = __ldg(e.rays + 2 * qi + 1);
+            const float3 o = make_float3(r0.x, r0.y, r0.z), d = make_float3(r1.x, r1.y, r1.z);
+            const float tmin = r0.w, tmax = r1.w;
+            if (!pp.in_items && !valid_query(o, d, tmin, tmax)) {
+                done = true;       // invalid: a miss, program over
+                p = 99;
+            } else if (seg_is_field(seg)) {
+                pass = true;       // not this launch's kind
+            } else {
+                float ta = tmin, tb2 = tmax;
+                bool active = true;
+                far_next = false;
+                if (seg != SEG_B_FULL) {
+                    const Split sp = batch_split(a, e, tmin, tmax);
+                    if (seg == SEG_B_NEAR || seg == SEG_B_NEAR_FAR) { ta = tmin; tb2 = sp.t1; active = sp.near_bvh; }
+                    else { ta = sp.t2; tb2 = tmax; active = sp.far_bvh; }
+                    if (seg == SEG_B_NEAR_FAR && sp.far_bvh) { far_next = true; far_a = sp.t2; far_b = tmax; }
+                    if (!active && far_next) { ta = far_a; tb2 = far_b; active = true; far_next = false; }
+                }
+                any_hit = e.any_hit != 0;
+                if (active && ta <= tb2 && a.root != INT32_MIN) {
+                    r = bvh_ray(o, d);
+                    s = trav_begin(a.root, ta, tb2);
+                    best.prim = -1;
+                    live = true;
+                } else {
+                    done = true;
+                }
+            }
+        } else if (live) {
+            if (trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt, kBatchTrip)) {
+                if (!s.found && far_next && a.root != INT32_MIN && far_a <= far_b) {
+                    s = trav_begin(a.root, far_a, far_b);  // any hit: the far triangles after the near ones
+                    best.prim = -1;
+                    far_next = false;
+                } else {
+                    done = true;
+                    found = s.found;
+                    live = false;
+                }
+            }
+        }
+        // after a miss the query moves to its next sub-interval, if any
+        const BatchEntry& e = tb.e[b];
+        const int next_p = pass ? p : p + 1;
+        const bool more = (pass || (done && !found)) && seg_at(e.mode, e.any_hit, next_p) != SEG_NONE;
+        const bool fwd = more && pp.out_items != nullptr;
+        forward_item(pp, fwd, pack_item(g, flags, next_p));
+        if ((done || pass) && !fwd) {
+            if (found) store_hit(e.hits + qi, best.t, best.prim, best.u, best.v, RT_TRACER_BVH, flags);
+            else store_hit(e.hits + qi, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
+        }
+        if (__ballot_sync(kFull, live || !drained) == 0) break;
+    }
+    if (COUNT) {
+        if (cnt.nodes) atomicAdd(&a.counters[0], (unsigned long long)cnt.nodes);
+        if (cnt.tris) atomicAdd(&a.counters[1], (unsigned long long)cnt.tris);
+    }
+}
+
+template <bool COUNT, int L>
+__global__ void k_batch_field(const TraceArgs a, const BatchTable tb, const Pipe pp)
+{
+    const unsigned n_in = pp.in_items ? *pp.in_count : pp.n_first;
+    Counts cnt = {0, 0, 0, 0};
+    bool drained = false, live = false;
+    int g = -1, p = 0, b = 0, k = 0;
+    int64_t qi = 0;
+    uint32_t flags = 0;
+    float3 o = make_float3(0.f, 0.f, 0.f), d = o;
+    float t = 0.f, tb2 = 0.f, t_prev = 0.f;
+    for (;;) {
+        bool got;
+        unsigned slot = 0;
+        take(pp, n_in, !live, drained, got, slot);
+        bool done = false, found = false, pass = false;
+        if (got) {
+            const int2 item = pp.in_items ? pp.in_items[slot] : make_int2((int)slot, 0);
+            g = item.x;
+            flags = (uint32_t)item.y & 0xffu;
+            p = (item.y >> 8) & 0xff;
+            b = find_batch(tb, g);
+            const BatchEntry& e = tb.e[b];
+            qi = g - e.offset;
+            const int seg = seg_at(e.mode, e.any_hit, p);
+            const float4 r0 = __ldg(e.rays + 2 * qi), r1 = __ldg(e.rays + 2 * qi + 1);
+            o = make_float3(r0.x, r0.y, r0.z);
+            d = make_float3(r1.x, r1.y, r1.z);
+            const float tmin = r0.w, tmax = r1.w;
+            if (!pp.in_items && !valid_query(o, d, tmin, tmax)) {
+                done = true;
+                p = 99;
+            } else if (!seg_is_field(seg)) {
+                pass = true;
+            } else {
+                float ta = tmin;
+                tb2 = tmax;
+                bool active = true;
+                if (seg == SEG_F_SPLIT) {
+                    const Split sp = batch_split(a, e, tmin, tmax);
+                    ta = sp.t1;
+                    tb2 = sp.t2;
+                    active = sp.field;
+                }
+                if (active && clip_grid(a, o, d, ta, tb2)) {
+                    if (COUNT) ++cnt.field;
+                    t = ta;
+                    t_prev = __int_as_float(0x7fc00000);
+                    k = 0;
+                    live = true;
+                } else {
+                    done = true;
+                }
+            }
+        } else if (live) {
+            for (int it = 0; it < kBatchSteps; ++it) {
+                if (COUNT) ++cnt.steps;
+                const int res = march_step<L>(a, o, d, t, tb2, t_prev);
+                ++k;
+                if (res == 1) { done = true; found = true; }
+                else if (res == 2) done = true;
+                else if (k >= a.max_steps) { flags |= RT_FLAG_STEP_LIMIT; done = true; }
+                if (done) break;
+            }
+            if (done) live = false;
+        }
+        const BatchEntry& e = tb.e[b];
+        const int next_p = pass ? p : p + 1;
+        const bool more = (pass || (done && !found)) && seg_at(e.mode, e.any_hit, next_p) != SEG_NONE;
+        const bool fwd = more && pp.out_items != nullptr;
+        forward_item(pp, fwd, pack_item(g, flags, next_p));
+        if ((done || pass) && !fwd) {
+            if (found) {
+                const float th = (a.refine_root && !isnan(t_prev)) ? refine<L>(a, o, d, t_prev, t) : t;
+                store_hit(e.hits + qi, th, -1, 0.f, 0.f, RT_TRACER_SDF, flags);
+            } else {
+                store_hit(e.hits + qi, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
+            }
+        }
+        if (__ballot_sync(kFull, live || !drained) == 0) break;
+    }
+    if (COUNT) {
+        if (cnt.steps) atomicAdd(&a.counters[2], (unsigned long long)cnt.steps);
+        if (cnt.field) atomicAdd(&a.counters[3], (unsigned long long)cnt.field);
+    }
+}
+
+struct BatchDevice {
+    int sms = 0;
+    cudaMemPool_t pool = nullptr;
+};
+std::mutex g_bmu;
+BatchDevice g_bdev[64];
+
+rt_status batch_device(BatchDevice*& out)
+{
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return rt_fail(RT_ERR_INVALID_ARG, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_bmu);
+    BatchDevice& d = g_bdev[dev];
+    if (d.sms == 0) {
+        RT_CUDA_TRY(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        RT_CUDA_TRY(cudaMemPoolCreate(&d.pool, &props));
+        uint64_t keep = ~0ull;
+        RT_CUDA_TRY(cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    out = &d;
+    return RT_OK;
+}
+
+template <class K>
+int grid_for(K kernel, const rt_tuning& tu, int sms)
+{
+    int per_sm = tu.blocks_per_sm;
+    if (per_sm <= 0) {
+        int fit = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, tu.block, 0) != cudaSuccess || fit < 1) fit = 1;
+        per_sm = fit;
+    }
+    return sms * per_sm;
+}
+
+}  // namespace
+
+extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, const rt_batch* batches, int32_t n_batches,
+                                      void* stream)
+{
+    if (!batches && n_batches > 0) return rt_fail(RT_ERR_INVALID_ARG, "batches is null");
+    if (n_batches < 0 || n_batches > RT_MAX_BATCHES)
+        return rt_fail(RT_ERR_INVALID_ARG, "n_batches %d not in 0..%d", n_batches, RT_MAX_BATCHES);
+    BatchTable tb = {};
+    int64_t total = 0;
+    bool need_scene = false, need_grid = false;
+    const rt_split_params* p0 = nullptr;
+    for (int k = 0; k < n_batches; ++k) {
+        const rt_batch& bt = batches[k];
+        const rt_split_params& p = bt.params;
+        if (p.mode < 0 || p.mode > 3) return rt_fail(RT_ERR_INVALID_ARG, "batch %d: mode %d", k, p.mode);
+        if (!(p.m_near >= 0.f) || !(p.m_far >= 0.f)) return rt_fail(RT_ERR_INVALID_ARG, "batch %d: negative multiplier", k);
+        if (p.any_hit != 0 && p.any_hit != 1) return rt_fail(RT_ERR_INVALID_ARG, "batch %d: any_hit", k);
+        if (p.max_steps < 1 || !(p.hit_eps_vox >= 0.f) || !(p.min_step_vox > 0.f) || isinf(p.hit_eps_vox) ||
+            isinf(p.min_step_vox))
+            return rt_fail(RT_ERR_INVALID_ARG, "batch %d: bad march parameters", k);
+        if (bt.n < 0) return rt_fail(RT_ERR_INVALID_ARG, "batch %d: n < 0", k);
+        if (bt.n > 0 && (!bt.d_rays || !bt.d_hits)) return rt_fail(RT_ERR_INVALID_ARG, "batch %d: null buffer", k);
+        if (((uintptr_t)bt.d_rays & 15u) || ((uintptr_t)bt.d_hits & 7u))
+            return rt_fail(RT_ERR_INVALID_ARG, "batch %d: misaligned buffer", k);
+        if (!p0) p0 = &p;
+        else if (p.max_steps != p0->max_steps || p.hit_eps_vox != p0->hit_eps_vox ||
+                 p.min_step_vox != p0->min_step_vox || p.refine_root != p0->refine_root)
+            return rt_fail(RT_ERR_INVALID_ARG, "batch %d: march parameters differ from batch 0", k);
+        need_scene |= p.mode != RT_MODE_SDF;
+        need_grid |= p.mode != RT_MODE_BVH;
+        tb.e[k].rays = reinterpret_cast<const float4*>(bt.d_rays);
+        tb.e[k].hits = bt.d_hits;
+        tb.e[k].offset = total;
+        tb.e[k].mode = p.mode;
+        tb.e[k].any_hit = p.any_hit;
+        tb.e[k].m_near = p.m_near;
+        tb.e[k].m_far = p.m_far;
+        total += bt.n;
+    }
+    tb.count = n_batches;
+    if (total > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "more than 2^31-1 queries");
+    if (need_scene && !sc) return rt_fail(RT_ERR_INVALID_ARG, "a batch needs the scene");
+    if (need_grid && !sdf) return rt_fail(RT_ERR_INVALID_ARG, "a batch needs the grid");
+    if (total == 0) return RT_OK;
+    int cur = -1;
+    RT_CUDA_TRY(cudaGetDevice(&cur));
+    if (sc && sc->device != cur) return rt_fail(RT_ERR_INVALID_ARG, "scene belongs to another device");
+    BatchDevice* dev = nullptr;
+    rt_status st = batch_device(dev);
+    if (st != RT_OK) return st;
+
+    TraceArgs a;
+    rt_fill_trace_args(a, need_scene ? sc : nullptr, need_grid ? sdf : nullptr, p0);
+    const rt_tuning& tu = rt_current_tuning();
+    if (tu.grid_layout == RT_LAYOUT_PLAIN) a.cells = nullptr;
+    a.n = total;
+    a.counters = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    const size_t ctr_bytes = 256, qbytes = (size_t)total * sizeof(int2);
+    void* scratch = nullptr;
+    RT_CUDA_TRY(cudaMallocFromPoolAsync(&scratch, ctr_bytes + 2 * qbytes, dev->pool, s));
+    unsigned* ctr = static_cast<unsigned*>(scratch);
+    int2* q[2] = {reinterpret_cast<int2*>(static_cast<char*>(scratch) + ctr_bytes),
+                  reinterpret_cast<int2*>(static_cast<char*>(scratch) + ctr_bytes + qbytes)};
+    rt_status rs = RT_OK;
+    cudaError_t e = cudaMemsetAsync(ctr, 0, ctr_bytes, s);
+    if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaMemsetAsync");
+    // launches: triangles, field, triangles
+    for (int k = 0; k < 3 && rs == RT_OK; ++k) {
+        Pipe pp;
+        pp.in_items = k > 0 ? q[(k - 1) & 1] : nullptr;
+        pp.in_count = k > 0 ? &ctr[3 + ((k - 1) & 1)] : nullptr;
+        pp.n_first = (unsigned)total;
+        pp.out_items = k < 2 ? q[k & 1] : nullptr;
+        pp.out_count = k < 2 ? &ctr[3 + (k & 1)] : nullptr;
+        pp.fetch = &ctr[k];
+        pp.refill_min = tu.refill_min;
+        if (k == 1 && need_grid) {
+            switch (grid_layout_of(a)) {
+#define RT_BATCH_FIELD(LL)                                                                            \
+    case LL:                                                                                          \
+        k_batch_field<false, LL><<<grid_for(k_batch_field<false, LL>, tu, dev->sms), tu.block, 0, s>>>(a, tb, pp); \
+        break;
+                RT_BATCH_FIELD(GL_PLAIN_F32)
+                RT_BATCH_FIELD(GL_PLAIN_F16)
+                RT_BATCH_FIELD(GL_CELLS_F32)
+                RT_BATCH_FIELD(GL_CELLS_F16)
+#undef RT_BATCH_FIELD
+            }
+        } else if (k == 1) {
+            // no batch uses the field: pass everything through an empty field launch
+            k_batch_field<false, GL_PLAIN_F32><<<grid_for(k_batch_field<false, GL_PLAIN_F32>, tu, dev->sms), tu.block, 0, s>>>(
+                a, tb, pp);
+        } else {
+            k_batch_bvh<false><<<grid_for(k_batch_bvh<false>, tu, dev->sms), tu.block, 0, s>>>(a, tb, pp);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rs = rt_cuda_fail(e, "stage launch");
+    }
+    e = cudaFreeAsync(scratch, s);
+    if (rs == RT_OK && e != cudaSuccess) rs = rt_cuda_fail(e, "cudaFreeAsync");
+    return rs;
+}

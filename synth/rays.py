@@ -98,58 +98,99 @@ def cosine_hemisphere(n: np.ndarray, u1: np.ndarray, u2: np.ndarray) -> np.ndarr
 
 
 def _surface_frame(scene: Scene):
+    """Per-triangle corner, edges, unit normal and area CDF (cached on the scene)."""
+    cached = getattr(scene, "_surface_frame_cache", None)
+    if cached is not None:
+        return cached
     V = scene.verts.astype(np.float64)
     F = scene.tris
-    e1 = V[F[:, 1]] - V[F[:, 0]]
-    e2 = V[F[:, 2]] - V[F[:, 0]]
-    cr = np.cross(e1, e2)
+    A = V[F[:, 0]]
+    E1 = V[F[:, 1]] - A
+    E2 = V[F[:, 2]] - A
+    cr = np.cross(E1, E2)
     area2 = np.linalg.norm(cr, axis=1)
     nrm = cr / np.maximum(area2, 1e-300)[:, None]
     cdf = np.cumsum(area2)
     cdf /= cdf[-1]
-    return V, F, nrm, cdf
+    out = (A, E1, E2, nrm, cdf)
+    scene._surface_frame_cache = out
+    return out
 
 
-def gi_rays(scene: Scene, n: int, seed: int, t_max: float, bias_frac: float = 1e-3,
-            width: int | None = None, height: int | None = None) -> np.ndarray:
-    """n GI rays from camera-facing, in-frustum surface points, tile-ordered."""
+def surface_points(scene: Scene, n: int, seed: int, stream: int = _S_GI_POS, width: int | None = None,
+                   height: int | None = None):
+    """n points on camera-facing triangle surfaces inside the view frustum, chosen
+    uniformly by area, returned in 8x8 screen-tile order: (points, unit normals)."""
     cam = scene.camera
     W = width or cam.width
     H = height or cam.height
-    V, F, nrm, cdf = _surface_frame(scene)
+    A, E1, E2, nrm, cdf = _surface_frame(scene)
     aspect = W / H
-    got_p, got_n, got_px, got_py = [], [], [], []
+    got = []
     have = 0
     offset = 0
     while have < n:
-        m = max(4 * (n - have), 1024)
-        u = rng.uniform(seed, _S_GI_POS, 3 * m, offset).reshape(m, 3)
-        offset += 3 * m
-        tri = np.minimum(np.searchsorted(cdf, u[:, 0], side="right"), F.shape[0] - 1)
+        m = max(4 * (n - have), 4096)
+        u = rng.uniform(seed, stream, 4 * m, offset).reshape(m, 4)
+        offset += 4 * m
+        # candidates in triangle order: sorted lookups into the area CDF
+        tri = np.minimum(np.searchsorted(cdf, np.sort(u[:, 0]), side="right"), cdf.size - 1)
         s1 = np.sqrt(u[:, 1])
-        b0, b1, b2 = 1 - s1, s1 * (1 - u[:, 2]), s1 * u[:, 2]
-        p = b0[:, None] * V[F[tri, 0]] + b1[:, None] * V[F[tri, 1]] + b2[:, None] * V[F[tri, 2]]
+        b1, b2 = s1 * (1 - u[:, 2]), s1 * u[:, 2]
+        p = A[tri] + b1[:, None] * E1[tri] + b2[:, None] * E2[tri]
         nn = nrm[tri]
         q = p - cam.eye
         z = q @ cam.forward
         zs = np.maximum(z, 1e-9)
         x = (q @ cam.right) / (zs * cam.tan_half_fov * aspect)
         y = (q @ cam.up) / (zs * cam.tan_half_fov)
-        keep = (np.einsum("ij,ij->i", nn, -q) > 0) & (z > 0.05) & (np.abs(x) < 1) & (np.abs(y) < 1)
-        idx = np.nonzero(keep)[0][: n - have]
-        got_p.append(p[idx])
-        got_n.append(nn[idx])
-        got_px.append(np.minimum(((x[idx] + 1) * 0.5 * W).astype(np.int64), W - 1))
-        got_py.append(np.minimum(((1 - y[idx]) * 0.5 * H).astype(np.int64), H - 1))
+        keep = (np.einsum("ij,ij->i", nn, q) < 0) & (z > 0.05) & (np.abs(x) < 1) & (np.abs(y) < 1)
+        idx = np.nonzero(keep)[0]
+        # an unbiased subset of the accepted candidates, chosen by their own random key
+        if idx.size > n - have:
+            idx = idx[np.argpartition(u[idx, 3], n - have - 1)[: n - have]]
+        px = np.minimum(((x[idx] + 1) * 0.5 * W).astype(np.int64), W - 1)
+        py = np.minimum(((1 - y[idx]) * 0.5 * H).astype(np.int64), H - 1)
+        got.append((p[idx], nn[idx], px, py))
         have += idx.size
-    p = np.concatenate(got_p)
-    nn = np.concatenate(got_n)
-    order = _tile_order(np.concatenate(got_px), np.concatenate(got_py), W)
-    p, nn = p[order], nn[order]
+    p = np.concatenate([g[0] for g in got])
+    nn = np.concatenate([g[1] for g in got])
+    order = _tile_order(np.concatenate([g[2] for g in got]), np.concatenate([g[3] for g in got]), W)
+    return p[order], nn[order]
+
+
+def gi_rays(scene: Scene, n: int, seed: int, t_max: float, bias_frac: float = 1e-3,
+            width: int | None = None, height: int | None = None) -> np.ndarray:
+    """n GI rays from camera-facing, in-frustum surface points, tile-ordered."""
+    p, nn = surface_points(scene, n, seed, _S_GI_POS, width, height)
     u = rng.uniform(seed, _S_GI_DIR, 2 * n).reshape(n, 2)
     d = cosine_hemisphere(nn, u[:, 0], u[:, 1])
     o = p + (bias_frac * scene.diagonal) * nn
     return _renorm(pack(o, d, 0.0, t_max))
+
+
+def ao_rays(p: np.ndarray, nn: np.ndarray, per_point: np.ndarray, seed: int, t_ao: float,
+            bias: float) -> np.ndarray:
+    """AO rays (Section 3, occlusion queries): per_point[i] cosine-weighted rays
+    from surface point i, t in [0, t_ao]."""
+    rep = np.repeat(np.arange(p.shape[0]), per_point)
+    m = rep.size
+    u = rng.uniform(seed, _S_AO, 2 * m).reshape(m, 2)
+    d = cosine_hemisphere(nn[rep], u[:, 0], u[:, 1])
+    o = p[rep] + bias * nn[rep]
+    return _renorm(pack(o, d, 0.0, t_ao))
+
+
+def shadow_rays(p: np.ndarray, nn: np.ndarray, lights: np.ndarray, seed: int, bias: float) -> np.ndarray:
+    """Shadow rays (Section 3, GI & shadow rays): from each surface point toward one
+    of the point lights picked at random, t in [0, distance - bias]."""
+    m = p.shape[0]
+    pick = (rng.uniform(seed, _S_SHADOW, m) * lights.shape[0]).astype(np.int64)
+    o = p + bias * nn
+    d = lights[pick] - o
+    dist = np.linalg.norm(d, axis=1)
+    d /= np.maximum(dist, 1e-12)[:, None]
+    return _renorm(pack(o, d, 0.0, np.maximum(dist - bias, 0.0)))
 
 
 def free_space_rays(scene: Scene, n: int, seed: int, margin: float, t_max: float | None = None) -> np.ndarray:

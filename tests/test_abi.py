@@ -46,6 +46,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(rq.rt_split_params) == 32
     assert ctypes.sizeof(rq.rt_scene_info) == 8 * 3 + 4 * 2 + 4 * 6 + 8
     assert ctypes.sizeof(rq.rt_tuning) == 20
+    assert ctypes.sizeof(rq.rt_batch) == 8 * 3 + 32
 
 
 def test_tuning_roundtrip_and_validation(rtlib):

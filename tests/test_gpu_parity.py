@@ -402,3 +402,86 @@ def test_timed_variant_reports_each_launch(tiny):
     finally:
         rq.rt_set_tuning(prev)
     assert torch.equal(a, c) and [x[0] for x in st] == ["all"]
+
+
+def _mixed_batches(w, rq):
+    s = w.s
+    prim = R.primary_rays(s)
+    p, nn = R.surface_points(s, 3000, 61)
+    bias = 1e-3 * s.diagonal
+    gi = R.gi_rays(s, 2500, 62, s.diagonal)
+    ao = R.ao_rays(p, nn, np.random.default_rng(1).integers(1, 5, size=p.shape[0]), 63, 0.5, bias)
+    lights = np.random.default_rng(2).uniform(0.3, np.array(s.room) - 0.3, size=(4, 3))
+    sh = R.shadow_rays(p, nn, lights, 64, bias)
+    mk = lambda **kw: rq.split_params(**kw)  # noqa: E731
+    return [
+        (prim, mk(mode=rq.MODE_BVH)),
+        (gi, mk(mode=rq.MODE_SPLIT1, m_near=2.0)),
+        (ao, mk(mode=rq.MODE_SPLIT1, m_near=2.0)),
+        (sh, mk(mode=rq.MODE_SPLIT2, m_near=2.0, m_far=2.0, any_hit=True)),
+        (gi[:1000], mk(mode=rq.MODE_SPLIT2, m_near=1.0, m_far=3.0)),
+        (gi[:777], mk(mode=rq.MODE_SPLIT1, m_near=2.0, any_hit=True)),
+        (gi[:0], mk(mode=rq.MODE_SDF)),
+        (gi[:555], mk(mode=rq.MODE_SDF)),
+    ]
+
+
+def test_batches_equal_one_call_per_batch(tiny, tuning):
+    rq = tiny.rq
+    batches = [(_cuda(r), p) for r, p in _mixed_batches(tiny, rq)]
+    outs = rq.rt_trace_batches(tiny.scene, tiny.sdf, batches)
+    for (rays, p), got in zip(batches, outs):
+        ref = rq.rt_trace_combined(tiny.scene, tiny.sdf, rays, p)
+        if p.any_hit:
+            assert torch.equal(got[:, 4] > 0, ref[:, 4] > 0)
+            assert torch.equal(got[:, 4] == rq.TRACER_SDF, ref[:, 4] == rq.TRACER_SDF)
+        else:
+            assert torch.equal(got, ref), (p.mode, p.m_near)
+
+
+def test_batches_replay_in_a_cuda_graph(tiny):
+    rq = tiny.rq
+    batches = [(_cuda(r), p) for r, p in _mixed_batches(tiny, rq)]
+    hits = [torch.empty((r.shape[0], 6), dtype=torch.int32, device="cuda") for r, _ in batches]
+    with_hits = [(r, p, h) for (r, p), h in zip(batches, hits)]
+    rq.rt_trace_batches(tiny.scene, tiny.sdf, with_hits)  # first call sets up pools outside the capture
+    ref = [h.clone() for h in hits]
+    for h in hits:
+        h.fill_(-1)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            rq.rt_trace_batches(tiny.scene, tiny.sdf, with_hits, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(3):
+        for h in hits:
+            h.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(hits, ref):
+            assert torch.equal(a, b)
+
+
+def test_batches_reject_mixed_march_parameters(tiny):
+    rq = tiny.rq
+    r = tiny.rays_d[:10]
+    with pytest.raises(rq.RtError):
+        rq.rt_trace_batches(tiny.scene, tiny.sdf, [(r, rq.split_params(max_steps=100)),
+                                                   (r, rq.split_params(max_steps=200))])
+
+
+def test_autotuner_picks_a_valid_tuning(tiny):
+    from paper_2305_07253_gb300 import autotune
+    rq = tiny.rq
+    p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=2.0)
+    space = autotune.default_space()[::7]
+    prev = rq.rt_get_tuning()
+    try:
+        best, results = autotune.autotune(lambda: rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p),
+                                          space=space, reps=2, warmup=1)
+        assert len(results) == len(space) and all(ms > 0 for _, ms in results)
+        assert rq.rt_get_tuning().as_dict() == best
+    finally:
+        rq.rt_set_tuning(prev)
