@@ -251,8 +251,8 @@ enum { RT_MAX_BATCHES = 16 };
 /* Several batches of queries in one call, for example the primary, shadow, AO
  * and GI rays of one frame (Section 3 uses one split for AO and GI rays and two
  * splits with any-hit for shadow rays).  The result equals one
- * rt_trace_combined per batch.  All batches run through one pipeline of three
- * persistent stage launches (triangles, field, triangles): every query follows
+ * rt_trace_combined per batch.  All batches run through one pipeline of four
+ * persistent stage launches (triangles, field, triangles, triangles): every query follows
  * its own batch's sub-interval program through it, so uneven batches share the
  * kernels instead of each paying its own launches and tails, and a frame is a
  * fixed sequence of launches that can be captured in a CUDA graph.

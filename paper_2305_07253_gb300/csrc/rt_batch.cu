@@ -8,9 +8,9 @@
 //   mode 1, closest   : triangles near, field
 //   mode 1, any hit   : field, triangles near
 //   mode 2, closest   : triangles near, field, triangles far
-//   mode 2, any hit   : field, then triangles near and far
-// The pipeline is three persistent launches -- triangles, field, triangles --
-// which covers every program above.  A query whose next sub-interval is not of
+//   mode 2, any hit   : field, triangles near, triangles far
+// The pipeline is four persistent launches -- triangles, field, triangles,
+// triangles -- which covers every program above.  A query whose next sub-interval is not of
 // a launch's kind passes through it to the next launch's queue.
 #include <mutex>
 
@@ -24,7 +24,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBatchTrip = 8;   // traversal iterations between refill checks
 constexpr int kBatchSteps = 4;  // march steps between refill checks
 
-enum Seg { SEG_NONE = 0, SEG_B_FULL, SEG_F_FULL, SEG_B_NEAR, SEG_F_SPLIT, SEG_B_FAR, SEG_B_NEAR_FAR };
+enum Seg { SEG_NONE = 0, SEG_B_FULL, SEG_F_FULL, SEG_B_NEAR, SEG_F_SPLIT, SEG_B_FAR };
+constexpr int kLaunches = 4;  // triangles, field, triangles, triangles
 
 struct BatchEntry {
     const float4* rays;
@@ -60,30 +61,28 @@ __device__ __forceinline__ int seg_at(int mode, int any_hit, int p)
         if (any_hit) return p == 0 ? SEG_F_SPLIT : (p == 1 ? SEG_B_NEAR : SEG_NONE);
         return p == 0 ? SEG_B_NEAR : (p == 1 ? SEG_F_SPLIT : SEG_NONE);
     default:
-        if (any_hit) return p == 0 ? SEG_F_SPLIT : (p == 1 ? SEG_B_NEAR_FAR : SEG_NONE);
+        if (any_hit) return p == 0 ? SEG_F_SPLIT : (p == 1 ? SEG_B_NEAR : (p == 2 ? SEG_B_FAR : SEG_NONE));
         return p == 0 ? SEG_B_NEAR : (p == 1 ? SEG_F_SPLIT : (p == 2 ? SEG_B_FAR : SEG_NONE));
     }
 }
 
 __device__ __forceinline__ bool seg_is_field(int s) { return s == SEG_F_FULL || s == SEG_F_SPLIT; }
 
-__device__ __forceinline__ int find_batch(const BatchTable& tb, int64_t g)
+// the batch table, staged in shared memory once per block (lanes index it freely)
+__device__ __forceinline__ void stage_table(const BatchTable& tb, BatchEntry* stb)
 {
-    int b = 0;
-#pragma unroll
-    for (int k = 1; k < RT_MAX_BATCHES; ++k)
-        if (k < tb.count && tb.e[k].offset <= g) b = k;
-    return b;
+    for (int k = threadIdx.x; k < tb.count; k += blockDim.x) stb[k] = tb.e[k];
+    __syncthreads();
 }
 
-// the split of Eq. 2 for this batch's multipliers
-__device__ __forceinline__ Split batch_split(const TraceArgs& a, const BatchEntry& e, float tmin, float tmax)
+__device__ __forceinline__ int find_batch(const BatchEntry* stb, int count, int64_t g)
 {
-    TraceArgs b = a;
-    b.mode = e.mode;
-    b.m_near = e.m_near;
-    b.m_far = e.m_far;
-    return make_split(b, tmin, tmax);
+    int lo = 0, hi = count - 1;  // last batch whose offset <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (stb[mid].offset <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 __device__ __forceinline__ void forward_item(const Pipe& pp, bool fwd, int2 item)
@@ -119,15 +118,18 @@ __device__ __forceinline__ int2 pack_item(int g, uint32_t flags, int p) { return
 template <bool COUNT>
 __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe pp)
 {
+    __shared__ BatchEntry stb[RT_MAX_BATCHES];
+    stage_table(tb, stb);
     const unsigned n_in = pp.in_items ? *pp.in_count : pp.n_first;
+    rt_hit* hits = nullptr;  // this lane's batch output
+    bool has_next = false;   // the query's program continues after this sub-interval
     int stack[RT_STACK_DEPTH];
     Counts cnt = {0, 0, 0, 0};
     bool drained = false, live = false;
     int g = -1, p = 0, b = 0;
     int64_t qi = 0;
     uint32_t flags = 0;
-    bool any_hit = false, far_next = false;
-    float far_a = 0.f, far_b = 0.f;
+    bool any_hit = false;
     BvhRay r;
     Trav s;
     Hit best;
@@ -141,28 +143,28 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
             g = item.x;
             flags = (uint32_t)item.y & 0xffu;
             p = (item.y >> 8) & 0xff;
-            b = find_batch(tb, g);
-            const BatchEntry& e = tb.e[b];
+            b = find_batch(stb, tb.count, g);
+            const BatchEntry e = stb[b];
             qi = g - e.offset;
+            hits = e.hits;
             const int seg = seg_at(e.mode, e.any_hit, p);
             const float4 r0 = __ldg(e.rays + 2 * qi), r1 = __ldg(e.rays + 2 * qi + 1);
             const float3 o = make_float3(r0.x, r0.y, r0.z), d = make_float3(r1.x, r1.y, r1.z);
             const float tmin = r0.w, tmax = r1.w;
+            has_next = false;
             if (!pp.in_items && !valid_query(o, d, tmin, tmax)) {
                 done = true;       // invalid: a miss, program over
-                p = 99;
             } else if (seg_is_field(seg)) {
-                pass = true;       // not this launch's kind
+                pass = true;       // not this launch's kind: hand on unchanged
+                has_next = true;
             } else {
+                has_next = seg_at(e.mode, e.any_hit, p + 1) != SEG_NONE;
                 float ta = tmin, tb2 = tmax;
                 bool active = true;
-                far_next = false;
                 if (seg != SEG_B_FULL) {
-                    const Split sp = batch_split(a, e, tmin, tmax);
-                    if (seg == SEG_B_NEAR || seg == SEG_B_NEAR_FAR) { ta = tmin; tb2 = sp.t1; active = sp.near_bvh; }
+                    const Split sp = make_split(e.mode, e.m_near, e.m_far, a.hsplit, tmin, tmax);
+                    if (seg == SEG_B_NEAR) { ta = tmin; tb2 = sp.t1; active = sp.near_bvh; }
                     else { ta = sp.t2; tb2 = tmax; active = sp.far_bvh; }
-                    if (seg == SEG_B_NEAR_FAR && sp.far_bvh) { far_next = true; far_a = sp.t2; far_b = tmax; }
-                    if (!active && far_next) { ta = far_a; tb2 = far_b; active = true; far_next = false; }
                 }
                 any_hit = e.any_hit != 0;
                 if (active && ta <= tb2 && a.root != INT32_MIN) {
@@ -176,26 +178,18 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
             }
         } else if (live) {
             if (trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt, kBatchTrip)) {
-                if (!s.found && far_next && a.root != INT32_MIN && far_a <= far_b) {
-                    s = trav_begin(a.root, far_a, far_b);  // any hit: the far triangles after the near ones
-                    best.prim = -1;
-                    far_next = false;
-                } else {
-                    done = true;
-                    found = s.found;
-                    live = false;
-                }
+                live = false;
+                done = true;
+                found = s.found;
             }
         }
         // after a miss the query moves to its next sub-interval, if any
-        const BatchEntry& e = tb.e[b];
-        const int next_p = pass ? p : p + 1;
-        const bool more = (pass || (done && !found)) && seg_at(e.mode, e.any_hit, next_p) != SEG_NONE;
+        const bool more = (pass || (done && !found)) && has_next;
         const bool fwd = more && pp.out_items != nullptr;
-        forward_item(pp, fwd, pack_item(g, flags, next_p));
+        forward_item(pp, fwd, pack_item(g, flags, pass ? p : p + 1));
         if ((done || pass) && !fwd) {
-            if (found) store_hit(e.hits + qi, best.t, best.prim, best.u, best.v, RT_TRACER_BVH, flags);
-            else store_hit(e.hits + qi, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
+            if (found) store_hit(hits + qi, best.t, best.prim, best.u, best.v, RT_TRACER_BVH, flags);
+            else store_hit(hits + qi, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
         }
         if (__ballot_sync(kFull, live || !drained) == 0) break;
     }
@@ -208,7 +202,11 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
 template <bool COUNT, int L>
 __global__ void k_batch_field(const TraceArgs a, const BatchTable tb, const Pipe pp)
 {
+    __shared__ BatchEntry stb[RT_MAX_BATCHES];
+    stage_table(tb, stb);
     const unsigned n_in = pp.in_items ? *pp.in_count : pp.n_first;
+    rt_hit* hits = nullptr;
+    bool has_next = false;
     Counts cnt = {0, 0, 0, 0};
     bool drained = false, live = false;
     int g = -1, p = 0, b = 0, k = 0;
@@ -226,25 +224,28 @@ __global__ void k_batch_field(const TraceArgs a, const BatchTable tb, const Pipe
             g = item.x;
             flags = (uint32_t)item.y & 0xffu;
             p = (item.y >> 8) & 0xff;
-            b = find_batch(tb, g);
-            const BatchEntry& e = tb.e[b];
+            b = find_batch(stb, tb.count, g);
+            const BatchEntry e = stb[b];
             qi = g - e.offset;
+            hits = e.hits;
             const int seg = seg_at(e.mode, e.any_hit, p);
             const float4 r0 = __ldg(e.rays + 2 * qi), r1 = __ldg(e.rays + 2 * qi + 1);
             o = make_float3(r0.x, r0.y, r0.z);
             d = make_float3(r1.x, r1.y, r1.z);
             const float tmin = r0.w, tmax = r1.w;
+            has_next = false;
             if (!pp.in_items && !valid_query(o, d, tmin, tmax)) {
                 done = true;
-                p = 99;
             } else if (!seg_is_field(seg)) {
                 pass = true;
+                has_next = true;
             } else {
+                has_next = seg_at(e.mode, e.any_hit, p + 1) != SEG_NONE;
                 float ta = tmin;
                 tb2 = tmax;
                 bool active = true;
                 if (seg == SEG_F_SPLIT) {
-                    const Split sp = batch_split(a, e, tmin, tmax);
+                    const Split sp = make_split(e.mode, e.m_near, e.m_far, a.hsplit, tmin, tmax);
                     ta = sp.t1;
                     tb2 = sp.t2;
                     active = sp.field;
@@ -271,17 +272,15 @@ __global__ void k_batch_field(const TraceArgs a, const BatchTable tb, const Pipe
             }
             if (done) live = false;
         }
-        const BatchEntry& e = tb.e[b];
-        const int next_p = pass ? p : p + 1;
-        const bool more = (pass || (done && !found)) && seg_at(e.mode, e.any_hit, next_p) != SEG_NONE;
+        const bool more = (pass || (done && !found)) && has_next;
         const bool fwd = more && pp.out_items != nullptr;
-        forward_item(pp, fwd, pack_item(g, flags, next_p));
+        forward_item(pp, fwd, pack_item(g, flags, pass ? p : p + 1));
         if ((done || pass) && !fwd) {
             if (found) {
                 const float th = (a.refine_root && !isnan(t_prev)) ? refine<L>(a, o, d, t_prev, t) : t;
-                store_hit(e.hits + qi, th, -1, 0.f, 0.f, RT_TRACER_SDF, flags);
+                store_hit(hits + qi, th, -1, 0.f, 0.f, RT_TRACER_SDF, flags);
             } else {
-                store_hit(e.hits + qi, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
+                store_hit(hits + qi, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
             }
         }
         if (__ballot_sync(kFull, live || !drained) == 0) break;
@@ -402,14 +401,15 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
     rt_status rs = RT_OK;
     cudaError_t e = cudaMemsetAsync(ctr, 0, ctr_bytes, s);
     if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaMemsetAsync");
-    // launches: triangles, field, triangles
-    for (int k = 0; k < 3 && rs == RT_OK; ++k) {
+    // launches: triangles, field, triangles, triangles; ctr[k] = fetch counter of
+    // launch k, ctr[8 + k] = number of queries launch k hands on (queues ping-pong)
+    for (int k = 0; k < kLaunches && rs == RT_OK; ++k) {
         Pipe pp;
         pp.in_items = k > 0 ? q[(k - 1) & 1] : nullptr;
-        pp.in_count = k > 0 ? &ctr[3 + ((k - 1) & 1)] : nullptr;
+        pp.in_count = k > 0 ? &ctr[8 + k - 1] : nullptr;
         pp.n_first = (unsigned)total;
-        pp.out_items = k < 2 ? q[k & 1] : nullptr;
-        pp.out_count = k < 2 ? &ctr[3 + (k & 1)] : nullptr;
+        pp.out_items = k + 1 < kLaunches ? q[k & 1] : nullptr;
+        pp.out_count = k + 1 < kLaunches ? &ctr[8 + k] : nullptr;
         pp.fetch = &ctr[k];
         pp.refill_min = tu.refill_min;
         if (k == 1 && need_grid) {

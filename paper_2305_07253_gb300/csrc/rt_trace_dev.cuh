@@ -424,21 +424,26 @@ struct Split {
     bool near_bvh, field, far_bvh;
 };
 
-__device__ __forceinline__ Split make_split(const TraceArgs& a, float tmin, float tmax)
+__device__ __forceinline__ Split make_split(int mode, float m_near, float m_far, float hsplit, float tmin, float tmax)
 {
     Split s;
-    s.t1 = fminf(fmaxf(__fmaf_rn(a.m_near, a.hsplit, tmin), tmin), tmax);
-    s.t2 = fminf(fmaxf(__fmaf_rn(-a.m_far, a.hsplit, tmax), s.t1), tmax);
-    s.near_bvh = a.m_near > 0.f;
-    if (a.mode == RT_MODE_SPLIT1) {
-        s.field = (a.m_near == 0.f) || (s.t1 < tmax);
+    s.t1 = fminf(fmaxf(__fmaf_rn(m_near, hsplit, tmin), tmin), tmax);
+    s.t2 = fminf(fmaxf(__fmaf_rn(-m_far, hsplit, tmax), s.t1), tmax);
+    s.near_bvh = m_near > 0.f;
+    if (mode == RT_MODE_SPLIT1) {
+        s.field = (m_near == 0.f) || (s.t1 < tmax);
         s.far_bvh = false;
         s.t2 = tmax;
     } else {
-        s.field = (s.t1 < s.t2) || (a.m_near == 0.f && a.m_far == 0.f);
-        s.far_bvh = a.m_far > 0.f;
+        s.field = (s.t1 < s.t2) || (m_near == 0.f && m_far == 0.f);
+        s.far_bvh = m_far > 0.f;
     }
     return s;
+}
+
+__device__ __forceinline__ Split make_split(const TraceArgs& a, float tmin, float tmax)
+{
+    return make_split(a.mode, a.m_near, a.m_far, a.hsplit, tmin, tmax);
 }
 
 // Eq. 1 is defined for real o, d and t_min <= t_max; anything else has no intersection
