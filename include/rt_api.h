@@ -288,8 +288,11 @@ rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, c
  *                 query runs all its sub-intervals.
  *   block         threads per block (multiple of 32, 32..1024)
  *   blocks_per_sm persistent grid = SMs x this (0: as many as fit)
- *   refill_min    a warp fetches new queries when at least this many lanes
- *                 are idle (1..32), or when all are
+ *   refill_min    triangle stages: a warp fetches new queries when at least
+ *                 this many lanes are idle (1..32), or when all are (32 keeps
+ *                 the rays of a warp together, which suits coherent rays)
+ *   refill_min_field  the same for the distance-field stages, whose queries
+ *                 end after very different step counts
  *   grid_layout   RT_LAYOUT_CELLS (default): use the cell-corner copy when it
  *                 exists; RT_LAYOUT_PLAIN: always read the plain grid
  * Results do not depend on the tuning. */
@@ -299,6 +302,7 @@ typedef struct {
     int32_t blocks_per_sm;
     int32_t refill_min;
     int32_t grid_layout;
+    int32_t refill_min_field;
 } rt_tuning;
 
 enum { RT_KERNEL_WAVEFRONT = 0, RT_KERNEL_SIMPLE = 1 };

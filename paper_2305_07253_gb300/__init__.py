@@ -55,7 +55,7 @@ class rt_split_params(ctypes.Structure):
 
 class rt_tuning(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("refill_min", ctypes.c_int32), ("grid_layout", ctypes.c_int32)]
+                ("refill_min", ctypes.c_int32), ("grid_layout", ctypes.c_int32), ("refill_min_field", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

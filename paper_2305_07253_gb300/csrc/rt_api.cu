@@ -13,7 +13,7 @@
 static thread_local char g_err[512] = "";
 
 // process-wide launch tuning (see rt_set_tuning)
-static rt_tuning g_tuning = {RT_KERNEL_WAVEFRONT, 128, 0, 16, RT_LAYOUT_CELLS};
+static rt_tuning g_tuning = {RT_KERNEL_WAVEFRONT, 128, 0, 16, RT_LAYOUT_CELLS, 16};
 
 const rt_tuning& rt_current_tuning() { return g_tuning; }
 
@@ -26,6 +26,8 @@ extern "C" rt_status rt_set_tuning(const rt_tuning* t)
         return rt_fail(RT_ERR_INVALID_ARG, "block %d must be a multiple of 32 in [32, 1024]", t->block);
     if (t->blocks_per_sm < 0 || t->blocks_per_sm > 64) return rt_fail(RT_ERR_INVALID_ARG, "blocks_per_sm %d", t->blocks_per_sm);
     if (t->refill_min < 1 || t->refill_min > 32) return rt_fail(RT_ERR_INVALID_ARG, "refill_min %d", t->refill_min);
+    if (t->refill_min_field < 1 || t->refill_min_field > 32)
+        return rt_fail(RT_ERR_INVALID_ARG, "refill_min_field %d", t->refill_min_field);
     if (t->grid_layout != RT_LAYOUT_CELLS && t->grid_layout != RT_LAYOUT_PLAIN)
         return rt_fail(RT_ERR_INVALID_ARG, "grid_layout %d", t->grid_layout);
     g_tuning = *t;

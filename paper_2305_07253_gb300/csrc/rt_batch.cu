@@ -411,7 +411,7 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
         pp.out_items = k + 1 < kLaunches ? q[k & 1] : nullptr;
         pp.out_count = k + 1 < kLaunches ? &ctr[8 + k] : nullptr;
         pp.fetch = &ctr[k];
-        pp.refill_min = tu.refill_min;
+        pp.refill_min = k == 1 ? tu.refill_min_field : tu.refill_min;
         if (k == 1 && need_grid) {
             switch (grid_layout_of(a)) {
 #define RT_BATCH_FIELD(LL)                                                                            \

@@ -432,7 +432,7 @@ rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s,
         sa.out_items = k + 1 < n_st ? q[k & 1] : nullptr;
         sa.out_count = k + 1 < n_st ? &ctr[3 + (k & 1)] : nullptr;
         sa.fetch = &ctr[k];
-        sa.refill_min = tu.refill_min;
+        sa.refill_min = (kinds[k] == ST_FIELD_FULL || kinds[k] == ST_FIELD_SPLIT) ? tu.refill_min_field : tu.refill_min;
         if (timing) {
             e = cudaEventRecord(timing->events[k], s);
             if (e != cudaSuccess) { rs = rt_cuda_fail(e, "cudaEventRecord"); break; }
@@ -589,7 +589,7 @@ extern "C" rt_status rt_trace_combined_noalloc(const rt_scene* sc, const rt_sdf*
         sa.out_items = k + 1 < n_st ? q[k & 1] : nullptr;
         sa.out_count = k + 1 < n_st ? &ctr[3 + (k & 1)] : nullptr;
         sa.fetch = &ctr[k];
-        sa.refill_min = tu.refill_min;
+        sa.refill_min = (kinds[k] == ST_FIELD_FULL || kinds[k] == ST_FIELD_SPLIT) ? tu.refill_min_field : tu.refill_min;
         st = launch_stage<false>(a, sa, tu, dev->sms, s);
         if (st != RT_OK) return st;
     }
