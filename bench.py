@@ -52,8 +52,11 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="set up, then run only warmup+steps launches of the --only traces (for ncu); prints timings")
     ap.add_argument("--only", default="all", choices=["all", "combined", "bvh", "sdf"])
-    ap.add_argument("--workload", default="frame", choices=["frame", "batching"],
-                    help="frame: the 1080p GI headline; batching: 8 frames of mixed primary/shadow/AO/GI batches")
+    ap.add_argument("--workload", default="frame", choices=["frame", "batching", "fit", "precision"],
+                    help="frame: the 1080p GI headline; batching: 8 frames of mixed primary/shadow/AO/GI "
+                         "batches; fit: gradient fit of a noisy 128^3 grid; precision: float16 vs float32 "
+                         "512^3 grid on the 8.2 M-triangle scene")
+    ap.add_argument("--fit-steps", type=int, default=200)
     ap.add_argument("--frames", type=int, default=8)
     return ap.parse_args()
 
@@ -540,12 +543,154 @@ def run_batching(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fit(args):
+    """Gradient fit of a noisy grid (differentiation workload): 102,532 triangles,
+    128^3 float32 grid = exact bake + N(0, (0.5 voxel)^2) noise, 1 M free-space rays
+    per step, loss = mean (t_field - t_triangles)^2, Adam, adjoint kernel backward."""
+    import torch
+
+    import paper_2305_07253_gb300 as rq
+    from paper_2305_07253_gb300 import fit as F
+    from synth import rng as RNG
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    s = S.make_scene("fit")
+    n = s.spec.grid_n
+    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
+    clean = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    sdf_clean = rq.rt_sdf_create(clean, s.lo, s.hi)
+    rq.rt_sdf_bake(scene, sdf_clean)
+    h = np.array(s.room) / (n - 1)
+    h_min = float(h.min())
+    noise = RNG.normal(s.seed, 501, n ** 3).astype(np.float32).reshape(n, n, n) * (0.5 * h_min)
+    grid = clean + torch.from_numpy(noise).to(dev)
+    sdf = rq.rt_sdf_create(grid, s.lo, s.hi)
+    rq.rt_sdf_prepare(sdf)
+    t0 = time.perf_counter()
+    margin = 2.0 * float(h.max())
+    pool = torch.from_numpy(R.free_space_rays(s, 4 * 1024 * 1024, 7, margin)).to(dev)
+    evals = torch.from_numpy(R.free_space_rays(s, 1024 * 1024, 8, margin)).to(dev)
+    gen_s = time.perf_counter() - t0
+    t_pool = rq.hit_fields(rq.rt_trace_bvh(scene, pool))["t"].clone()
+    t_eval = rq.hit_fields(rq.rt_trace_bvh(scene, evals))["t"].clone()
+    per = 1024 * 1024
+
+    def batches(step):
+        k = step % 4
+        return pool[k * per:(k + 1) * per], t_pool[k * per:(k + 1) * per]
+
+    before = F.disagreement(scene, sdf, evals, t_eval)
+    clean_d = F.disagreement(scene, sdf_clean, evals, t_eval)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hist = F.fit_grid(scene, sdf, batches, args.fit_steps, lr=0.05 * h_min, log_every=20)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    after = F.disagreement(scene, sdf, evals, t_eval)
+    line = {"metric": "gradient-fit steps/s and field-vs-triangle hit-t disagreement", "value":
+            args.fit_steps / (ms * 1e-3), "unit": "steps/s", "n_gpus": 1, "steps": args.fit_steps,
+            "higher_is_better": True, "data": "synthetic (seeded procedural scene and rays)", "dtype": "f32",
+            "config": {"workload": "fit-noisy-grid", "n_tris": int(s.n_tris), "grid": [n, n, n],
+                       "rays_per_step": per, "noise_sigma_m": 0.5 * h_min, "lr": 0.05 * h_min,
+                       "input_generation_s": gen_s},
+            "ms_per_step": ms / args.fit_steps,
+            "disagreement": {"noisy_init": before, "fitted": after, "clean_bake": clean_d},
+            "loss_history": [[hh.step, hh.loss] for hh in hist]}
+    print(json.dumps(line), flush=True)
+
+
+def run_precision(args):
+    """Float16 vs float32 storage of a 512^3 grid on the 8,201,612-triangle scene,
+    1080p GI rays: rays/s per split setting, and hit-t error against the fp64
+    checker per tracer segment (the checker runs in this workload's CPU leg)."""
+    import torch
+
+    import paper_2305_07253_gb300 as rq
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    s = S.make_scene("precision")
+    n = s.spec.grid_n
+    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
+    g32 = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    sdf32 = rq.rt_sdf_create(g32, s.lo, s.hi)
+    rq.rt_sdf_bake(scene, sdf32, rq.BAKE_BVH)
+    g16 = g32.half()
+    sdf16 = rq.rt_sdf_create(g16, s.lo, s.hi)
+    rq.rt_sdf_prepare(sdf16)
+    rays = R.gi_rays(s, 1920 * 1080, 7, 30.0)
+    rd = torch.from_numpy(rays).to(dev)
+    hits = torch.empty((rd.shape[0], 6), dtype=torch.int32, device=dev)
+    K, W = max(3, args.steps // 10), max(3, args.warmup)
+
+    def timed(sdf, p):
+        for _ in range(W):
+            rq.rt_trace_combined(scene, sdf, rd, p, hits)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            rq.rt_trace_combined(scene, sdf, rd, p, hits)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    sample = np.linspace(0, rays.shape[0] - 1, 4096).astype(np.int64)
+    res, got = {}, {}
+    for m in (0.0, M_MIDDLE, math.inf):
+        p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
+        for name, sdf in (("f32", sdf32), ("f16", sdf16)):
+            ms = timed(sdf, p)
+            h = rq.rt_trace_combined(scene, sdf, rd, p).cpu().numpy()[sample]
+            got[(m, name)] = h
+            res[f"m={m}/{name}"] = {"ms": ms, "rays_per_s": rays.shape[0] / (ms * 1e-3)}
+    # hit-t error against the fp64 checker on the sample (CPU leg)
+    import oracle as O
+    t0 = time.perf_counter()
+    bvh = O.BVH(s.verts, s.tris)
+    ogrid = O.Grid(s.lo, s.hi, [n, n, n], src=bvh)
+    errs = {}
+    for m in (0.0, M_MIDDLE, math.inf):
+        o = O.trace_combined(bvh, ogrid, rays[sample], O.make_params(mode=1, m_near=m), precision=64)
+        for name in ("f32", "f16"):
+            g = got[(m, name)]
+            gt = g[:, 0].view(np.float32).astype(np.float64)
+            gtr = g[:, 4]
+            e = {}
+            for seg, tr in (("bvh_resolved", 1), ("sdf_resolved", 2)):
+                sel = (gtr == tr) & (o["tracer"] == tr)
+                r = np.abs(gt[sel] - o["t"][sel]) / np.maximum(1.0, np.abs(o["t"][sel]))
+                e[seg] = {"n": int(sel.sum()), "mean_rel": float(r.mean()) if r.size else 0.0,
+                          "p99_rel": float(np.quantile(r, 0.99)) if r.size else 0.0,
+                          "max_rel": float(r.max()) if r.size else 0.0}
+            e["tracer_agreement"] = float(np.mean(gtr == o["tracer"]))
+            errs[f"m={m}/{name}"] = e
+    cpu_s = time.perf_counter() - t0
+    line = {"metric": "float16 vs float32 grid: rays/s and hit-t error vs fp64, per split setting",
+            "value": res[f"m={M_MIDDLE}/f16"]["rays_per_s"], "unit": UNIT, "n_gpus": 1, "steps": K,
+            "higher_is_better": True, "data": "synthetic (seeded procedural scene and rays)", "dtype": "f16 grid, f32 math",
+            "config": {"workload": "precision-512", "n_tris": int(s.n_tris), "grid": [n, n, n],
+                       "grid_bytes": {"f32": int(g32.numel() * 4), "f16": int(g16.numel() * 2)},
+                       "rays": int(rays.shape[0]), "t_max_m": 30.0},
+            "timing": res, "hit_t_err_vs_fp64": errs,
+            "cpu_leg": {"sample": "4096 evenly spaced GI rays, fp64 checker with its own BVH and exact bake",
+                        "seconds": cpu_s}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batching":
         run_batching(args)
+    elif args.workload == "fit":
+        run_fit(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 
