@@ -124,6 +124,9 @@ typedef struct {
     int64_t n_nodes;     /* internal BVH nodes (64 bytes each) */
     int32_t max_depth;   /* deepest leaf; traversal stack holds RT_STACK_DEPTH entries */
     int32_t stack_depth;
+    int64_t n_wide_nodes;  /* 80-byte nodes of the 8-wide tree (0: not built) */
+    int32_t wide_depth;    /* levels of the 8-wide tree */
+    int32_t pad_;
     float lo[3], hi[3];  /* bounds of all triangles */
     int64_t device_bytes;
 } rt_scene_info;
@@ -293,6 +296,10 @@ rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, c
  *                 the rays of a warp together, which suits coherent rays)
  *   refill_min_field  the same for the distance-field stages, whose queries
  *                 end after very different step counts
+ *   bvh_width     8 (default): traverse the 8-wide compressed tree (80-byte
+ *                 nodes, 8-bit child bounds, octant-ordered children); 2: the
+ *                 binary tree (64-byte nodes).  Scenes whose wide tree would
+ *                 be deeper than its traversal stack use the binary tree.
  *   grid_layout   RT_LAYOUT_CELLS (default): use the cell-corner copy when it
  *                 exists; RT_LAYOUT_PLAIN: always read the plain grid
  * Results do not depend on the tuning. */
@@ -303,6 +310,7 @@ typedef struct {
     int32_t refill_min;
     int32_t grid_layout;
     int32_t refill_min_field;
+    int32_t bvh_width;
 } rt_tuning;
 
 enum { RT_KERNEL_WAVEFRONT = 0, RT_KERNEL_SIMPLE = 1 };

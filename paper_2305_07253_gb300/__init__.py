@@ -55,7 +55,8 @@ class rt_split_params(ctypes.Structure):
 
 class rt_tuning(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("refill_min", ctypes.c_int32), ("grid_layout", ctypes.c_int32), ("refill_min_field", ctypes.c_int32)]
+                ("refill_min", ctypes.c_int32), ("grid_layout", ctypes.c_int32), ("refill_min_field", ctypes.c_int32),
+                ("bvh_width", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,7 +72,8 @@ MAX_BATCHES = 16
 
 class rt_scene_info(ctypes.Structure):
     _fields_ = [("n_tris", ctypes.c_int64), ("n_verts", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
-                ("max_depth", ctypes.c_int32), ("stack_depth", ctypes.c_int32), ("lo", ctypes.c_float * 3),
+                ("max_depth", ctypes.c_int32), ("stack_depth", ctypes.c_int32), ("n_wide_nodes", ctypes.c_int64),
+                ("wide_depth", ctypes.c_int32), ("pad_", ctypes.c_int32), ("lo", ctypes.c_float * 3),
                 ("hi", ctypes.c_float * 3), ("device_bytes", ctypes.c_int64)]
 
 

@@ -13,7 +13,7 @@
 static thread_local char g_err[512] = "";
 
 // process-wide launch tuning (see rt_set_tuning)
-static rt_tuning g_tuning = {RT_KERNEL_WAVEFRONT, 128, 0, 16, RT_LAYOUT_CELLS, 16};
+static rt_tuning g_tuning = {RT_KERNEL_WAVEFRONT, 128, 0, 16, RT_LAYOUT_CELLS, 16, 8};
 
 const rt_tuning& rt_current_tuning() { return g_tuning; }
 
@@ -28,6 +28,7 @@ extern "C" rt_status rt_set_tuning(const rt_tuning* t)
     if (t->refill_min < 1 || t->refill_min > 32) return rt_fail(RT_ERR_INVALID_ARG, "refill_min %d", t->refill_min);
     if (t->refill_min_field < 1 || t->refill_min_field > 32)
         return rt_fail(RT_ERR_INVALID_ARG, "refill_min_field %d", t->refill_min_field);
+    if (t->bvh_width != 2 && t->bvh_width != 8) return rt_fail(RT_ERR_INVALID_ARG, "bvh_width %d", t->bvh_width);
     if (t->grid_layout != RT_LAYOUT_CELLS && t->grid_layout != RT_LAYOUT_PLAIN)
         return rt_fail(RT_ERR_INVALID_ARG, "grid_layout %d", t->grid_layout);
     g_tuning = *t;
@@ -92,6 +93,10 @@ void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, con
     if (sc) {
         a.nodes = sc->nodes;
         a.tris = sc->tris;
+        if (g_tuning.bvh_width == 8 && sc->wnodes) {
+            a.wnodes = sc->wnodes;
+            a.wtris = sc->wtris;
+        }
         a.root = sc->n_tris == 0 ? INT32_MIN : (sc->n_tris == 1 ? ~0 : 0);
     } else {
         a.root = INT32_MIN;
@@ -159,6 +164,9 @@ extern "C" rt_status rt_scene_info_get(const rt_scene* sc, rt_scene_info* info)
     info->n_nodes = sc->n_nodes;
     info->max_depth = sc->max_depth;
     info->stack_depth = RT_STACK_DEPTH;
+    info->n_wide_nodes = sc->wnodes ? sc->n_wnodes : 0;
+    info->wide_depth = sc->wide_depth;
+    info->pad_ = 0;
     for (int k = 0; k < 3; ++k) {
         info->lo[k] = sc->lo[k];
         info->hi[k] = sc->hi[k];
@@ -173,6 +181,8 @@ extern "C" rt_status rt_scene_destroy(rt_scene* sc)
     cudaFree(sc->nodes);
     cudaFree(sc->tris);
     cudaFree(sc->pn);
+    cudaFree(sc->wnodes);
+    cudaFree(sc->wtris);
     delete sc;
     return RT_OK;
 }

@@ -115,7 +115,7 @@ __device__ __forceinline__ void take(const Pipe& pp, unsigned n_in, bool idle, b
 // queue item: x = global query index, y = flags | (program position << 8)
 __device__ __forceinline__ int2 pack_item(int g, uint32_t flags, int p) { return make_int2(g, (int)(flags | (p << 8))); }
 
-template <bool COUNT>
+template <bool COUNT, bool WIDE>
 __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe pp)
 {
     __shared__ BatchEntry stb[RT_MAX_BATCHES];
@@ -123,7 +123,7 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
     const unsigned n_in = pp.in_items ? *pp.in_count : pp.n_first;
     rt_hit* hits = nullptr;  // this lane's batch output
     bool has_next = false;   // the query's program continues after this sub-interval
-    int stack[RT_STACK_DEPTH];
+    typename TravOf<WIDE>::entry stack[TravOf<WIDE>::depth];
     Counts cnt = {0, 0, 0, 0};
     bool drained = false, live = false;
     int g = -1, p = 0, b = 0;
@@ -131,7 +131,7 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
     uint32_t flags = 0;
     bool any_hit = false;
     BvhRay r;
-    Trav s;
+    typename TravOf<WIDE>::state s;
     Hit best;
     for (;;) {
         bool got;
@@ -169,7 +169,7 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
                 any_hit = e.any_hit != 0;
                 if (active && ta <= tb2 && a.root != INT32_MIN) {
                     r = bvh_ray(o, d);
-                    s = trav_begin(a.root, ta, tb2);
+                    s = tbegin<WIDE>(a, r, ta, tb2);
                     best.prim = -1;
                     live = true;
                 } else {
@@ -177,7 +177,7 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
                 }
             }
         } else if (live) {
-            if (trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt, kBatchTrip)) {
+            if (ttrip<COUNT, WIDE>(a, r, s, stack, any_hit, best, flags, cnt, kBatchTrip)) {
                 live = false;
                 done = true;
                 found = s.found;
@@ -428,8 +428,10 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
             // no batch uses the field: pass everything through an empty field launch
             k_batch_field<false, GL_PLAIN_F32><<<grid_for(k_batch_field<false, GL_PLAIN_F32>, tu, dev->sms), tu.block, 0, s>>>(
                 a, tb, pp);
+        } else if (a.wnodes) {
+            k_batch_bvh<false, true><<<grid_for(k_batch_bvh<false, true>, tu, dev->sms), tu.block, 0, s>>>(a, tb, pp);
         } else {
-            k_batch_bvh<false><<<grid_for(k_batch_bvh<false>, tu, dev->sms), tu.block, 0, s>>>(a, tb, pp);
+            k_batch_bvh<false, false><<<grid_for(k_batch_bvh<false, false>, tu, dev->sms), tu.block, 0, s>>>(a, tb, pp);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) rs = rt_cuda_fail(e, "stage launch");

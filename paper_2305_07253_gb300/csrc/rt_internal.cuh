@@ -8,6 +8,14 @@
 //              d = (child0, child1, -, -)   child >= 0: internal node,
 //                                           child < 0 : leaf = triangle ~child
 //   tris   : 48 B per triangle in leaf (Morton) order: v0.xyz|prim, v1.xyz|-, v2.xyz|-
+//   wnodes : the same tree collapsed to 8-wide nodes of 80 B (five 16-byte vectors):
+//              a  = (origin x, y, z, bits: exponent x | y << 8 | z << 16 | internal mask << 24)
+//              b  = (first child node, first triangle, meta slots 0-3, meta slots 4-7)
+//              q0 = (qlo.x[0..7], qlo.y[0..7]), q1 = (qlo.z[0..7], qhi.x[0..7]),
+//              q2 = (qhi.y[0..7], qhi.z[0..7])   8-bit child bounds, box = origin + q * 2^(e-127)
+//            meta byte: 0 empty, else leaf (count << 5 | first triangle offset) or, with the
+//            internal-mask bit set, an inner child at first child + (inner children in lower slots)
+//   wtris  : 48 B per triangle in wide-leaf order (each node's leaf triangles contiguous)
 //   pn     : 112 B per triangle in leaf order: face normal, 3 edge and 3 vertex
 //            pseudonormals (float4 each), read only by the distance bake
 //   grid   : caller memory, dense n0*n1*n2 float32 or float16, x fastest
@@ -30,6 +38,13 @@ struct __align__(32) BNode {
     int4 d;
 };
 
+struct __align__(16) WNode {
+    float4 a;
+    uint4 b, q0, q1, q2;
+};
+
+#define RT_WSTACK_DEPTH 32
+
 struct rt_scene {
     int device;
     int64_t n_tris, n_verts, n_nodes;
@@ -37,6 +52,10 @@ struct rt_scene {
     BNode* nodes;
     float4* tris;   // 3 per triangle
     float4* pn;     // 7 per triangle
+    WNode* wnodes;  // null when the wide tree is not available
+    float4* wtris;  // 3 per triangle
+    int64_t n_wnodes;
+    int32_t wide_depth;
     float lo[3], hi[3];
     int64_t bytes;
 };
@@ -55,6 +74,8 @@ struct rt_sdf {
 struct TraceArgs {
     const BNode* nodes;
     const float4* tris;
+    const WNode* wnodes;  // null: binary traversal
+    const float4* wtris;
     int32_t root;        // 0 (internal), ~0 (single leaf) or INT32_MIN (no triangles)
     const void* grid;    // null: no field
     const void* cells;   // null: read the plain grid
@@ -97,5 +118,8 @@ rt_status rt_launch_backward(const TraceArgs& a, const float* grad_t, float* gra
 rt_status rt_build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, cudaStream_t s,
                          rt_scene* out);
 rt_status rt_launch_bake(const rt_scene* sc, const rt_sdf* sdf, int32_t method, cudaStream_t s);
+rt_status rt_build_wide(rt_scene* sc, const int2* child, const int2* range, const float4* node_lo,
+                        const float4* node_hi, const float4* leaf_lo, const float4* leaf_hi, float pad,
+                        cudaStream_t s);
 rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s);
 void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, const rt_split_params* p);

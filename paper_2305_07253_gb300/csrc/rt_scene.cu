@@ -124,7 +124,8 @@ __device__ __forceinline__ int delta(const uint64_t* keys, int64_t n, int64_t i,
 }
 
 // children: >= 0 internal node, < 0 leaf ~k (sorted position k)
-__global__ void k_hierarchy(const uint64_t* keys, int64_t n, int2* child, int32_t* parent_int, int32_t* parent_leaf)
+__global__ void k_hierarchy(const uint64_t* keys, int64_t n, int2* child, int2* range, int32_t* parent_int,
+                            int32_t* parent_leaf)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
@@ -148,6 +149,7 @@ __global__ void k_hierarchy(const uint64_t* keys, int64_t n, int2* child, int32_
     int left = (lo == gamma) ? ~(int)gamma : (int)gamma;
     int right = (hi == gamma + 1) ? ~(int)(gamma + 1) : (int)(gamma + 1);
     child[i] = make_int2(left, right);
+    range[i] = make_int2((int)lo, (int)hi);  // sorted triangles lo..hi under node i
     if (left < 0) parent_leaf[~left] = (int32_t)i; else parent_int[left] = (int32_t)i;
     if (right < 0) parent_leaf[~right] = (int32_t)i; else parent_int[right] = (int32_t)i;
     if (i == 0) parent_int[0] = -1;
@@ -327,6 +329,8 @@ rt_status rt_build_scene(const float* V, int64_t nv, const int32_t* F, int64_t n
     ALLOC(vals, nt * sizeof(int32_t));
     ALLOC(vals2, nt * sizeof(int32_t));
     ALLOC(child, (nt - 1) * sizeof(int2));
+    DevBuf nrange;
+    ALLOC(nrange, (nt - 1) * sizeof(int2));
     ALLOC(par_i, (nt - 1) * sizeof(int32_t));
     ALLOC(par_l, nt * sizeof(int32_t));
     ALLOC(llo, nt * sizeof(float4));
@@ -370,7 +374,7 @@ rt_status rt_build_scene(const float* V, int64_t nv, const int32_t* F, int64_t n
     RT_CUDA_TRY(cudaMemsetAsync(visit.p, 0, (nt > 1 ? nt - 1 : 1) * sizeof(int), s));
     RT_CUDA_TRY(cudaMemsetAsync(depth.p, 0, sizeof(int), s));
     if (nt > 1) {
-        k_hierarchy<<<grid_for(nt - 1), kBlock, 0, s>>>(skeys, nt, child.as<int2>(), par_i.as<int32_t>(),
+        k_hierarchy<<<grid_for(nt - 1), kBlock, 0, s>>>(skeys, nt, child.as<int2>(), nrange.as<int2>(), par_i.as<int32_t>(),
                                                         par_l.as<int32_t>());
         RT_CUDA_TRY(cudaGetLastError());
     } else {
@@ -413,6 +417,11 @@ rt_status rt_build_scene(const float* V, int64_t nv, const int32_t* F, int64_t n
     }
     k_pack_tris<<<grid_for(nt), kBlock, 0, s>>>(V, F, order, nt, sc->tris);
     RT_CUDA_TRY(cudaGetLastError());
+    {
+        rt_status ws = rt_build_wide(sc, child.as<int2>(), nrange.as<int2>(), nlo.as<float4>(), nhi.as<float4>(),
+                                     llo.as<float4>(), lhi.as<float4>(), pad, s);
+        if (ws != RT_OK) return ws;
+    }
 
     // pseudonormals
     ALLOC(fn, nt * sizeof(float4));

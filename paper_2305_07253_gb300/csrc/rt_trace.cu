@@ -33,7 +33,7 @@ constexpr int kFieldBudget = RT_FIELD_BUDGET;  // march steps between two refill
 // ---------------------------------------------------------------------------
 // simple kernel: one thread per query
 // ---------------------------------------------------------------------------
-template <bool COUNT, int L>
+template <bool COUNT, int L, bool WIDE>
 __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts& cnt)
 {
     const float4 r0 = __ldg(a.rays + 2 * i), r1 = __ldg(a.rays + 2 * i + 1);
@@ -45,7 +45,7 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
 
     if (!valid_query(o, d, tmin, tmax)) {
     } else if (a.mode == RT_MODE_BVH) {
-        if (bvh_segment<COUNT>(a, o, d, tmin, tmax, a.any_hit, h, flags, cnt)) tracer = RT_TRACER_BVH;
+        if (bvh_segment<COUNT, WIDE>(a, o, d, tmin, tmax, a.any_hit, h, flags, cnt)) tracer = RT_TRACER_BVH;
     } else if (a.mode == RT_MODE_SDF) {
         March m = sdf_march<COUNT, L>(a, o, d, tmin, tmax, flags, cnt);
         if (m.hit) {
@@ -62,12 +62,12 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
                     h.t = (a.refine_root && !isnan(m.t_prev)) ? refine<L>(a, o, d, m.t_prev, m.t) : m.t;
                 }
             }
-            if (tracer == RT_TRACER_MISS && s.near_bvh && bvh_segment<COUNT>(a, o, d, tmin, s.t1, true, h, flags, cnt))
+            if (tracer == RT_TRACER_MISS && s.near_bvh && bvh_segment<COUNT, WIDE>(a, o, d, tmin, s.t1, true, h, flags, cnt))
                 tracer = RT_TRACER_BVH;
-            if (tracer == RT_TRACER_MISS && s.far_bvh && bvh_segment<COUNT>(a, o, d, s.t2, tmax, true, h, flags, cnt))
+            if (tracer == RT_TRACER_MISS && s.far_bvh && bvh_segment<COUNT, WIDE>(a, o, d, s.t2, tmax, true, h, flags, cnt))
                 tracer = RT_TRACER_BVH;
         } else {
-            if (s.near_bvh && bvh_segment<COUNT>(a, o, d, tmin, s.t1, false, h, flags, cnt)) tracer = RT_TRACER_BVH;
+            if (s.near_bvh && bvh_segment<COUNT, WIDE>(a, o, d, tmin, s.t1, false, h, flags, cnt)) tracer = RT_TRACER_BVH;
             if (tracer == RT_TRACER_MISS && s.field) {
                 March m = sdf_march<COUNT, L>(a, o, d, s.t1, s.t2, flags, cnt);
                 if (m.hit) {
@@ -75,7 +75,7 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
                     h.t = (a.refine_root && !isnan(m.t_prev)) ? refine<L>(a, o, d, m.t_prev, m.t) : m.t;
                 }
             }
-            if (tracer == RT_TRACER_MISS && s.far_bvh && bvh_segment<COUNT>(a, o, d, s.t2, tmax, false, h, flags, cnt))
+            if (tracer == RT_TRACER_MISS && s.far_bvh && bvh_segment<COUNT, WIDE>(a, o, d, s.t2, tmax, false, h, flags, cnt))
                 tracer = RT_TRACER_BVH;
         }
     }
@@ -94,12 +94,12 @@ __device__ __forceinline__ void flush_counts(const TraceArgs& a, const Counts& c
     if (cnt.field) atomicAdd(&a.counters[3], (unsigned long long)cnt.field);
 }
 
-template <bool COUNT, int L>
+template <bool COUNT, int L, bool WIDE>
 __global__ void k_trace(const TraceArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     Counts cnt = {0, 0, 0, 0};
-    if (i < a.n) trace_one<COUNT, L>(a, i, cnt);
+    if (i < a.n) trace_one<COUNT, L, WIDE>(a, i, cnt);
     if (COUNT) flush_counts(a, cnt);
 }
 
@@ -181,18 +181,18 @@ __device__ __forceinline__ void refill(const StageArgs& st, unsigned n_in, bool 
     }
 }
 
-template <bool COUNT>
+template <bool COUNT, bool WIDE>
 __global__ void k_stage_bvh(const TraceArgs a, const StageArgs st)
 {
     const unsigned n_in = st.first ? (unsigned)a.n : *st.in_count;
     const bool any_hit = a.any_hit != 0;
-    int stack[RT_STACK_DEPTH];
+    typename TravOf<WIDE>::entry stack[TravOf<WIDE>::depth];
     Counts cnt = {0, 0, 0, 0};
     bool drained = false, live = false;
     int query = -1;
     uint32_t flags = 0;
     BvhRay r;
-    Trav s;
+    typename TravOf<WIDE>::state s;
     Hit best;
     for (;;) {
         bool got;
@@ -209,7 +209,7 @@ __global__ void k_stage_bvh(const TraceArgs a, const StageArgs st)
             bool active = stage_segment(a, st.kind, query, o, d, ta, tb, invalid);
             if (active && ta <= tb && a.root != INT32_MIN) {
                 r = bvh_ray(o, d);
-                s = trav_begin(a.root, ta, tb);
+                s = tbegin<WIDE>(a, r, ta, tb);
                 best.prim = -1;
                 live = true;
             } else {
@@ -217,7 +217,7 @@ __global__ void k_stage_bvh(const TraceArgs a, const StageArgs st)
                 final_miss = invalid;
             }
         } else if (live) {
-            if (trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt, kTripBudget)) {
+            if (ttrip<COUNT, WIDE>(a, r, s, stack, any_hit, best, flags, cnt, kTripBudget)) {
                 done = true;
                 found = s.found;
                 live = false;
@@ -365,9 +365,12 @@ rt_status launch_stage(const TraceArgs& a, const StageArgs& st, const rt_tuning&
             RT_FIELD_CASE(GL_CELLS_F16)
 #undef RT_FIELD_CASE
         }
+    } else if (a.wnodes) {
+        int blocks = persistent_blocks(k_stage_bvh<COUNT, true>, tu.block, tu, sms);
+        k_stage_bvh<COUNT, true><<<blocks, tu.block, 0, s>>>(a, st);
     } else {
-        int blocks = persistent_blocks(k_stage_bvh<COUNT>, tu.block, tu, sms);
-        k_stage_bvh<COUNT><<<blocks, tu.block, 0, s>>>(a, st);
+        int blocks = persistent_blocks(k_stage_bvh<COUNT, false>, tu.block, tu, sms);
+        k_stage_bvh<COUNT, false><<<blocks, tu.block, 0, s>>>(a, st);
     }
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
@@ -465,15 +468,30 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
         RT_CUDA_TRY(cudaEventRecord(timing->events[0], s));
         timing->kinds[0] = RT_STAGE_ALL;
     }
-    switch (grid_layout_of(a) + (counted ? 4 : 0)) {
-    case 0: k_trace<false, GL_PLAIN_F32><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
-    case 1: k_trace<false, GL_PLAIN_F16><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
-    case 2: k_trace<false, GL_CELLS_F32><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
-    case 3: k_trace<false, GL_CELLS_F16><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
-    case 4: k_trace<true, GL_PLAIN_F32><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
-    case 5: k_trace<true, GL_PLAIN_F16><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
-    case 6: k_trace<true, GL_CELLS_F32><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
-    default: k_trace<true, GL_CELLS_F16><<<(unsigned)blocks, tu.block, 0, s>>>(a); break;
+    {
+        const int sel = grid_layout_of(a) + (counted ? 4 : 0) + (a.wnodes ? 8 : 0);
+        const unsigned nb = (unsigned)blocks;
+        switch (sel) {
+#define RT_SIMPLE_CASE(K, C, LL, W) \
+    case K: k_trace<C, LL, W><<<nb, tu.block, 0, s>>>(a); break;
+            RT_SIMPLE_CASE(0, false, GL_PLAIN_F32, false)
+            RT_SIMPLE_CASE(1, false, GL_PLAIN_F16, false)
+            RT_SIMPLE_CASE(2, false, GL_CELLS_F32, false)
+            RT_SIMPLE_CASE(3, false, GL_CELLS_F16, false)
+            RT_SIMPLE_CASE(4, true, GL_PLAIN_F32, false)
+            RT_SIMPLE_CASE(5, true, GL_PLAIN_F16, false)
+            RT_SIMPLE_CASE(6, true, GL_CELLS_F32, false)
+            RT_SIMPLE_CASE(7, true, GL_CELLS_F16, false)
+            RT_SIMPLE_CASE(8, false, GL_PLAIN_F32, true)
+            RT_SIMPLE_CASE(9, false, GL_PLAIN_F16, true)
+            RT_SIMPLE_CASE(10, false, GL_CELLS_F32, true)
+            RT_SIMPLE_CASE(11, false, GL_CELLS_F16, true)
+            RT_SIMPLE_CASE(12, true, GL_PLAIN_F32, true)
+            RT_SIMPLE_CASE(13, true, GL_PLAIN_F16, true)
+            RT_SIMPLE_CASE(14, true, GL_CELLS_F32, true)
+            default: k_trace<true, GL_CELLS_F16, true><<<nb, tu.block, 0, s>>>(a); break;
+#undef RT_SIMPLE_CASE
+        }
     }
     RT_CUDA_TRY(cudaGetLastError());
     if (timing) {

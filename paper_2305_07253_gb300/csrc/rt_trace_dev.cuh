@@ -222,16 +222,169 @@ __device__ __forceinline__ bool trav_trip(const TraceArgs& a, const BvhRay& r, T
     return false;
 }
 
-// Whole triangle segment in one call (used by the one-thread-per-query kernel).
+// ---------------------------------------------------------------------------
+// 8-wide compressed tree (layout in rt_internal.cuh).  Each iteration tests one
+// triangle or visits one node: the 8 child boxes are decoded from their 8-bit
+// bounds and slab-tested, inner children that are hit go into a group mask in
+// rank order (rank = slot xor ray octant, roughly near to far), leaf triangles
+// that are hit into a triangle mask.  Groups wait on a stack of 64-bit entries
+// (first child, inner mask, remaining ranks).
+// ---------------------------------------------------------------------------
+struct WTrav {
+    uint32_t base;    // first child of the node whose children form the group
+    uint32_t masks;   // inner mask (bits 0-7) | remaining ranks (bits 8-15)
+    uint32_t tbase;   // first triangle of the node whose leaves are pending
+    uint32_t tmask;   // pending triangles (bit = offset from tbase)
+    int sp;
+    float ta, tbest;
+    bool found;
+    uint32_t guard;
+    int oct;
+};
+
+__device__ __forceinline__ WTrav wtrav_begin(const BvhRay& r, float ta, float tb)
+{
+    WTrav s;
+    s.oct = (r.idir.x < 0.f ? 1 : 0) | (r.idir.y < 0.f ? 2 : 0) | (r.idir.z < 0.f ? 4 : 0);
+    s.base = 0;                           // the root: a group of one inner child in slot 0
+    s.masks = 1u | ((1u << (0 ^ s.oct)) << 8);
+    s.tbase = 0;
+    s.tmask = 0;
+    s.sp = 0;
+    s.ta = ta;
+    s.tbest = tb;
+    s.found = false;
+    s.guard = 0;
+    return s;
+}
+
+__device__ __forceinline__ float byte_to_float(uint32_t w, int k)
+{
+    return __uint_as_float(0x4B000000u | ((w >> (8 * k)) & 0xffu)) - 8388608.0f;
+}
+
+// slab tests of the 8 children of wide node w; returns the new group and leaf masks
+__device__ __forceinline__ void visit_wide(const WNode* nodes, uint32_t w, const BvhRay& r, WTrav& s)
+{
+    const uint4* np = reinterpret_cast<const uint4*>(nodes + w);
+    const float4 na = __ldg(reinterpret_cast<const float4*>(np));
+    const uint4 nb = __ldg(np + 1), q0 = __ldg(np + 2), q1 = __ldg(np + 3), q2 = __ldg(np + 4);
+    const uint32_t bits = __float_as_uint(na.w);
+    const float sx = __uint_as_float((bits & 0xffu) << 23) * r.idir.x;
+    const float sy = __uint_as_float(((bits >> 8) & 0xffu) << 23) * r.idir.y;
+    const float sz = __uint_as_float(((bits >> 16) & 0xffu) << 23) * r.idir.z;
+    const float bx = (na.x - r.o.x) * r.idir.x;
+    const float by = (na.y - r.o.y) * r.idir.y;
+    const float bz = (na.z - r.o.z) * r.idir.z;
+    const uint32_t imask = bits >> 24;
+    uint32_t rmask = 0, tmask = 0;
+#pragma unroll
+    for (int slot = 0; slot < 8; ++slot) {
+        const int k = slot & 3;
+        const uint32_t lx = slot < 4 ? q0.x : q0.y, ly = slot < 4 ? q0.z : q0.w;
+        const uint32_t lz = slot < 4 ? q1.x : q1.y, hx = slot < 4 ? q1.z : q1.w;
+        const uint32_t hy = slot < 4 ? q2.x : q2.y, hz = slot < 4 ? q2.z : q2.w;
+        const float x0 = fmaf(byte_to_float(lx, k), sx, bx), x1 = fmaf(byte_to_float(hx, k), sx, bx);
+        const float y0 = fmaf(byte_to_float(ly, k), sy, by), y1 = fmaf(byte_to_float(hy, k), sy, by);
+        const float z0 = fmaf(byte_to_float(lz, k), sz, bz), z1 = fmaf(byte_to_float(hz, k), sz, bz);
+        const float tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), s.ta));
+        const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), s.tbest));
+        if (tn <= tf) {
+            if (imask & (1u << slot)) {
+                rmask |= 1u << (slot ^ s.oct);
+            } else {
+                const uint32_t meta = ((slot < 4 ? nb.z : nb.w) >> (8 * k)) & 0xffu;
+                if (meta) tmask |= ((1u << (meta >> 5)) - 1u) << (meta & 31u);
+            }
+        }
+    }
+    s.base = nb.x;
+    s.masks = imask | (rmask << 8);
+    s.tbase = nb.y;
+    s.tmask = tmask;
+}
+
 template <bool COUNT>
+__device__ __forceinline__ bool wtrav_trip(const TraceArgs& a, const BvhRay& r, WTrav& s, uint64_t* stack,
+                                           bool any_hit, Hit& best, uint32_t& flags, Counts& cnt, int budget)
+{
+    for (int it = 0; it < budget; ++it) {
+        if (++s.guard > (1u << 26)) {  // bounded by the tree size; stops only a corrupt structure
+            flags |= RT_FLAG_ITER_LIMIT;
+            return true;
+        }
+        if (s.tmask) {
+            const int bit = __ffs(s.tmask) - 1;
+            s.tmask &= s.tmask - 1u;
+            if (COUNT) ++cnt.tris;
+            if (test_triangle(a.wtris, (int)(s.tbase + bit), r, s.ta, s.tbest, s.found, best)) {
+                s.found = true;
+                if (any_hit) return true;
+            }
+            continue;
+        }
+        uint32_t rm = s.masks >> 8;
+        if (rm) {
+            const int rank = __ffs(rm) - 1;
+            rm &= rm - 1u;
+            const uint32_t imask = s.masks & 0xffu;
+            const int slot = rank ^ s.oct;
+            const uint32_t w = s.base + __popc(imask & ((1u << slot) - 1u));
+            if (rm) {
+                if (s.sp < RT_WSTACK_DEPTH) stack[s.sp++] = ((uint64_t)s.base << 32) | imask | (rm << 8);
+                else flags |= RT_FLAG_STACK_OVERFLOW;
+            }
+            if (COUNT) ++cnt.nodes;
+            visit_wide(a.wnodes, w, r, s);
+            continue;
+        }
+        if (s.sp == 0) return true;
+        const uint64_t e = stack[--s.sp];
+        s.base = (uint32_t)(e >> 32);
+        s.masks = (uint32_t)e;
+    }
+    return false;
+}
+
+// The traversal of either tree behind one interface for the kernels.
+template <bool WIDE> struct TravOf;
+template <> struct TravOf<false> {
+    using state = Trav;
+    using entry = int;
+    static constexpr int depth = RT_STACK_DEPTH;
+};
+template <> struct TravOf<true> {
+    using state = WTrav;
+    using entry = uint64_t;
+    static constexpr int depth = RT_WSTACK_DEPTH;
+};
+
+template <bool WIDE>
+__device__ __forceinline__ typename TravOf<WIDE>::state tbegin(const TraceArgs& a, const BvhRay& r, float ta, float tb)
+{
+    if constexpr (WIDE) return wtrav_begin(r, ta, tb);
+    else return trav_begin(a.root, ta, tb);
+}
+
+template <bool COUNT, bool WIDE>
+__device__ __forceinline__ bool ttrip(const TraceArgs& a, const BvhRay& r, typename TravOf<WIDE>::state& s,
+                                      typename TravOf<WIDE>::entry* stack, bool any_hit, Hit& best, uint32_t& flags,
+                                      Counts& cnt, int budget)
+{
+    if constexpr (WIDE) return wtrav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt, budget);
+    else return trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt, budget);
+}
+
+// Whole triangle segment in one call (used by the one-thread-per-query kernel).
+template <bool COUNT, bool WIDE = false>
 __device__ __forceinline__ bool bvh_segment(const TraceArgs& a, float3 o, float3 d, float ta, float tb, bool any_hit,
                                             Hit& best, uint32_t& flags, Counts& cnt)
 {
     if (a.root == INT32_MIN || !(ta <= tb)) return false;
     const BvhRay r = bvh_ray(o, d);
-    int stack[RT_STACK_DEPTH];
-    Trav s = trav_begin(a.root, ta, tb);
-    while (!trav_trip<COUNT>(a, r, s, stack, any_hit, best, flags, cnt, 1 << 30)) {
+    typename TravOf<WIDE>::entry stack[TravOf<WIDE>::depth];
+    typename TravOf<WIDE>::state s = tbegin<WIDE>(a, r, ta, tb);
+    while (!ttrip<COUNT, WIDE>(a, r, s, stack, any_hit, best, flags, cnt, 1 << 30)) {
     }
     return s.found;
 }

@@ -44,9 +44,39 @@ def test_binding_export_list_matches_header():
 def test_struct_sizes_match_header():
     import paper_2305_07253_gb300 as rq
     assert ctypes.sizeof(rq.rt_split_params) == 32
-    assert ctypes.sizeof(rq.rt_scene_info) == 8 * 3 + 4 * 2 + 4 * 6 + 8
-    assert ctypes.sizeof(rq.rt_tuning) == 24
+    assert ctypes.sizeof(rq.rt_scene_info) == 8 * 3 + 4 * 2 + 8 + 4 * 2 + 4 * 6 + 8
+    assert ctypes.sizeof(rq.rt_tuning) == 28
     assert ctypes.sizeof(rq.rt_batch) == 8 * 3 + 32
+
+
+def test_ctypes_structs_match_the_c_header(tmp_path):
+    """Sizes and field offsets of the binding's structs equal what a C compiler
+    makes of include/rt_api.h."""
+    import shutil
+    import subprocess
+
+    import paper_2305_07253_gb300 as rq
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"rt_split_params": rq.rt_split_params, "rt_tuning": rq.rt_tuning, "rt_batch": rq.rt_batch,
+               "rt_scene_info": rq.rt_scene_info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rt_api.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(out[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
 
 
 def test_tuning_roundtrip_and_validation(rtlib):
@@ -56,7 +86,7 @@ def test_tuning_roundtrip_and_validation(rtlib):
         t = rq.rt_get_tuning()
         assert (t.kernel, t.block, t.refill_min) == (rq.KERNEL_SIMPLE, 256, 4)
         for bad in (dict(block=48), dict(block=0), dict(refill_min=0), dict(refill_min=33), dict(kernel=7),
-                    dict(grid_layout=5), dict(blocks_per_sm=-1), dict(refill_min_field=0)):
+                    dict(grid_layout=5), dict(blocks_per_sm=-1), dict(refill_min_field=0), dict(bvh_width=4)):
             with pytest.raises(rq.RtError):
                 rq.rt_set_tuning(**bad)
         assert rq.rt_get_tuning().block == 256  # a rejected call changes nothing

@@ -55,6 +55,8 @@ TUNINGS = {
     "simple-plain": dict(kernel=1, grid_layout=1),
     "wavefront-refill1-b64": dict(kernel=0, grid_layout=0, refill_min=1, block=64),
     "wavefront-refill32-b256": dict(kernel=0, grid_layout=0, refill_min=32, block=256, blocks_per_sm=2),
+    "wavefront-bvh2": dict(kernel=0, bvh_width=2),
+    "simple-bvh2": dict(kernel=1, bvh_width=2),
 }
 
 
@@ -83,6 +85,8 @@ def test_scene_build_info(tiny, medium):
         inf = w.scene.info()
         assert inf.n_tris == w.s.n_tris and inf.n_nodes == w.s.n_tris - 1
         assert 1 <= inf.max_depth <= inf.stack_depth
+        # the 8-wide tree: fewer levels, at most one node per binary internal node
+        assert 1 <= inf.n_wide_nodes <= inf.n_nodes and 1 <= inf.wide_depth < inf.max_depth
         np.testing.assert_allclose(np.array(inf.lo), w.s.verts.min(axis=0), rtol=0, atol=0)
         np.testing.assert_allclose(np.array(inf.hi), w.s.verts.max(axis=0), rtol=0, atol=0)
 
