@@ -296,10 +296,10 @@ rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, c
  *                 the rays of a warp together, which suits coherent rays)
  *   refill_min_field  the same for the distance-field stages, whose queries
  *                 end after very different step counts
- *   bvh_width     8 (default): traverse the 8-wide compressed tree (80-byte
- *                 nodes, 8-bit child bounds, octant-ordered children); 2: the
- *                 binary tree (64-byte nodes).  Scenes whose wide tree would
- *                 be deeper than its traversal stack use the binary tree.
+ *   bvh_width     2 (default): the binary tree (64-byte nodes); 8: the 8-wide
+ *                 compressed tree (80-byte nodes, 8-bit child bounds,
+ *                 octant-ordered children).  Scenes whose wide tree would be
+ *                 deeper than its traversal stack use the binary tree.
  *   grid_layout   RT_LAYOUT_CELLS (default): use the cell-corner copy when it
  *                 exists; RT_LAYOUT_PLAIN: always read the plain grid
  * Results do not depend on the tuning. */

@@ -17,15 +17,15 @@ from . import (KERNEL_SIMPLE, KERNEL_WAVEFRONT, LAYOUT_CELLS, LAYOUT_PLAIN, rt_g
 
 def default_space() -> list[dict]:
     space = []
-    for block, refill, refill_f, per_sm in itertools.product((64, 128, 256), (8, 16, 24, 32), (8, 16, 24),
-                                                            (0, 4)):
+    for width, block, refill, refill_f, per_sm in itertools.product((8, 2), (64, 128, 256), (8, 16, 32), (8, 16, 24),
+                                                                   (0, 4)):
         space.append(dict(kernel=KERNEL_WAVEFRONT, block=block, refill_min=refill, refill_min_field=refill_f,
-                          blocks_per_sm=per_sm, grid_layout=LAYOUT_CELLS))
+                          blocks_per_sm=per_sm, grid_layout=LAYOUT_CELLS, bvh_width=width))
     space.append(dict(kernel=KERNEL_WAVEFRONT, block=128, refill_min=16, refill_min_field=16, blocks_per_sm=0,
-                      grid_layout=LAYOUT_PLAIN))
-    for block, layout in itertools.product((64, 128, 256), (LAYOUT_CELLS, LAYOUT_PLAIN)):
+                      grid_layout=LAYOUT_PLAIN, bvh_width=8))
+    for width, block, layout in itertools.product((8, 2), (64, 128, 256), (LAYOUT_CELLS, LAYOUT_PLAIN)):
         space.append(dict(kernel=KERNEL_SIMPLE, block=block, refill_min=16, refill_min_field=16, blocks_per_sm=0,
-                          grid_layout=layout))
+                          grid_layout=layout, bvh_width=width))
     return space
 
 

@@ -13,7 +13,7 @@
 static thread_local char g_err[512] = "";
 
 // process-wide launch tuning (see rt_set_tuning)
-static rt_tuning g_tuning = {RT_KERNEL_WAVEFRONT, 128, 0, 16, RT_LAYOUT_CELLS, 16, 8};
+static rt_tuning g_tuning = {RT_KERNEL_WAVEFRONT, 128, 0, 16, RT_LAYOUT_CELLS, 16, 2};
 
 const rt_tuning& rt_current_tuning() { return g_tuning; }
 

@@ -55,8 +55,8 @@ TUNINGS = {
     "simple-plain": dict(kernel=1, grid_layout=1),
     "wavefront-refill1-b64": dict(kernel=0, grid_layout=0, refill_min=1, block=64),
     "wavefront-refill32-b256": dict(kernel=0, grid_layout=0, refill_min=32, block=256, blocks_per_sm=2),
-    "wavefront-bvh2": dict(kernel=0, bvh_width=2),
-    "simple-bvh2": dict(kernel=1, bvh_width=2),
+    "wavefront-bvh8": dict(kernel=0, bvh_width=8),
+    "simple-bvh8": dict(kernel=1, bvh_width=8),
 }
 
 
@@ -486,6 +486,7 @@ def test_autotuner_picks_a_valid_tuning(tiny):
         best, results = autotune.autotune(lambda: rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p),
                                           space=space, reps=2, warmup=1)
         assert len(results) == len(space) and all(ms > 0 for _, ms in results)
-        assert rq.rt_get_tuning().as_dict() == best
+        now = rq.rt_get_tuning().as_dict()
+        assert all(now[k] == v for k, v in best.items())
     finally:
         rq.rt_set_tuning(prev)
