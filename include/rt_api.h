@@ -166,8 +166,9 @@ rt_status rt_sdf_destroy(rt_sdf* sdf);
  * itself; call it after writing the grid memory any other way (for example
  * after an optimiser step), otherwise the traces keep reading the old copy.
  * Traces read the plain grid until the first prepare, or when the tuning
- * selects the plain layout.  Memory: 8x (cells) the grid, owned by the
- * handle, released by rt_sdf_destroy.  Enqueued on `stream`. */
+ * selects the plain layout.  Also builds the x-pair copy (see rt_tuning).
+ * Memory: about 8x (cells) + 2x (pairs) the grid, owned by the handle,
+ * released by rt_sdf_destroy.  Enqueued on `stream`. */
 rt_status rt_sdf_prepare(rt_sdf* sdf, void* stream);
 
 /* Fill the grid of `sdf` with the signed distance to the nearest triangle of
@@ -301,7 +302,9 @@ rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, c
  *                 octant-ordered children).  Scenes whose wide tree would be
  *                 deeper than its traversal stack use the binary tree.
  *   grid_layout   RT_LAYOUT_CELLS (default): use the cell-corner copy when it
- *                 exists; RT_LAYOUT_PLAIN: always read the plain grid
+ *                 exists; RT_LAYOUT_PLAIN: always read the plain grid;
+ *                 RT_LAYOUT_PAIRS: the copy of x-neighbour pairs (4 loads a
+ *                 step, twice the grid's size) when it exists
  * Results do not depend on the tuning. */
 typedef struct {
     int32_t kernel;
@@ -314,7 +317,7 @@ typedef struct {
 } rt_tuning;
 
 enum { RT_KERNEL_WAVEFRONT = 0, RT_KERNEL_SIMPLE = 1 };
-enum { RT_LAYOUT_CELLS = 0, RT_LAYOUT_PLAIN = 1 };
+enum { RT_LAYOUT_CELLS = 0, RT_LAYOUT_PLAIN = 1, RT_LAYOUT_PAIRS = 2 };
 
 rt_status rt_set_tuning(const rt_tuning* tuning);
 rt_status rt_get_tuning(rt_tuning* tuning);

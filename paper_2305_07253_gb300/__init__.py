@@ -32,7 +32,7 @@ GRID_F32, GRID_F16 = 0, 1
 BAKE_AUTO, BAKE_BRUTE, BAKE_BVH = 0, 1, 2
 
 KERNEL_WAVEFRONT, KERNEL_SIMPLE = 0, 1
-LAYOUT_CELLS, LAYOUT_PLAIN = 0, 1
+LAYOUT_CELLS, LAYOUT_PLAIN, LAYOUT_PAIRS = 0, 1, 2
 
 EXPORTS = ("rt_scene_build", "rt_scene_info_get", "rt_scene_destroy", "rt_sdf_create", "rt_sdf_destroy",
            "rt_sdf_prepare", "rt_sdf_bake", "rt_trace_bvh", "rt_trace_sdf", "rt_trace_combined",

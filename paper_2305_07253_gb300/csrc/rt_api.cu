@@ -13,7 +13,7 @@
 static thread_local char g_err[512] = "";
 
 // process-wide launch tuning (see rt_set_tuning)
-static rt_tuning g_tuning = {RT_KERNEL_WAVEFRONT, 128, 0, 16, RT_LAYOUT_CELLS, 16, 2};
+static rt_tuning g_tuning = {RT_KERNEL_WAVEFRONT, 128, 0, 32, RT_LAYOUT_CELLS, 16, 2};
 
 const rt_tuning& rt_current_tuning() { return g_tuning; }
 
@@ -29,7 +29,7 @@ extern "C" rt_status rt_set_tuning(const rt_tuning* t)
     if (t->refill_min_field < 1 || t->refill_min_field > 32)
         return rt_fail(RT_ERR_INVALID_ARG, "refill_min_field %d", t->refill_min_field);
     if (t->bvh_width != 2 && t->bvh_width != 8) return rt_fail(RT_ERR_INVALID_ARG, "bvh_width %d", t->bvh_width);
-    if (t->grid_layout != RT_LAYOUT_CELLS && t->grid_layout != RT_LAYOUT_PLAIN)
+    if (t->grid_layout != RT_LAYOUT_CELLS && t->grid_layout != RT_LAYOUT_PLAIN && t->grid_layout != RT_LAYOUT_PAIRS)
         return rt_fail(RT_ERR_INVALID_ARG, "grid_layout %d", t->grid_layout);
     g_tuning = *t;
     return RT_OK;
@@ -104,6 +104,7 @@ void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, con
     if (sdf) {
         a.grid = sdf->grid;
         a.cells = sdf->cells;
+        a.pairs = sdf->pairs;
         a.grid_f16 = sdf->dtype == RT_GRID_F16;
         for (int k = 0; k < 3; ++k) {
             a.glo[k] = sdf->lo[k];
@@ -207,6 +208,8 @@ extern "C" rt_status rt_sdf_create(const void* d_grid, int32_t dtype, const floa
     if (!g) return rt_fail(RT_ERR_OOM, "host allocation failed");
     g->cells = nullptr;
     g->cells_bytes = 0;
+    g->pairs = nullptr;
+    g->pairs_bytes = 0;
     cudaGetDevice(&g->device);
     g->grid = d_grid;
     g->dtype = dtype;
@@ -227,6 +230,7 @@ extern "C" rt_status rt_sdf_destroy(rt_sdf* sdf)
 {
     if (!sdf) return RT_OK;
     if (sdf->cells) cudaFree(sdf->cells);
+    if (sdf->pairs) cudaFree(sdf->pairs);
     delete sdf;
     return RT_OK;
 }

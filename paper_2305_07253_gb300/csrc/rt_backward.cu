@@ -73,8 +73,10 @@ rt_status rt_launch_backward(const TraceArgs& a, const float* grad_t, float* gra
     const int64_t blocks = (a.n + kBwdBlock - 1) / kBwdBlock;
     if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "too many rays");
     // float32 grids only (checked by the caller); the march reads the cell copy when present
-    if (a.cells) k_backward<GL_CELLS_F32><<<(unsigned)blocks, kBwdBlock, 0, s>>>(a, grad_t, grad_grid);
-    else k_backward<GL_PLAIN_F32><<<(unsigned)blocks, kBwdBlock, 0, s>>>(a, grad_t, grad_grid);
+    TraceArgs b = a;
+    b.pairs = nullptr;
+    if (b.cells) k_backward<GL_CELLS_F32><<<(unsigned)blocks, kBwdBlock, 0, s>>>(b, grad_t, grad_grid);
+    else k_backward<GL_PLAIN_F32><<<(unsigned)blocks, kBwdBlock, 0, s>>>(b, grad_t, grad_grid);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }

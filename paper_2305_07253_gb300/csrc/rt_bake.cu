@@ -224,10 +224,44 @@ __global__ void k_cells(const void* grid, int32_t f16, int32_t nx, int32_t ny, i
     }
 }
 
+// x-pair copy: entry (i,j,k) = (g[i,j,k], g[i+1,j,k]), i < nx-1, x fastest
+__global__ void k_pairs(const void* grid, int32_t f16, int32_t nx, int32_t ny, int32_t nz, void* pairs)
+{
+    const int64_t px = nx - 1;
+    const int64_t count = px * ny * (int64_t)nz;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= count) return;
+    const int64_t i = c % px, jk = c / px;
+    const int64_t b = i + (int64_t)nx * jk;
+    if (f16) {
+        const __half* g = reinterpret_cast<const __half*>(grid);
+        reinterpret_cast<__half2*>(pairs)[c] = __halves2half2(g[b], g[b + 1]);
+    } else {
+        const float* g = reinterpret_cast<const float*>(grid);
+        reinterpret_cast<float2*>(pairs)[c] = make_float2(g[b], g[b + 1]);
+    }
+}
+
 }  // namespace
 
 rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s)
 {
+    {
+        const int64_t pc = (int64_t)(sdf->n[0] - 1) * sdf->n[1] * sdf->n[2];
+        const int64_t pb = pc * (sdf->dtype == RT_GRID_F16 ? 4 : 8);
+        if (!sdf->pairs || sdf->pairs_bytes != pb) {
+            if (sdf->pairs) cudaFree(sdf->pairs);
+            sdf->pairs = nullptr;
+            sdf->pairs_bytes = 0;
+            RT_CUDA_TRY(cudaMalloc(&sdf->pairs, (size_t)pb));
+            sdf->pairs_bytes = pb;
+        }
+        const int64_t blocks = (pc + 255) / 256;
+        if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "grid too large");
+        k_pairs<<<(unsigned)blocks, 256, 0, s>>>(sdf->grid, sdf->dtype == RT_GRID_F16, sdf->n[0], sdf->n[1],
+                                                 sdf->n[2], sdf->pairs);
+        RT_CUDA_TRY(cudaGetLastError());
+    }
     const int64_t count = (int64_t)(sdf->n[0] - 1) * (sdf->n[1] - 1) * (sdf->n[2] - 1);
     const int64_t bytes = count * (sdf->dtype == RT_GRID_F16 ? 16 : 32);
     if (!sdf->cells || sdf->cells_bytes != bytes) {

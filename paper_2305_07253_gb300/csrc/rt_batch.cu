@@ -387,7 +387,7 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
     TraceArgs a;
     rt_fill_trace_args(a, need_scene ? sc : nullptr, need_grid ? sdf : nullptr, p0);
     const rt_tuning& tu = rt_current_tuning();
-    if (tu.grid_layout == RT_LAYOUT_PLAIN) a.cells = nullptr;
+    rt_apply_layout(a, tu);
     a.n = total;
     a.counters = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
@@ -422,6 +422,8 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
                 RT_BATCH_FIELD(GL_PLAIN_F16)
                 RT_BATCH_FIELD(GL_CELLS_F32)
                 RT_BATCH_FIELD(GL_CELLS_F16)
+                RT_BATCH_FIELD(GL_PAIRS_F32)
+                RT_BATCH_FIELD(GL_PAIRS_F16)
 #undef RT_BATCH_FIELD
             }
         } else if (k == 1) {

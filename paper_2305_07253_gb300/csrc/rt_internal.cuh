@@ -23,6 +23,10 @@
 //            stored together (32 B float32 / 16 B float16 per cell, cells x
 //            fastest), so one march step is one vector load instead of eight
 //            scalar ones; identical values, identical arithmetic
+//   pairs  : optional library copy with the two x-neighbours (i, i+1) of every
+//            sample stored together (8 B float32 / 4 B float16, (n0-1) x n1 x n2,
+//            x fastest): a march step is four small loads from a copy twice the
+//            grid's size, small enough to stay in L2 where the cell copy is not
 #pragma once
 
 #include <cuda_fp16.h>
@@ -67,6 +71,8 @@ struct rt_sdf {
     int32_t n[3];
     void* cells;        // library-owned cell-corner copy (null until rt_sdf_prepare)
     int64_t cells_bytes;
+    void* pairs;        // library-owned x-pair copy (null until rt_sdf_prepare)
+    int64_t pairs_bytes;
     int device;
 };
 
@@ -78,7 +84,8 @@ struct TraceArgs {
     const float4* wtris;
     int32_t root;        // 0 (internal), ~0 (single leaf) or INT32_MIN (no triangles)
     const void* grid;    // null: no field
-    const void* cells;   // null: read the plain grid
+    const void* cells;   // null: read the plain grid (or the pairs)
+    const void* pairs;   // null: no x-pair copy
     int32_t grid_f16;
     float glo[3], ghi[3], gih[3];
     int32_t gn[3];
@@ -104,6 +111,14 @@ rt_status rt_cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 const rt_tuning& rt_current_tuning();
+
+// which grid copy the march reads under a tuning: the cell copy, the x-pair copy
+// or the plain grid (a copy is used only if rt_sdf_prepare has built it)
+inline void rt_apply_layout(TraceArgs& a, const rt_tuning& tu)
+{
+    if (tu.grid_layout != RT_LAYOUT_CELLS) a.cells = nullptr;
+    if (tu.grid_layout != RT_LAYOUT_PAIRS) a.pairs = nullptr;
+}
 
 // launchers implemented in the .cu files
 // timing: when non-null, events[k] is recorded before launch k and events[n] after

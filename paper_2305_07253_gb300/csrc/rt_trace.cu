@@ -363,6 +363,8 @@ rt_status launch_stage(const TraceArgs& a, const StageArgs& st, const rt_tuning&
             RT_FIELD_CASE(GL_PLAIN_F16)
             RT_FIELD_CASE(GL_CELLS_F32)
             RT_FIELD_CASE(GL_CELLS_F16)
+            RT_FIELD_CASE(GL_PAIRS_F32)
+            RT_FIELD_CASE(GL_PAIRS_F16)
 #undef RT_FIELD_CASE
         }
     } else if (a.wnodes) {
@@ -453,13 +455,26 @@ rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s,
     return rs;
 }
 
+template <bool C, bool W>
+void launch_simple(const TraceArgs& a, int L, unsigned nb, int block, cudaStream_t s)
+{
+    switch (L) {
+    case GL_PLAIN_F32: k_trace<C, GL_PLAIN_F32, W><<<nb, block, 0, s>>>(a); break;
+    case GL_PLAIN_F16: k_trace<C, GL_PLAIN_F16, W><<<nb, block, 0, s>>>(a); break;
+    case GL_CELLS_F32: k_trace<C, GL_CELLS_F32, W><<<nb, block, 0, s>>>(a); break;
+    case GL_CELLS_F16: k_trace<C, GL_CELLS_F16, W><<<nb, block, 0, s>>>(a); break;
+    case GL_PAIRS_F32: k_trace<C, GL_PAIRS_F32, W><<<nb, block, 0, s>>>(a); break;
+    default: k_trace<C, GL_PAIRS_F16, W><<<nb, block, 0, s>>>(a); break;
+    }
+}
+
 }  // namespace
 
 rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, StageTiming* timing)
 {
     const rt_tuning& tu = rt_current_tuning();
     TraceArgs a = a0;
-    if (tu.grid_layout == RT_LAYOUT_PLAIN) a.cells = nullptr;
+    rt_apply_layout(a, tu);
     if (tu.kernel == RT_KERNEL_WAVEFRONT)
         return counted ? run_wavefront<true>(a, tu, s, timing) : run_wavefront<false>(a, tu, s, timing);
     const int64_t blocks = (a.n + tu.block - 1) / tu.block;
@@ -469,28 +484,14 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
         timing->kinds[0] = RT_STAGE_ALL;
     }
     {
-        const int sel = grid_layout_of(a) + (counted ? 4 : 0) + (a.wnodes ? 8 : 0);
         const unsigned nb = (unsigned)blocks;
-        switch (sel) {
-#define RT_SIMPLE_CASE(K, C, LL, W) \
-    case K: k_trace<C, LL, W><<<nb, tu.block, 0, s>>>(a); break;
-            RT_SIMPLE_CASE(0, false, GL_PLAIN_F32, false)
-            RT_SIMPLE_CASE(1, false, GL_PLAIN_F16, false)
-            RT_SIMPLE_CASE(2, false, GL_CELLS_F32, false)
-            RT_SIMPLE_CASE(3, false, GL_CELLS_F16, false)
-            RT_SIMPLE_CASE(4, true, GL_PLAIN_F32, false)
-            RT_SIMPLE_CASE(5, true, GL_PLAIN_F16, false)
-            RT_SIMPLE_CASE(6, true, GL_CELLS_F32, false)
-            RT_SIMPLE_CASE(7, true, GL_CELLS_F16, false)
-            RT_SIMPLE_CASE(8, false, GL_PLAIN_F32, true)
-            RT_SIMPLE_CASE(9, false, GL_PLAIN_F16, true)
-            RT_SIMPLE_CASE(10, false, GL_CELLS_F32, true)
-            RT_SIMPLE_CASE(11, false, GL_CELLS_F16, true)
-            RT_SIMPLE_CASE(12, true, GL_PLAIN_F32, true)
-            RT_SIMPLE_CASE(13, true, GL_PLAIN_F16, true)
-            RT_SIMPLE_CASE(14, true, GL_CELLS_F32, true)
-            default: k_trace<true, GL_CELLS_F16, true><<<nb, tu.block, 0, s>>>(a); break;
-#undef RT_SIMPLE_CASE
+        const int L = grid_layout_of(a);
+        if (a.wnodes) {
+            if (counted) launch_simple<true, true>(a, L, nb, tu.block, s);
+            else launch_simple<false, true>(a, L, nb, tu.block, s);
+        } else {
+            if (counted) launch_simple<true, false>(a, L, nb, tu.block, s);
+            else launch_simple<false, false>(a, L, nb, tu.block, s);
         }
     }
     RT_CUDA_TRY(cudaGetLastError());
@@ -587,7 +588,7 @@ extern "C" rt_status rt_trace_combined_noalloc(const rt_scene* sc, const rt_sdf*
     a.n = n;
     a.counters = nullptr;
     const rt_tuning& tu = rt_current_tuning();
-    if (tu.grid_layout == RT_LAYOUT_PLAIN) a.cells = nullptr;
+    rt_apply_layout(a, tu);
     cudaStream_t s = (cudaStream_t)stream;
 
     int kinds[3];

@@ -413,11 +413,12 @@ __device__ __forceinline__ bool bvh_segment(const TraceArgs& a, float3 o, float3
 // Grid storage seen by the march, fixed at compile time so that a step has no
 // layout or type branches: the caller's plain grid (float32 / float16) or the
 // library's cell-corner copy (float32 / float16).
-enum GridLayout { GL_PLAIN_F32 = 0, GL_PLAIN_F16 = 1, GL_CELLS_F32 = 2, GL_CELLS_F16 = 3 };
+enum GridLayout { GL_PLAIN_F32 = 0, GL_PLAIN_F16 = 1, GL_CELLS_F32 = 2, GL_CELLS_F16 = 3, GL_PAIRS_F32 = 4,
+                  GL_PAIRS_F16 = 5 };
 
 __host__ __device__ __forceinline__ int grid_layout_of(const TraceArgs& a)
 {
-    return (a.cells ? 2 : 0) + (a.grid_f16 ? 1 : 0);
+    return (a.cells ? 2 : (a.pairs ? 4 : 0)) + (a.grid_f16 ? 1 : 0);
 }
 
 template <int L>
@@ -478,6 +479,25 @@ __device__ __forceinline__ void corners(const TraceArgs& a, const Cell& c, float
     }
     if (L == GL_CELLS_F32) {
         ldg8(reinterpret_cast<const float*>(a.cells) + 8 * cell_index(a, c), v);
+        return;
+    }
+    if (L == GL_PAIRS_F32 || L == GL_PAIRS_F16) {
+        const int64_t px = a.gn[0] - 1;
+        const int64_t p00 = c.i0[0] + px * (c.i0[1] + (int64_t)a.gn[1] * c.i0[2]);
+        const int64_t sy = px, sz = px * a.gn[1];
+        const int64_t idx[4] = {p00, p00 + sy, p00 + sz, p00 + sz + sy};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (L == GL_PAIRS_F32) {
+                const float2 e = __ldg(reinterpret_cast<const float2*>(a.pairs) + idx[q]);
+                v[2 * q] = e.x;
+                v[2 * q + 1] = e.y;
+            } else {
+                const __half2 e = __ldg(reinterpret_cast<const __half2*>(a.pairs) + idx[q]);
+                v[2 * q] = __low2float(e);
+                v[2 * q + 1] = __high2float(e);
+            }
+        }
         return;
     }
     const int64_t b = grid_base(a, c);

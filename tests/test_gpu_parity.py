@@ -56,6 +56,8 @@ TUNINGS = {
     "wavefront-refill1-b64": dict(kernel=0, grid_layout=0, refill_min=1, block=64),
     "wavefront-refill32-b256": dict(kernel=0, grid_layout=0, refill_min=32, block=256, blocks_per_sm=2),
     "wavefront-bvh8": dict(kernel=0, bvh_width=8),
+    "wavefront-pairs": dict(kernel=0, grid_layout=2),
+    "simple-pairs": dict(kernel=1, grid_layout=2),
     "simple-bvh8": dict(kernel=1, bvh_width=8),
 }
 
