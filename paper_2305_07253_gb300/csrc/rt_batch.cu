@@ -200,7 +200,7 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
 }
 
 template <bool COUNT, int L>
-__global__ void k_batch_field(const TraceArgs a, const BatchTable tb, const Pipe pp)
+__global__ void __maxnreg__(40) k_batch_field(const TraceArgs a, const BatchTable tb, const Pipe pp)
 {
     __shared__ BatchEntry stb[RT_MAX_BATCHES];
     stage_table(tb, stb);
