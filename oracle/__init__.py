@@ -72,6 +72,15 @@ def lib():
             L.or_trace_combined.argtypes = [P, P, P, i64, P, i32, i32, P]
             L.or_grid_sample.argtypes = [P, P, i64, P, P]
             L.or_sdf_root_adjoint.argtypes = [P, P, i64, P, P, P, P]
+            L.or_grid_new_lattice.argtypes = [P, ctypes.c_double, P, P, P]
+            L.or_grid_new_lattice.restype = P
+            L.or_cascade_new.argtypes = [P, ctypes.c_double, i32, i32, P, P]
+            L.or_cascade_new.restype = P
+            L.or_cascade_free.argtypes = [P]
+            L.or_cascade_level_grid.argtypes = [P, i32, P, P, P]
+            L.or_cascade_level_grid.restype = i32
+            L.or_cascade_level_of.argtypes = [P, P, i64, i32, P]
+            L.or_trace_combined_cascade.argtypes = [P, P, P, i64, P, i32, i32, P, P]
             _lib = L
     return _lib
 
@@ -205,6 +214,69 @@ class Grid:
         return phi, grad
 
 
+class Cascade:
+    """Camera-centred cascade of `levels` grids of n^3 samples (Section 3, "Distance
+    Field Generation").  Level k: voxel h0 * 2^k, samples at (ilo_k + i) * h_k with
+    ilo_k = floor(center / h_k) - (n-1)//2.  values: (levels, n, n, n) or None to
+    evaluate samples on first use from `src`."""
+
+    def __init__(self, center, h0: float, n: int, levels: int, values=None, src: BVH | None = None):
+        self.center = _f64(center)
+        self.h0 = float(h0)
+        self.n = int(n)
+        self.levels = int(levels)
+        self.src = src
+        self._vals = None if values is None else _f64(values).reshape(-1)
+        if self._vals is not None:
+            assert self._vals.size == self.levels * self.n ** 3
+        self.h = lib().or_cascade_new(_ptr(self.center), self.h0, self.n, self.levels,
+                                      _ptr(self._vals) if self._vals is not None else None,
+                                      src.h if src is not None else None)
+        if not self.h:
+            raise ValueError("cascade needs 1..16 levels, n >= 2, h0 > 0 and values or a source BVH")
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.or_cascade_free(self.h)
+            self.h = None
+
+    def level(self, k: int):
+        """(ilo (3,) int64, h) of level k."""
+        ilo = np.zeros(3, dtype=np.int64)
+        h = ctypes.c_double(0.0)
+        if not lib().or_cascade_level_grid(self.h, int(k), _ptr(ilo), ctypes.byref(h), None):
+            raise IndexError(k)
+        return ilo, h.value
+
+    def box(self, k: int):
+        ilo, h = self.level(k)
+        return ilo * h, (ilo + self.n - 1) * h
+
+    def points(self, k: int) -> np.ndarray:
+        """Sample positions of level k, x fastest (fp64)."""
+        ilo, h = self.level(k)
+        r = np.arange(self.n)
+        kk, jj, ii = np.meshgrid(r, r, r, indexing="ij")
+        return np.stack([(ilo[0] + ii) * h, (ilo[1] + jj) * h, (ilo[2] + kk) * h], axis=-1).reshape(-1, 3)
+
+    def values(self, k: int, idx, nthreads: int | None = None) -> np.ndarray:
+        g = ctypes.c_void_p()
+        ilo = np.zeros(3, dtype=np.int64)
+        h = ctypes.c_double(0.0)
+        if not lib().or_cascade_level_grid(self.h, int(k), _ptr(ilo), ctypes.byref(h), ctypes.byref(g)):
+            raise IndexError(k)
+        idx = np.ascontiguousarray(idx, dtype=np.int64).reshape(-1)
+        out = np.zeros(idx.size)
+        lib().or_grid_values(g, _ptr(idx), idx.size, nthreads or default_threads(), _ptr(out))
+        return out
+
+    def level_of(self, P, precision: int = 64) -> np.ndarray:
+        P = _f64(P).reshape(-1, 3)
+        out = np.zeros(P.shape[0], dtype=np.int32)
+        lib().or_cascade_level_of(self.h, _ptr(P), P.shape[0], int(precision), _ptr(out))
+        return out
+
+
 def make_params(mode=1, any_hit=False, m_near=2.0, m_far=2.0, max_steps=256, hit_eps_vox=0.01,
                 min_step_vox=0.01) -> Params:
     return Params(int(mode), int(any_hit), float(m_near), float(m_far), int(max_steps), 0, float(hit_eps_vox),
@@ -219,10 +291,18 @@ def trace_sdf(grid: Grid, rays, params: Params, precision: int = 64, nthreads: i
     return hits
 
 
-def trace_combined(bvh: BVH | None, grid: Grid | None, rays, params: Params, precision: int = 64,
-                   nthreads: int | None = None):
+def trace_combined(bvh: BVH | None, grid: Grid | Cascade | None, rays, params: Params, precision: int = 64,
+                   nthreads: int | None = None, split_points: bool = False):
+    """Combined query on one grid or on a cascade.  split_points=True also returns
+    (n, 2) t_1, t_2 of each split query (NaN where the query has no split; cascade only)."""
     R = _rays(rays)
     hits = np.zeros(R.shape[0], dtype=HIT_DTYPE)
+    if isinstance(grid, Cascade):
+        t12 = np.full((R.shape[0], 2), np.nan)
+        lib().or_trace_combined_cascade(bvh.h if bvh else None, grid.h, _ptr(R), R.shape[0], ctypes.byref(params),
+                                        precision, nthreads or default_threads(), _ptr(hits), _ptr(t12))
+        return (hits, t12) if split_points else hits
+    assert not split_points, "split points are reported for cascades"
     lib().or_trace_combined(bvh.h if bvh else None, grid.h if grid else None, _ptr(R), R.shape[0],
                             ctypes.byref(params), precision, nthreads or default_threads(), _ptr(hits))
     return hits

@@ -683,14 +683,24 @@ struct or_grid {
     double* val;
     uint8_t* known; /* NULL when dense */
     const or_bvh* src;
+    int32_t lattice;  /* 1: sample (i,j,k) sits at (ilo + (i,j,k)) * h */
+    int64_t ilo[3];
 };
+
+static void sample_position(const or_grid* g, int64_t ix, int64_t iy, int64_t iz, double p[3])
+{
+    const int64_t ii[3] = {ix, iy, iz};
+    for (int a = 0; a < 3; ++a)
+        p[a] = g->lattice ? (double)(g->ilo[a] + ii[a]) * g->h[a] : g->lo[a] + (double)ii[a] * g->h[a];
+}
 
 static double grid_get(const or_grid* g, int64_t i)
 {
     if (!g->known || __atomic_load_n(&g->known[i], __ATOMIC_ACQUIRE)) return g->val[i];
     int64_t nx = g->n[0], ny = g->n[1];
     int64_t ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
-    double p[3] = {g->lo[0] + (double)ix * g->h[0], g->lo[1] + (double)iy * g->h[1], g->lo[2] + (double)iz * g->h[2]};
+    double p[3];
+    sample_position(g, ix, iy, iz, p);
     double v = bvh_sdf_point(g->src, p, NULL);
     /* identical values may be written by several threads; each store is whole */
     uint64_t bitsv;
@@ -728,6 +738,29 @@ or_grid* or_grid_new(const double lo[3], const double hi[3], const int32_t n[3],
     return g;
 }
 
+or_grid* or_grid_new_lattice(const int64_t ilo[3], double h, const int32_t n[3], const double* values,
+                             const or_bvh* src)
+{
+    if (!(h > 0)) return NULL;
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (double)ilo[a] * h;
+        hi[a] = (double)(ilo[a] + n[a] - 1) * h;
+    }
+    or_grid* g = or_grid_new(lo, hi, n, values, src);
+    if (!g) return NULL;
+    g->lattice = 1;
+    for (int a = 0; a < 3; ++a) {
+        /* the spacing is h itself, not (hi - lo) / (n - 1) rounded again */
+        g->ilo[a] = ilo[a];
+        g->h[a] = h;
+        g->ih[a] = 1.0 / h;
+        g->h_f[a] = (float)h;
+        g->ih_f[a] = 1.0f / g->h_f[a];
+    }
+    return g;
+}
+
 void or_grid_free(or_grid* g)
 {
     if (!g) return;
@@ -754,6 +787,60 @@ void or_grid_values(or_grid* g, const int64_t* idx, int64_t count, int32_t nthre
     parallel_for(count, nthreads, 64, gv_range, &c);
 }
 
+/* ------------------------------------------------------------------------ */
+/* camera-centred cascade (Section 3, "Distance Field Generation")           */
+/* ------------------------------------------------------------------------ */
+#define OR_MAX_LEVELS 16
+struct or_cascade {
+    int32_t levels, n;
+    or_grid* lv[OR_MAX_LEVELS];
+};
+
+/* Level k: voxel h_k = h0 * 2^k; n samples per axis at (ilo_k + i) * h_k with
+ * ilo_k = floor(center / h_k) - floor((n - 1) / 2), so that the centre lies in
+ * the middle cell and a move of the centre by whole voxels moves the lattice
+ * origin by whole samples. */
+static void cascade_origin(const double center[3], double h0, int32_t n, int32_t k, int64_t ilo[3], double* h)
+{
+    *h = ldexp(h0, k);
+    for (int a = 0; a < 3; ++a) ilo[a] = (int64_t)floor(center[a] / *h) - (int64_t)((n - 1) / 2);
+}
+
+or_cascade* or_cascade_new(const double center[3], double h0, int32_t n, int32_t levels, const double* values,
+                           const or_bvh* src)
+{
+    if (levels < 1 || levels > OR_MAX_LEVELS || n < 2 || !(h0 > 0)) return NULL;
+    if (!values && !src) return NULL;
+    or_cascade* c = (or_cascade*)calloc(1, sizeof(or_cascade));
+    c->levels = levels;
+    c->n = n;
+    const int32_t nn[3] = {n, n, n};
+    const int64_t per = (int64_t)n * n * n;
+    for (int32_t k = 0; k < levels; ++k) {
+        int64_t ilo[3];
+        double h;
+        cascade_origin(center, h0, n, k, ilo, &h);
+        c->lv[k] = or_grid_new_lattice(ilo, h, nn, values ? values + k * per : NULL, src);
+    }
+    return c;
+}
+
+void or_cascade_free(or_cascade* c)
+{
+    if (!c) return;
+    for (int32_t k = 0; k < c->levels; ++k) or_grid_free(c->lv[k]);
+    free(c);
+}
+
+int32_t or_cascade_level_grid(const or_cascade* c, int32_t k, int64_t ilo[3], double* h, or_grid** grid)
+{
+    if (k < 0 || k >= c->levels) return 0;
+    for (int a = 0; a < 3; ++a) ilo[a] = c->lv[k]->ilo[a];
+    *h = c->lv[k]->h[0];
+    if (grid) *grid = c->lv[k];
+    return 1;
+}
+
 /* the two precisions of the distance-field segment */
 #define GRID_FETCH(g, i) ((REAL)grid_get((g), (i)))
 #define REAL double
@@ -763,6 +850,10 @@ void or_grid_values(or_grid* g, const int64_t* idx, int64_t count, int32_t nthre
 #define FMAX fmax
 #define FLOOR floor
 #define FABS fabs
+#define GLO(g) ((g)->lo)
+#define GHI(g) ((g)->hi)
+#define GIH(g) ((g)->ih)
+#define GH(g) ((g)->h)
 #include "march.inc"
 #undef REAL
 #undef SFX
@@ -771,6 +862,10 @@ void or_grid_values(or_grid* g, const int64_t* idx, int64_t count, int32_t nthre
 #undef FMAX
 #undef FLOOR
 #undef FABS
+#undef GLO
+#undef GHI
+#undef GIH
+#undef GH
 #define REAL float
 #define SFX(x) x##_f
 #define FMA fmaf
@@ -778,6 +873,10 @@ void or_grid_values(or_grid* g, const int64_t* idx, int64_t count, int32_t nthre
 #define FMAX fmaxf
 #define FLOOR floorf
 #define FABS fabsf
+#define GLO(g) ((g)->lo_f)
+#define GHI(g) ((g)->hi_f)
+#define GIH(g) ((g)->ih_f)
+#define GH(g) ((g)->h_f)
 #include "march.inc"
 #undef REAL
 #undef SFX
@@ -786,11 +885,25 @@ void or_grid_values(or_grid* g, const int64_t* idx, int64_t count, int32_t nthre
 #undef FMAX
 #undef FLOOR
 #undef FABS
+#undef GLO
+#undef GHI
+#undef GIH
+#undef GH
 
-/* distance-field segment [ta, tb] in the requested precision */
-static int sdf_segment(const or_grid* g, const float* ray, double ta, double tb, const or_params* p,
-                       int precision, or_hit* h)
+/* distance-field segment [ta, tb] in the requested precision, on one grid or
+ * on a cascade */
+static int sdf_segment(const or_grid* g, const or_cascade* cas, const float* ray, double ta, double tb,
+                       const or_params* p, int precision, or_hit* h)
 {
+    if (cas) {
+        if (precision == 32) {
+            float o[3] = {ray[0], ray[1], ray[2]}, d[3] = {ray[4], ray[5], ray[6]};
+            return march_cascade_f(cas, o, d, (float)ta, (float)tb, (float)p->hit_eps_vox, (float)p->min_step_vox,
+                                   p->max_steps, h);
+        }
+        double o[3] = {ray[0], ray[1], ray[2]}, d[3] = {ray[4], ray[5], ray[6]};
+        return march_cascade_d(cas, o, d, ta, tb, p->hit_eps_vox, p->min_step_vox, p->max_steps, h);
+    }
     if (precision == 32) {
         float o[3] = {ray[0], ray[1], ray[2]}, d[3] = {ray[4], ray[5], ray[6]};
         float hmin = fminf(fminf(g->h_f[0], g->h_f[1]), g->h_f[2]);
@@ -810,6 +923,8 @@ typedef struct {
     const or_params* p;
     int precision;
     or_hit* hits;
+    const or_cascade* cas; /* when set, the field is this cascade instead of g */
+    double* t12;           /* optional: the split points t_1, t_2 of each query */
 } comb_ctx;
 
 /* Eq. 2 split and the ordering rules of Section 2 for one query. */
@@ -826,39 +941,60 @@ static void combined_one(const comb_ctx* c, int64_t i)
         return;
     }
     int mode = p->mode;
-    if (mode == 0 || !c->g) {
+    const int have_field = c->g || c->cas;
+    if (mode == 0 || !have_field) {
         bvh_segment(c->b, o, d, tmin, tmax, p->any_hit, &h);
         c->hits[i] = h;
         return;
     }
     if (mode == 3 || !c->b) {
-        sdf_segment(c->g, r, tmin, tmax, p, c->precision, &h);
+        sdf_segment(c->g, c->cas, r, tmin, tmax, p, c->precision, &h);
         c->hits[i] = h;
         return;
     }
-    /* split points t_1 (and t_2) from the voxel size times the multipliers */
+    /* split points t_1 (and t_2) from the voxel size times the multipliers.
+     * One grid: its largest voxel edge.  Cascade (Section 3, "GI & Shadow
+     * Rays"): the voxel size at the start point o + t_min d for t_1 and at the
+     * end point o + t_max d for t_2. */
     double t1, t2;
     if (c->precision == 32) {
-        float hs = fmaxf(fmaxf(c->g->h_f[0], c->g->h_f[1]), c->g->h_f[2]);
         float a = (float)tmin, bb = (float)tmax;
-        float x1 = fminf(fmaxf(fmaf((float)p->m_near, hs, a), a), bb);
-        float x2 = fminf(fmaxf(fmaf(-(float)p->m_far, hs, bb), x1), bb);
+        float hn, hf;
+        if (c->cas) {
+            float of[3] = {r[0], r[1], r[2]}, df[3] = {r[4], r[5], r[6]};
+            hn = voxel_at_f(c->cas, of, df, a);
+            hf = voxel_at_f(c->cas, of, df, bb);
+        } else {
+            hn = hf = fmaxf(fmaxf(c->g->h_f[0], c->g->h_f[1]), c->g->h_f[2]);
+        }
+        float x1 = fminf(fmaxf(fmaf((float)p->m_near, hn, a), a), bb);
+        float x2 = fminf(fmaxf(fmaf(-(float)p->m_far, hf, bb), x1), bb);
         t1 = x1;
         t2 = x2;
     } else {
-        double hs = fmax(fmax(c->g->h[0], c->g->h[1]), c->g->h[2]);
-        t1 = fmin(fmax(fma(p->m_near, hs, tmin), tmin), tmax);
-        t2 = fmin(fmax(fma(-p->m_far, hs, tmax), t1), tmax);
+        double hn, hf;
+        if (c->cas) {
+            hn = voxel_at_d(c->cas, o, d, tmin);
+            hf = voxel_at_d(c->cas, o, d, tmax);
+        } else {
+            hn = hf = fmax(fmax(c->g->h[0], c->g->h[1]), c->g->h[2]);
+        }
+        t1 = fmin(fmax(fma(p->m_near, hn, tmin), tmin), tmax);
+        t2 = fmin(fmax(fma(-p->m_far, hf, tmax), t1), tmax);
+    }
+    if (c->t12) {
+        c->t12[2 * i] = t1;
+        c->t12[2 * i + 1] = mode == 1 ? tmax : t2;
     }
     int near_bvh = p->m_near > 0;
     if (mode == 1) {
         int field = (p->m_near == 0) || (t1 < tmax);
         if (p->any_hit) {
-            if (field && sdf_segment(c->g, r, t1, tmax, p, c->precision, &h)) { c->hits[i] = h; return; }
+            if (field && sdf_segment(c->g, c->cas, r, t1, tmax, p, c->precision, &h)) { c->hits[i] = h; return; }
             if (near_bvh) bvh_segment(c->b, o, d, tmin, t1, 1, &h);
         } else {
             if (near_bvh && bvh_segment(c->b, o, d, tmin, t1, 0, &h)) { c->hits[i] = h; return; }
-            if (field) sdf_segment(c->g, r, t1, tmax, p, c->precision, &h);
+            if (field) sdf_segment(c->g, c->cas, r, t1, tmax, p, c->precision, &h);
         }
         c->hits[i] = h;
         return;
@@ -867,12 +1003,12 @@ static void combined_one(const comb_ctx* c, int64_t i)
     int field = (t1 < t2) || (p->m_near == 0 && p->m_far == 0);
     int far_bvh = p->m_far > 0;
     if (p->any_hit) {
-        if (field && sdf_segment(c->g, r, t1, t2, p, c->precision, &h)) { c->hits[i] = h; return; }
+        if (field && sdf_segment(c->g, c->cas, r, t1, t2, p, c->precision, &h)) { c->hits[i] = h; return; }
         if (near_bvh && bvh_segment(c->b, o, d, tmin, t1, 1, &h)) { c->hits[i] = h; return; }
         if (far_bvh) bvh_segment(c->b, o, d, t2, tmax, 1, &h);
     } else {
         if (near_bvh && bvh_segment(c->b, o, d, tmin, t1, 0, &h)) { c->hits[i] = h; return; }
-        if (field && sdf_segment(c->g, r, t1, t2, p, c->precision, &h)) { c->hits[i] = h; return; }
+        if (field && sdf_segment(c->g, c->cas, r, t1, t2, p, c->precision, &h)) { c->hits[i] = h; return; }
         if (far_bvh) bvh_segment(c->b, o, d, t2, tmax, 0, &h);
     }
     c->hits[i] = h;
@@ -889,15 +1025,35 @@ void or_trace_sdf(const or_grid* g, const float* rays, int64_t nr, const or_para
 {
     or_params q = *p;
     q.mode = 3;
-    comb_ctx c = {NULL, g, rays, &q, precision, hits};
+    comb_ctx c = {NULL, g, rays, &q, precision, hits, NULL, NULL};
     parallel_for(nr, nthreads, 16, comb_range, &c);
 }
 
 void or_trace_combined(const or_bvh* b, const or_grid* g, const float* rays, int64_t nr,
                        const or_params* p, int32_t precision, int32_t nthreads, or_hit* hits)
 {
-    comb_ctx c = {b, g, rays, p, precision, hits};
+    comb_ctx c = {b, g, rays, p, precision, hits, NULL, NULL};
     parallel_for(nr, nthreads, 16, comb_range, &c);
+}
+
+void or_trace_combined_cascade(const or_bvh* b, const or_cascade* cas, const float* rays, int64_t nr,
+                               const or_params* p, int32_t precision, int32_t nthreads, or_hit* hits,
+                               double* t12)
+{
+    comb_ctx c = {b, NULL, rays, p, precision, hits, cas, t12};
+    parallel_for(nr, nthreads, 16, comb_range, &c);
+}
+
+void or_cascade_level_of(const or_cascade* c, const double* P, int64_t np, int32_t precision, int32_t* level)
+{
+    for (int64_t i = 0; i < np; ++i) {
+        if (precision == 32) {
+            float q[3] = {(float)P[3 * i], (float)P[3 * i + 1], (float)P[3 * i + 2]};
+            level[i] = level_of_f(c, q);
+        } else {
+            level[i] = level_of_d(c, P + 3 * i);
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -50,6 +50,7 @@ typedef struct {
 
 typedef struct or_bvh or_bvh;
 typedef struct or_grid or_grid;
+typedef struct or_cascade or_cascade;
 
 /* Watertight ray/triangle test (Woop, Benthin & Wald, JCGT 2(1), 2013), fp64.
  * Returns 1 when the ray's line meets the triangle; out = {t, u, v}. */
@@ -78,6 +79,10 @@ void or_sdf_points_bvh(const or_bvh* b, const double* P, int64_t np, int32_t nth
  * computed on first use from `src` by or_sdf_points_bvh. */
 or_grid* or_grid_new(const double lo[3], const double hi[3], const int32_t n[3], const double* values,
                      const or_bvh* src);
+/* Grid on an integer lattice: sample (i,j,k) at (ilo + (i,j,k)) * h, the same
+ * spacing h on every axis (h is used as given, not recomputed from the box). */
+or_grid* or_grid_new_lattice(const int64_t ilo[3], double h, const int32_t n[3], const double* values,
+                             const or_bvh* src);
 void or_grid_free(or_grid* g);
 void or_grid_values(or_grid* g, const int64_t* idx, int64_t count, int32_t nthreads, double* out);
 
@@ -88,6 +93,24 @@ void or_trace_sdf(const or_grid* g, const float* rays, int64_t nr, const or_para
                   int32_t nthreads, or_hit* hits);
 void or_trace_combined(const or_bvh* b, const or_grid* g, const float* rays, int64_t nr,
                        const or_params* p, int32_t precision, int32_t nthreads, or_hit* hits);
+
+/* Camera-centred cascade of `levels` lattice grids of n^3 samples (Section 3,
+ * "Distance Field Generation").  Level k has voxel h0 * 2^k and lattice origin
+ * ilo_k = floor(center / h_k) - floor((n-1)/2) per axis.  values (nullable):
+ * levels * n^3 doubles, level after level, x fastest; NULL evaluates them on
+ * first use from `src`.  Tracing on a cascade samples, at each march step, the
+ * finest level whose box holds the point, with eps_hit and eps_min scaled by
+ * that level's voxel; the split points use the voxel at the query's start
+ * (t_1) and end (t_2) points.  t12 (nullable, 2 per ray) receives t_1 and t_2
+ * of split queries (mode 1 reports t_2 = t_max). */
+or_cascade* or_cascade_new(const double center[3], double h0, int32_t n, int32_t levels, const double* values,
+                           const or_bvh* src);
+void or_cascade_free(or_cascade* c);
+int32_t or_cascade_level_grid(const or_cascade* c, int32_t k, int64_t ilo[3], double* h, or_grid** grid);
+void or_cascade_level_of(const or_cascade* c, const double* P, int64_t np, int32_t precision, int32_t* level);
+void or_trace_combined_cascade(const or_bvh* b, const or_cascade* c, const float* rays, int64_t nr,
+                               const or_params* p, int32_t precision, int32_t nthreads, or_hit* hits,
+                               double* t12);
 
 /* Trilinear value and gradient of the grid interpolant at points (fp64). */
 void or_grid_sample(const or_grid* g, const double* P, int64_t np, double* phi, double* grad);
