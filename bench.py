@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="set up, then run only warmup+steps launches of the --only traces (for ncu); prints timings")
     ap.add_argument("--only", default="all", choices=["all", "combined", "bvh", "sdf"])
-    ap.add_argument("--workload", default="frame", choices=["frame", "batching", "fit", "precision", "ao"],
+    ap.add_argument("--workload", default="frame", choices=["frame", "batching", "fit", "precision", "ao", "cascade"],
                     help="frame: the 1080p GI headline; batching: 8 frames of mixed primary/shadow/AO/GI "
                          "batches; fit: gradient fit of a noisy 128^3 grid; precision: float16 vs float32 "
                          "512^3 grid on the 8.2 M-triangle scene")
@@ -689,8 +689,8 @@ def run_precision(args):
 def run_ao(args):
     """Ambient occlusion with the three tracers (the numeric form of the paper's
     AO comparison, Section 3 "Occlusion Queries" and Fig. 2): 262,144 camera-facing
-    surface points, 16 cosine rays each, t in [0, t_ao]; AO = fraction of rays
-    that hit.  For each t_ao and split multiplier: tracing time, and the AO error
+    surface points, 16 cosine rays each, t in [0, t_ao]; AO = share of a point's
+    rays that reach t_ao unoccluded.  For each t_ao and split multiplier: tracing time, and the AO error
     against triangles only (mean |dAO|, mean signed dAO = darkening, share of
     points off by more than 0.1)."""
     import torch
@@ -747,6 +747,107 @@ def run_ao(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_ms(fn, reps, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_cascade(args):
+    """The paper's distance-field set-up (Section 3, "Distance Field Generation"):
+    camera-centred cascades of 5 levels, 64^3 with a 0.1 m finest voxel for the
+    combined query and 128^3 with 0.05 m for field-only tracing, on the frame
+    scene.  Reports, per form: 1080p GI tracing time (t_max 30 m; combined: one
+    split, m = 2, t_1 from the voxel at the ray's origin) and agreement with
+    triangles only; AO (t_ao = 2 m, 16 rays per point) time and error against
+    triangles only; the cost of a full cascade bake and of rolling updates (the
+    camera moving one finest voxel per axis per frame, Section 3)."""
+    import torch
+
+    import paper_2305_07253_gb300 as rq
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    s = S.make_scene("frame")
+    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
+    eye = np.asarray(s.camera.eye, dtype=np.float32)
+    K = max(5, args.steps // 10)
+    forms = {"combined": (64, 0.1), "field_only": (128, 0.05)}
+    cas = {}
+    bake_ms = {}
+    for name, (n, h0) in forms.items():
+        g = torch.empty((5, n, n, n), dtype=torch.float32, device=dev)
+        sdf = rq.rt_cascade_create(g, h0, eye)
+        bake_ms[name] = _time_ms(lambda: rq.rt_sdf_bake(scene, sdf, rq.BAKE_BVH), 3, warm=1)
+        cas[name] = (g, sdf)
+    gi = torch.from_numpy(R.gi_rays(s, 1920 * 1080, 7, 30.0)).to(dev)
+    p_pts, nn = R.surface_points(s, 1 << 18, 31)
+    ao_rays = torch.from_numpy(R.ao_rays(p_pts, nn, np.full(1 << 18, 16, dtype=np.int64), 32, 2.0,
+                                         1e-3 * s.diagonal)).to(dev)
+    out = {"bake_ms": bake_ms, "gi": {}, "ao": {}}
+    hits = torch.empty((gi.shape[0], 6), dtype=torch.int32, device=dev)
+    ao_hits = torch.empty((ao_rays.shape[0], 6), dtype=torch.int32, device=dev)
+    runs = {"bvh_only": (None, rq.split_params(mode=rq.MODE_BVH)),
+            "combined": (cas["combined"][1], rq.split_params(mode=rq.MODE_SPLIT1, m_near=M_MIDDLE)),
+            "field_only": (cas["field_only"][1], rq.split_params(mode=rq.MODE_SDF)),
+            "field_only_coarse": (cas["combined"][1], rq.split_params(mode=rq.MODE_SDF))}
+    ref_t = ref_ao = None
+    for name, (sdf, prm) in runs.items():
+        ms = _time_ms(lambda: rq.rt_trace_combined(scene, sdf, gi, prm, hits), K)
+        f = rq.hit_fields(hits)
+        t = f["t"].double()
+        if ref_t is None:
+            ref_t = t.clone()
+        both = torch.isfinite(t) & torch.isfinite(ref_t)
+        rel = ((t - ref_t).abs() / ref_t.clamp(min=1e-6))[both]
+        out["gi"][name] = {"ms": ms, "rays_per_s": gi.shape[0] / (ms * 1e-3),
+                           "hit_agreement": float((torch.isfinite(t) == torch.isfinite(ref_t)).float().mean()),
+                           "mean_rel_dt": float(rel.mean()) if rel.numel() else 0.0,
+                           "share_rel_dt_above_1pct": float((rel > 0.01).float().mean()) if rel.numel() else 0.0}
+        ms = _time_ms(lambda: rq.rt_trace_combined(scene, sdf, ao_rays, prm, ao_hits), K)
+        ao = 1.0 - (ao_hits[:, 4] > 0).float().reshape(-1, 16).mean(dim=1)
+        if ref_ao is None:
+            ref_ao = ao.clone()
+        d = ao - ref_ao
+        out["ao"][name] = {"ms": ms, "mean_abs_dAO": float(d.abs().mean()), "mean_dAO": float(d.mean()),
+                           "share_off_0.1": float((d.abs() > 0.1).float().mean())}
+    # rolling updates: the camera walks one finest voxel per axis per frame
+    roll = {}
+    for name, (n, h0) in forms.items():
+        g, sdf = cas[name]
+        frames = 64
+        times, moved = [], []
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        c = eye.astype(np.float64)
+        for f in range(frames):
+            c = c + np.float32(h0)
+            e[0].record()
+            moved.append(rq.rt_cascade_recenter(scene, sdf, c.astype(np.float32)))
+            e[1].record()
+            torch.cuda.synchronize()
+            times.append(e[0].elapsed_time(e[1]))
+        times = np.array(times[4:])
+        roll[name] = {"mean_ms": float(times.mean()), "max_ms": float(times.max()),
+                      "levels_moved_per_frame": float(np.mean(moved[4:])), "frames": frames - 4}
+    out["rolling"] = roll
+    line = {"metric": "cascaded distance field: GI and AO tracing, error vs triangles only, cascade update cost",
+            "value": out["gi"]["combined"]["rays_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic (seeded procedural scene and rays)", "dtype": "f32",
+            "config": {"workload": "frame-cascade", "n_tris": int(s.n_tris), "levels": 5,
+                       "combined": {"n": 64, "h0": 0.1}, "field_only": {"n": 128, "h0": 0.05},
+                       "gi_rays": int(gi.shape[0]), "ao_rays": int(ao_rays.shape[0]), "m": M_MIDDLE},
+            "cascade": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -759,6 +860,8 @@ def main():
         run_precision(args)
     elif args.workload == "ao":
         run_ao(args)
+    elif args.workload == "cascade":
+        run_cascade(args)
     else:
         run_ours(args)
 

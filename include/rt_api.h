@@ -153,8 +153,8 @@ rt_status rt_scene_destroy(rt_scene* scene);
  * h = (hi - lo) / (n - 1) per axis, x fastest: value (i,j,k) is at element
  * i + n0*(j + n1*k).  dtype RT_GRID_F32 or RT_GRID_F16 (converted exactly to
  * float for the arithmetic).  n >= 2 per axis, hi > lo.  The paper's field is
- * a set of camera-centred cascades (Section 3, "Distance Field Generation");
- * this library uses one dense grid. */
+ * a set of camera-centred cascades (Section 3, "Distance Field Generation"):
+ * see rt_cascade_create; this call describes one dense grid. */
 rt_status rt_sdf_create(const void* d_grid, int32_t dtype, const float lo[3], const float hi[3],
                         const int32_t n[3], rt_sdf** out);
 rt_status rt_sdf_destroy(rt_sdf* sdf);
@@ -168,7 +168,8 @@ rt_status rt_sdf_destroy(rt_sdf* sdf);
  * Traces read the plain grid until the first prepare, or when the tuning
  * selects the plain layout.  Also builds the x-pair copy (see rt_tuning).
  * Memory: about 8x (cells) + 2x (pairs) the grid, owned by the handle,
- * released by rt_sdf_destroy.  Enqueued on `stream`. */
+ * released by rt_sdf_destroy.  On a cascade: the cell copy of every level
+ * (no x-pair copy).  Enqueued on `stream`. */
 rt_status rt_sdf_prepare(rt_sdf* sdf, void* stream);
 
 /* Fill the grid of `sdf` with the signed distance to the nearest triangle of
@@ -179,8 +180,60 @@ rt_status rt_sdf_prepare(rt_sdf* sdf, void* stream);
  * definition.  method: RT_BAKE_BRUTE tests every triangle for every sample
  * (triangles staged through shared memory); RT_BAKE_BVH prunes with the BVH
  * (same result up to float rounding); RT_BAKE_AUTO picks by problem size.  Writes through the
- * grid pointer given to rt_sdf_create. */
+ * grid pointer given to rt_sdf_create.  On a cascade (rt_cascade_create) every
+ * level is baked at its lattice points (ilo_k + i) * h_k, each coordinate
+ * rounded once from that product, so that a level moved by rt_cascade_recenter
+ * holds the same values as one baked at its new place. */
 rt_status rt_sdf_bake(const rt_scene* scene, rt_sdf* sdf, int32_t method, void* stream);
+
+#define RT_MAX_LEVELS 8
+
+/* Camera-centred cascade of distance-field grids (Section 3, "Distance Field
+ * Generation": the field is built in cascades centred on the camera, with
+ * smaller voxels close to it; 5 levels of 64^3 with a 0.1 m smallest voxel in
+ * the paper's combined set-up, twice the resolution for field-only tracing).
+ *   d_grid  caller memory of levels * n^3 values of `dtype` (RT_GRID_F32 or
+ *           RT_GRID_F16), level after level, x fastest within a level, 16-byte
+ *           aligned; not copied, must outlive the handle
+ *   levels  1..RT_MAX_LEVELS;  n: samples per axis of every level, 2..1024
+ *   h0      voxel edge of the finest level (finite, > 0); level k has
+ *           h_k = h0 * 2^k, the same on all three axes
+ *   center  the camera position (finite)
+ * Level k's samples sit at (ilo_k + (i,j,l)) * h_k with, per axis,
+ * ilo_k = floor(center / h_k) - floor((n-1)/2): the centre lies in the middle
+ * cell of every level, and the levels nest.  The handle is accepted wherever
+ * an rt_sdf is; on a cascade the queries use, at each march step, the
+ * trilinear sample of the finest level whose closed box holds the point (the
+ * coarsest level's outside all boxes), with eps_hit and eps_min scaled by
+ * that level's voxel instead of the grid's smallest voxel edge; t_1 uses
+ * the voxel at the query's start point o + t_min d and t_2 the voxel at its end
+ * point o + t_max d (Section 3, "GI & Shadow Rays"); the march is clipped to
+ * the coarsest level's box.  A cascade is always read through its cell-corner
+ * copy: fill it with rt_sdf_bake (or write the values and call rt_sdf_prepare)
+ * before tracing; a trace before that returns RT_ERR_INVALID_ARG, as does
+ * rt_trace_combined_backward on a cascade.  Errors: RT_ERR_INVALID_ARG for
+ * the argument rules above or |center / h0| >= 2^22. */
+rt_status rt_cascade_create(const void* d_grid, int32_t dtype, int32_t levels, int32_t n, float h0,
+                            const float center[3], rt_sdf** out);
+
+/* Rolling update (Section 3, "Distance Field Generation": when the camera
+ * moves, only the cascade slices that changed are rebuilt).  Moves the
+ * cascade to a new centre.  Every level whose lattice origin changes keeps the
+ * samples that the old and new lattices share (moved within its memory) and
+ * fills only the new slices with the exact distance of rt_sdf_bake (BVH
+ * method); a level that moved by n or more samples on an axis is baked
+ * whole.  The cell-corner copy of each changed level is rebuilt.  The values
+ * equal those of a full rt_sdf_bake at the new centre.  Enqueued on
+ * `stream`; uses a device scratch of one level owned by the handle (allocated
+ * on the first call).  *moved (nullable) receives the number of levels that
+ * changed.  Errors: RT_ERR_INVALID_ARG (not a cascade, null or non-finite
+ * centre, |center / h0| >= 2^22), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_cascade_recenter(const rt_scene* scene, rt_sdf* sdf, const float center[3], void* stream,
+                              int32_t* moved);
+
+/* Geometry of level k of a cascade: lattice origin ilo[3] and voxel edge *h.
+ * Errors: RT_ERR_INVALID_ARG when sdf is not a cascade or k is out of range. */
+rt_status rt_cascade_level(const rt_sdf* sdf, int32_t k, int32_t ilo[3], float* h);
 
 /* The pure triangle technique: closest hit (any_hit = 0) or any hit
  * (any_hit = 1) on [t_min, t_max] for n rays.  d_rays: n rt_ray; d_hits: n
@@ -279,7 +332,7 @@ rt_status rt_trace_batches(const rt_scene* scene, const rt_sdf* sdf, const rt_ba
  * Queries with grad phi . d > -1e-6 (tangent), a field hit at the start of
  * the sub-interval, or another tracer contribute nothing.  The forward pass
  * is not stored: the kernel re-marches each ray.  The grid must be
- * RT_GRID_F32. */
+ * RT_GRID_F32 and not a cascade. */
 rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays,
                                      int64_t n, const rt_split_params* params, const rt_hit* d_hits,
                                      const float* d_grad_t, float* d_grad_grid, void* stream);

@@ -38,7 +38,7 @@ EXPORTS = ("rt_scene_build", "rt_scene_info_get", "rt_scene_destroy", "rt_sdf_cr
            "rt_sdf_prepare", "rt_sdf_bake", "rt_trace_bvh", "rt_trace_sdf", "rt_trace_combined",
            "rt_trace_combined_counted", "rt_trace_combined_timed", "rt_trace_combined_noalloc",
            "rt_trace_combined_backward", "rt_trace_batches", "rt_set_tuning", "rt_get_tuning",
-           "rt_last_error", "rt_version")
+           "rt_cascade_create", "rt_cascade_recenter", "rt_cascade_level", "rt_last_error", "rt_version")
 
 
 class RtError(RuntimeError):
@@ -110,6 +110,9 @@ def lib() -> ctypes.CDLL:
             "rt_trace_combined_noalloc": [P, P, P, i64, P, P, P],
             "rt_trace_batches": [P, P, P, i32, P],
             "rt_trace_combined_backward": [P, P, P, i64, P, P, P, P, P],
+            "rt_cascade_create": [P, i32, i32, i32, ctypes.c_float, P, P],
+            "rt_cascade_recenter": [P, P, P, P, P],
+            "rt_cascade_level": [P, i32, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -175,13 +178,16 @@ class Scene:
 
 
 class Sdf:
-    """rt_sdf handle describing a dense grid tensor (nz, ny, nx); keeps the tensor alive."""
+    """rt_sdf handle describing a dense grid tensor (nz, ny, nx), or a cascade
+    tensor (levels, n, n, n); keeps the tensor alive."""
 
-    def __init__(self, handle: int, grid: torch.Tensor, lo, hi):
+    def __init__(self, handle: int, grid: torch.Tensor, lo, hi, levels: int = 0, h0: float = 0.0):
         self.handle = ctypes.c_void_p(handle)
         self.grid = grid
         self.lo = tuple(float(v) for v in lo)
         self.hi = tuple(float(v) for v in hi)
+        self.levels = levels
+        self.h0 = h0
 
     def close(self) -> None:
         if self.handle and _lib is not None:
@@ -210,6 +216,49 @@ def rt_sdf_create(grid: torch.Tensor, lo, hi) -> Sdf:
     out = ctypes.c_void_p()
     _check(lib().rt_sdf_create(_dptr(grid), dtype, _f3(lo), _f3(hi), n, ctypes.byref(out)))
     return Sdf(out.value, grid, lo, hi)
+
+
+MAX_LEVELS = 8
+
+
+def rt_cascade_create(grid: torch.Tensor, h0: float, center) -> Sdf:
+    """Wrap a (levels, n, n, n) float32/float16 CUDA tensor as a camera-centred
+    cascade: level k has voxel h0 * 2^k and lattice origin
+    floor(center / h_k) - (n-1)//2 per axis."""
+    if grid.dim() != 4 or not (grid.shape[1] == grid.shape[2] == grid.shape[3]):
+        raise ValueError("cascade grid must be (levels, n, n, n)")
+    dtype = {torch.float32: GRID_F32, torch.float16: GRID_F16}[grid.dtype]
+    out = ctypes.c_void_p()
+    _check(lib().rt_cascade_create(_dptr(grid), dtype, grid.shape[0], grid.shape[1], float(h0), _f3(center),
+                                   ctypes.byref(out)))
+    sdf = Sdf(out.value, grid, (0, 0, 0), (0, 0, 0), levels=grid.shape[0], h0=float(h0))
+    lo, hi = rt_cascade_box(sdf, sdf.levels - 1)
+    sdf.lo, sdf.hi = tuple(lo), tuple(hi)
+    return sdf
+
+
+def rt_cascade_level(sdf: Sdf, k: int):
+    """(ilo (3 ints), h) of level k."""
+    ilo = (ctypes.c_int32 * 3)()
+    h = ctypes.c_float()
+    _check(lib().rt_cascade_level(sdf.handle, int(k), ilo, ctypes.byref(h)))
+    return tuple(ilo), h.value
+
+
+def rt_cascade_box(sdf: Sdf, k: int):
+    """Box [lo, hi] of level k (float64 of the lattice corners)."""
+    ilo, h = rt_cascade_level(sdf, k)
+    n = sdf.grid.shape[1]
+    return [i * h for i in ilo], [(i + n - 1) * h for i in ilo]
+
+
+def rt_cascade_recenter(scene: Scene, sdf: Sdf, center, stream=None) -> int:
+    """Rolling update to a new centre; returns the number of levels that moved."""
+    moved = ctypes.c_int32(0)
+    _check(lib().rt_cascade_recenter(scene.handle, sdf.handle, _f3(center), _stream(stream), ctypes.byref(moved)))
+    lo, hi = rt_cascade_box(sdf, sdf.levels - 1)
+    sdf.lo, sdf.hi = tuple(lo), tuple(hi)
+    return moved.value
 
 
 def rt_sdf_bake(scene: Scene, sdf: Sdf, method: int = BAKE_AUTO, stream=None) -> None:

@@ -86,8 +86,23 @@ static rt_status check_io(const rt_ray* rays, int64_t n, const rt_hit* hits)
     return RT_OK;
 }
 
+// Cascade level k as the queries see it: h = h0 * 2^k (exact), box corners
+// (float)ilo * h and (float)(ilo + n - 1) * h rounded once, ih = 1 / h rounded once.
+void rt_cascade_geometry(const rt_sdf* sdf, int k, float lo[3], float hi[3], float* h, float* ih)
+{
+    const float hk = ldexpf(sdf->h0, k);
+    for (int a = 0; a < 3; ++a) {
+        volatile float l = (float)sdf->ilo[k][a] * hk;
+        volatile float u = (float)(sdf->ilo[k][a] + sdf->n[a] - 1) * hk;
+        lo[a] = l;
+        hi[a] = u;
+    }
+    *h = hk;
+    *ih = 1.0f / hk;
+}
+
 // Host-side set-up of the split (the same float operations the queries use).
-void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, const rt_split_params* p)
+rt_status rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, const rt_split_params* p)
 {
     memset(&a, 0, sizeof(a));
     if (sc) {
@@ -116,6 +131,19 @@ void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, con
         a.hsplit = fmaxf(fmaxf(sdf->h[0], sdf->h[1]), sdf->h[2]);
         a.eps_hit = p->hit_eps_vox * hmin;
         a.eps_min = p->min_step_vox * hmin;
+        if (sdf->levels > 0) {
+            if (!sdf->cells)
+                return rt_fail(RT_ERR_INVALID_ARG, "cascade has no cell copy yet: call rt_sdf_bake or rt_sdf_prepare");
+            a.levels = sdf->levels;
+            const int64_t c = sdf->n[0] - 1;
+            a.level_cells = c * c * c;
+            for (int k = 0; k < sdf->levels; ++k) {
+                CascLevel& v = a.lv[k];
+                rt_cascade_geometry(sdf, k, v.lo, v.hi, &v.h, &v.ih);
+                v.eps_hit = p->hit_eps_vox * v.h;
+                v.eps_min = p->min_step_vox * v.h;
+            }
+        }
     }
     a.max_steps = p->max_steps;
     a.mode = p->mode;
@@ -123,6 +151,7 @@ void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, con
     a.refine_root = p->refine_root;
     a.m_near = p->m_near;
     a.m_far = p->m_far;
+    return RT_OK;
 }
 
 static rt_status device_matches(int dev)
@@ -206,10 +235,7 @@ extern "C" rt_status rt_sdf_create(const void* d_grid, int32_t dtype, const floa
     if (cnt > ((int64_t)1 << 40)) return rt_fail(RT_ERR_INVALID_ARG, "grid too large");
     rt_sdf* g = new (std::nothrow) rt_sdf();
     if (!g) return rt_fail(RT_ERR_OOM, "host allocation failed");
-    g->cells = nullptr;
-    g->cells_bytes = 0;
-    g->pairs = nullptr;
-    g->pairs_bytes = 0;
+    memset(g, 0, sizeof(*g));
     cudaGetDevice(&g->device);
     g->grid = d_grid;
     g->dtype = dtype;
@@ -231,7 +257,125 @@ extern "C" rt_status rt_sdf_destroy(rt_sdf* sdf)
     if (!sdf) return RT_OK;
     if (sdf->cells) cudaFree(sdf->cells);
     if (sdf->pairs) cudaFree(sdf->pairs);
+    if (sdf->scratch) cudaFree(sdf->scratch);
     delete sdf;
+    return RT_OK;
+}
+
+// lattice origin of level k around `center` (floor taken in double)
+static bool cascade_origin(const float center[3], float h0, int32_t n, int k, int32_t ilo[3])
+{
+    const double hk = ldexp((double)h0, k);
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(center[a]) || !(fabs((double)center[a] / (double)h0) < 4194304.0)) return false;
+        ilo[a] = (int32_t)floor((double)center[a] / hk) - (n - 1) / 2;
+    }
+    return true;
+}
+
+extern "C" rt_status rt_cascade_create(const void* d_grid, int32_t dtype, int32_t levels, int32_t n, float h0,
+                                       const float center[3], rt_sdf** out)
+{
+    if (!out) return rt_fail(RT_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (!d_grid || !center) return rt_fail(RT_ERR_INVALID_ARG, "null argument");
+    if (dtype != RT_GRID_F32 && dtype != RT_GRID_F16) return rt_fail(RT_ERR_INVALID_ARG, "dtype %d", dtype);
+    if (!aligned16(d_grid)) return rt_fail(RT_ERR_INVALID_ARG, "grid not 16-byte aligned");
+    if (levels < 1 || levels > RT_MAX_LEVELS)
+        return rt_fail(RT_ERR_INVALID_ARG, "levels %d not in 1..%d", levels, RT_MAX_LEVELS);
+    if (n < 2 || n > 1024) return rt_fail(RT_ERR_INVALID_ARG, "n %d not in 2..1024", n);
+    if (!(h0 > 0.f) || isinf(h0)) return rt_fail(RT_ERR_INVALID_ARG, "h0 must be finite and > 0");
+    rt_sdf* g = new (std::nothrow) rt_sdf();
+    if (!g) return rt_fail(RT_ERR_OOM, "host allocation failed");
+    memset(g, 0, sizeof(*g));
+    cudaGetDevice(&g->device);
+    g->grid = d_grid;
+    g->dtype = dtype;
+    g->levels = levels;
+    g->h0 = h0;
+    for (int k = 0; k < levels; ++k) {
+        if (!cascade_origin(center, h0, n, k, g->ilo[k])) {
+            delete g;
+            return rt_fail(RT_ERR_INVALID_ARG, "centre must be finite with |center / h0| < 2^22");
+        }
+    }
+    for (int a = 0; a < 3; ++a) g->n[a] = n;
+    // the coarsest level's box clips every march
+    float lo[3], hi[3], h, ih;
+    rt_cascade_geometry(g, levels - 1, lo, hi, &h, &ih);
+    for (int a = 0; a < 3; ++a) {
+        g->lo[a] = lo[a];
+        g->hi[a] = hi[a];
+        g->h[a] = h;
+        g->ih[a] = ih;
+    }
+    *out = g;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_cascade_level(const rt_sdf* sdf, int32_t k, int32_t ilo[3], float* h)
+{
+    if (!sdf || !ilo || !h) return rt_fail(RT_ERR_INVALID_ARG, "null argument");
+    if (sdf->levels < 1) return rt_fail(RT_ERR_INVALID_ARG, "not a cascade");
+    if (k < 0 || k >= sdf->levels) return rt_fail(RT_ERR_INVALID_ARG, "level %d not in 0..%d", k, sdf->levels - 1);
+    for (int a = 0; a < 3; ++a) ilo[a] = sdf->ilo[k][a];
+    *h = ldexpf(sdf->h0, k);
+    return RT_OK;
+}
+
+extern "C" rt_status rt_cascade_recenter(const rt_scene* sc, rt_sdf* sdf, const float center[3], void* stream,
+                                         int32_t* moved)
+{
+    if (moved) *moved = 0;
+    if (!sc || !sdf || !center) return rt_fail(RT_ERR_INVALID_ARG, "null argument");
+    if (sdf->levels < 1) return rt_fail(RT_ERR_INVALID_ARG, "not a cascade");
+    rt_status st = device_matches(sc->device);
+    if (st != RT_OK) return st;
+    int32_t ilo[RT_MAX_LEVELS][3];
+    for (int k = 0; k < sdf->levels; ++k)
+        if (!cascade_origin(center, sdf->h0, sdf->n[0], k, ilo[k]))
+            return rt_fail(RT_ERR_INVALID_ARG, "centre must be finite with |center / h0| < 2^22");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = sdf->n[0];
+    const int64_t level_bytes = n * n * n * (sdf->dtype == RT_GRID_F16 ? 2 : 4);
+    if (!sdf->cells) {
+        st = rt_launch_prepare(sdf, s);  // allocates the cell copy
+        if (st != RT_OK) return st;
+    }
+    int32_t count = 0;
+    for (int k = 0; k < sdf->levels; ++k) {
+        int32_t shift[3];
+        bool same = true, far = false;
+        for (int a = 0; a < 3; ++a) {
+            shift[a] = ilo[k][a] - sdf->ilo[k][a];
+            same = same && shift[a] == 0;
+            far = far || shift[a] >= n || shift[a] <= -n;
+        }
+        if (same) continue;
+        const void* keep = nullptr;
+        if (!far) {
+            if (!sdf->scratch) {
+                RT_CUDA_TRY(cudaMalloc(&sdf->scratch, (size_t)level_bytes));
+                sdf->scratch_bytes = level_bytes;
+            }
+            const char* src = static_cast<const char*>(sdf->grid) + k * level_bytes;
+            RT_CUDA_TRY(cudaMemcpyAsync(sdf->scratch, src, (size_t)level_bytes, cudaMemcpyDeviceToDevice, s));
+            keep = sdf->scratch;
+        }
+        for (int a = 0; a < 3; ++a) sdf->ilo[k][a] = ilo[k][a];
+        st = rt_launch_cascade_bake(sc, sdf, k, RT_BAKE_BVH, keep, shift, s);
+        if (st != RT_OK) return st;
+        st = rt_launch_cascade_cells(sdf, k, s);
+        if (st != RT_OK) return st;
+        ++count;
+    }
+    float lo[3], hi[3], h, ih;
+    rt_cascade_geometry(sdf, sdf->levels - 1, lo, hi, &h, &ih);
+    for (int a = 0; a < 3; ++a) {
+        sdf->lo[a] = lo[a];
+        sdf->hi[a] = hi[a];
+    }
+    if (moved) *moved = count;
     return RT_OK;
 }
 
@@ -271,7 +415,8 @@ static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ra
     if (counters && ((uintptr_t)counters & 7u)) return rt_fail(RT_ERR_INVALID_ARG, "counters misaligned");
     if (n == 0) return RT_OK;
     TraceArgs a;
-    rt_fill_trace_args(a, p->mode == RT_MODE_SDF ? nullptr : sc, p->mode == RT_MODE_BVH ? nullptr : sdf, p);
+    st = rt_fill_trace_args(a, p->mode == RT_MODE_SDF ? nullptr : sc, p->mode == RT_MODE_BVH ? nullptr : sdf, p);
+    if (st != RT_OK) return st;
     a.rays = reinterpret_cast<const float4*>(rays);
     a.hits = hits;
     a.n = n;
@@ -353,12 +498,14 @@ extern "C" rt_status rt_trace_combined_backward(const rt_scene* sc, const rt_sdf
     if (st != RT_OK) return st;
     if (!sdf) return rt_fail(RT_ERR_INVALID_ARG, "grid is null");
     if (sdf->dtype != RT_GRID_F32) return rt_fail(RT_ERR_INVALID_ARG, "backward needs a float32 grid");
+    if (sdf->levels > 0) return rt_fail(RT_ERR_INVALID_ARG, "backward does not take a cascade");
     if (n > 0 && (!grad_t || !grad_grid)) return rt_fail(RT_ERR_INVALID_ARG, "null gradient buffer");
     if (params->mode != RT_MODE_SDF && params->mode != RT_MODE_BVH && !sc)
         return rt_fail(RT_ERR_INVALID_ARG, "combined modes need the scene");
     if (n == 0) return RT_OK;
     TraceArgs a;
-    rt_fill_trace_args(a, params->mode == RT_MODE_SDF ? nullptr : sc, sdf, params);
+    st = rt_fill_trace_args(a, params->mode == RT_MODE_SDF ? nullptr : sc, sdf, params);
+    if (st != RT_OK) return st;
     a.rays = reinterpret_cast<const float4*>(rays);
     a.hits = const_cast<rt_hit*>(hits);
     a.n = n;

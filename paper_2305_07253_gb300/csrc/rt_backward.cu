@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kBwdBlock) k_backward(const TraceArgs a, const
     const float3 o = make_float3(r0.x, r0.y, r0.z), d = make_float3(r1.x, r1.y, r1.z);
     float ts = r0.w, te = r1.w;
     if (a.mode == RT_MODE_SPLIT1 || a.mode == RT_MODE_SPLIT2) {
-        Split s = make_split(a, r0.w, r1.w);
+        Split s = make_split(a, o, d, r0.w, r1.w);
         ts = s.t1;
         te = s.t2;
     }

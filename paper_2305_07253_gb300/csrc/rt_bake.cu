@@ -10,6 +10,7 @@
 // Two kernels with the same result: brute force (every triangle, staged through
 // shared memory in tiles) and a BVH-pruned nearest query.
 #include <math.h>
+#include <string.h>
 
 #include "rt_trace_dev.cuh"
 
@@ -105,13 +106,37 @@ struct BakeArgs {
     float lo[3], h[3];
     int32_t n[3];
     int64_t count;
+    // cascade level: samples at (ilo + i) * h[0], one rounding per coordinate,
+    // so a sample's position depends only on its absolute lattice index
+    int32_t lattice;
+    int32_t ilo[3];
+    // rolling update: when set, sample i takes the value of sample i + shift of
+    // `keep` (the level before the move) wherever that lies inside the level
+    const void* keep;
+    int32_t shift[3];
 };
 
 __device__ __forceinline__ float3 sample_pos(const BakeArgs& b, int64_t i)
 {
     int64_t ix = i % b.n[0], iy = (i / b.n[0]) % b.n[1], iz = i / ((int64_t)b.n[0] * b.n[1]);
+    if (b.lattice)
+        return make_float3(__fmul_rn((float)(b.ilo[0] + ix), b.h[0]), __fmul_rn((float)(b.ilo[1] + iy), b.h[0]),
+                           __fmul_rn((float)(b.ilo[2] + iz), b.h[0]));
     return make_float3(fmaf((float)ix, b.h[0], b.lo[0]), fmaf((float)iy, b.h[1], b.lo[1]),
                        fmaf((float)iz, b.h[2], b.lo[2]));
+}
+
+// rolling update: copy the kept value of sample i; false when i must be baked
+__device__ __forceinline__ bool take_kept(const BakeArgs& b, int64_t i)
+{
+    if (!b.keep) return false;
+    const int64_t nx = b.n[0], ny = b.n[1];
+    const int64_t ix = i % nx + b.shift[0], iy = (i / nx) % ny + b.shift[1], iz = i / (nx * ny) + b.shift[2];
+    if (ix < 0 || ix >= nx || iy < 0 || iy >= ny || iz < 0 || iz >= b.n[2]) return false;
+    const int64_t src = ix + nx * (iy + ny * iz);
+    if (b.f16) reinterpret_cast<__half*>(b.grid)[i] = reinterpret_cast<const __half*>(b.keep)[src];
+    else reinterpret_cast<float*>(b.grid)[i] = reinterpret_cast<const float*>(b.keep)[src];
+    return true;
 }
 
 __device__ __forceinline__ void store(const BakeArgs& b, int64_t i, float v)
@@ -124,7 +149,7 @@ __global__ void __launch_bounds__(kBakeBlock) k_bake_brute(const BakeArgs b)
 {
     __shared__ float4 tile[3 * kTile];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < b.count;
+    const bool live = i < b.count && !take_kept(b, i);  // every thread stays for the barriers
     const float3 p = sample_pos(b, live ? i : 0);
     Nearest nb = {__int_as_float(0x7f800000), -1, 0x7fffffff};
     for (int64_t t0 = 0; t0 < b.n_tris; t0 += kTile) {
@@ -161,7 +186,7 @@ __device__ __forceinline__ float box_d2(float lx, float hx, float ly, float hy, 
 __global__ void __launch_bounds__(kBakeBlock) k_bake_bvh(const BakeArgs b)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.count) return;
+    if (i >= b.count || take_kept(b, i)) return;
     const float3 p = sample_pos(b, i);
     Nearest nb = {__int_as_float(0x7f800000), -1, 0x7fffffff};
     int stack[RT_STACK_DEPTH];
@@ -245,8 +270,38 @@ __global__ void k_pairs(const void* grid, int32_t f16, int32_t nx, int32_t ny, i
 
 }  // namespace
 
+rt_status rt_launch_cascade_cells(const rt_sdf* sdf, int k, cudaStream_t s)
+{
+    const int64_t n = sdf->n[0];
+    const int64_t count = (n - 1) * (n - 1) * (n - 1);
+    const int64_t esz = sdf->dtype == RT_GRID_F16 ? 2 : 4;
+    const void* grid = static_cast<const char*>(sdf->grid) + k * n * n * n * esz;
+    void* cells = static_cast<char*>(sdf->cells) + k * count * 8 * esz;
+    const int64_t blocks = (count + 255) / 256;
+    k_cells<<<(unsigned)blocks, 256, 0, s>>>(grid, sdf->dtype == RT_GRID_F16, (int32_t)n, (int32_t)n, (int32_t)n,
+                                             cells);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
 rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s)
 {
+    if (sdf->levels > 0) {
+        const int64_t n = sdf->n[0];
+        const int64_t bytes = sdf->levels * (n - 1) * (n - 1) * (n - 1) * (sdf->dtype == RT_GRID_F16 ? 16 : 32);
+        if (!sdf->cells || sdf->cells_bytes != bytes) {
+            if (sdf->cells) cudaFree(sdf->cells);
+            sdf->cells = nullptr;
+            sdf->cells_bytes = 0;
+            RT_CUDA_TRY(cudaMalloc(&sdf->cells, (size_t)bytes));
+            sdf->cells_bytes = bytes;
+        }
+        for (int k = 0; k < sdf->levels; ++k) {
+            rt_status st = rt_launch_cascade_cells(sdf, k, s);
+            if (st != RT_OK) return st;
+        }
+        return RT_OK;
+    }
     {
         const int64_t pc = (int64_t)(sdf->n[0] - 1) * sdf->n[1] * sdf->n[2];
         const int64_t pb = pc * (sdf->dtype == RT_GRID_F16 ? 4 : 8);
@@ -280,9 +335,53 @@ rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s)
     return RT_OK;
 }
 
-rt_status rt_launch_bake(const rt_scene* sc, const rt_sdf* sdf, int32_t method, cudaStream_t s)
+static rt_status launch_bake_args(BakeArgs& b, int32_t method, cudaStream_t s)
+{
+    if (method == RT_BAKE_AUTO) method = (double)b.count * (double)b.n_tris <= 17179869184.0 ? RT_BAKE_BRUTE : RT_BAKE_BVH;
+    const int64_t blocks = (b.count + kBakeBlock - 1) / kBakeBlock;
+    if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "grid too large for one launch");
+    if (method == RT_BAKE_BRUTE) k_bake_brute<<<(unsigned)blocks, kBakeBlock, 0, s>>>(b);
+    else k_bake_bvh<<<(unsigned)blocks, kBakeBlock, 0, s>>>(b);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status rt_launch_cascade_bake(const rt_scene* sc, const rt_sdf* sdf, int k, int32_t method, const void* keep,
+                                 const int32_t shift[3], cudaStream_t s)
 {
     BakeArgs b;
+    memset(&b, 0, sizeof(b));
+    b.nodes = sc->nodes;
+    b.tris = sc->tris;
+    b.pn = sc->pn;
+    b.n_tris = sc->n_tris;
+    const int64_t n = sdf->n[0];
+    const int64_t esz = sdf->dtype == RT_GRID_F16 ? 2 : 4;
+    b.grid = static_cast<char*>(const_cast<void*>(sdf->grid)) + k * n * n * n * esz;
+    b.f16 = sdf->dtype == RT_GRID_F16;
+    b.count = n * n * n;
+    b.lattice = 1;
+    b.h[0] = b.h[1] = b.h[2] = ldexpf(sdf->h0, k);
+    for (int a = 0; a < 3; ++a) {
+        b.n[a] = (int32_t)n;
+        b.ilo[a] = sdf->ilo[k][a];
+        b.shift[a] = shift ? shift[a] : 0;
+    }
+    b.keep = keep;
+    return launch_bake_args(b, method, s);
+}
+
+rt_status rt_launch_bake(const rt_scene* sc, const rt_sdf* sdf, int32_t method, cudaStream_t s)
+{
+    if (sdf->levels > 0) {
+        for (int k = 0; k < sdf->levels; ++k) {
+            rt_status st = rt_launch_cascade_bake(sc, sdf, k, method, nullptr, nullptr, s);
+            if (st != RT_OK) return st;
+        }
+        return RT_OK;
+    }
+    BakeArgs b;
+    memset(&b, 0, sizeof(b));
     b.nodes = sc->nodes;
     b.tris = sc->tris;
     b.pn = sc->pn;
@@ -296,11 +395,5 @@ rt_status rt_launch_bake(const rt_scene* sc, const rt_sdf* sdf, int32_t method, 
         b.n[k] = sdf->n[k];
         b.count *= sdf->n[k];
     }
-    if (method == RT_BAKE_AUTO) method = (double)b.count * (double)b.n_tris <= 17179869184.0 ? RT_BAKE_BRUTE : RT_BAKE_BVH;
-    const int64_t blocks = (b.count + kBakeBlock - 1) / kBakeBlock;
-    if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "grid too large for one launch");
-    if (method == RT_BAKE_BRUTE) k_bake_brute<<<(unsigned)blocks, kBakeBlock, 0, s>>>(b);
-    else k_bake_bvh<<<(unsigned)blocks, kBakeBlock, 0, s>>>(b);
-    RT_CUDA_TRY(cudaGetLastError());
-    return RT_OK;
+    return launch_bake_args(b, method, s);
 }

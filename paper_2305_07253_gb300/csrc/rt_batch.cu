@@ -162,7 +162,9 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
                 float ta = tmin, tb2 = tmax;
                 bool active = true;
                 if (seg != SEG_B_FULL) {
-                    const Split sp = make_split(e.mode, e.m_near, e.m_far, a.hsplit, tmin, tmax);
+                    float hn, hf;
+                    split_voxels(a, o, d, tmin, tmax, hn, hf);
+                    const Split sp = make_split(e.mode, e.m_near, e.m_far, hn, hf, tmin, tmax);
                     if (seg == SEG_B_NEAR) { ta = tmin; tb2 = sp.t1; active = sp.near_bvh; }
                     else { ta = sp.t2; tb2 = tmax; active = sp.far_bvh; }
                 }
@@ -245,7 +247,9 @@ __global__ void __maxnreg__(40) k_batch_field(const TraceArgs a, const BatchTabl
                 tb2 = tmax;
                 bool active = true;
                 if (seg == SEG_F_SPLIT) {
-                    const Split sp = make_split(e.mode, e.m_near, e.m_far, a.hsplit, tmin, tmax);
+                    float hn, hf;
+                    split_voxels(a, o, d, tmin, tmax, hn, hf);
+                    const Split sp = make_split(e.mode, e.m_near, e.m_far, hn, hf, tmin, tmax);
                     ta = sp.t1;
                     tb2 = sp.t2;
                     active = sp.field;
@@ -385,7 +389,8 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
     if (st != RT_OK) return st;
 
     TraceArgs a;
-    rt_fill_trace_args(a, need_scene ? sc : nullptr, need_grid ? sdf : nullptr, p0);
+    st = rt_fill_trace_args(a, need_scene ? sc : nullptr, need_grid ? sdf : nullptr, p0);
+    if (st != RT_OK) return st;
     const rt_tuning& tu = rt_current_tuning();
     rt_apply_layout(a, tu);
     a.n = total;
@@ -424,6 +429,8 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
                 RT_BATCH_FIELD(GL_CELLS_F16)
                 RT_BATCH_FIELD(GL_PAIRS_F32)
                 RT_BATCH_FIELD(GL_PAIRS_F16)
+                RT_BATCH_FIELD(GL_CASC_F32)
+                RT_BATCH_FIELD(GL_CASC_F16)
 #undef RT_BATCH_FIELD
             }
         } else if (k == 1) {

@@ -67,13 +67,26 @@ struct rt_scene {
 struct rt_sdf {
     const void* grid;
     int32_t dtype;
-    float lo[3], hi[3], h[3], ih[3];
+    float lo[3], hi[3], h[3], ih[3];  // one grid; on a cascade: the coarsest level's box
     int32_t n[3];
     void* cells;        // library-owned cell-corner copy (null until rt_sdf_prepare)
     int64_t cells_bytes;
     void* pairs;        // library-owned x-pair copy (null until rt_sdf_prepare)
     int64_t pairs_bytes;
     int device;
+    // cascade (levels > 0): level k holds n^3 samples at (ilo[k] + i) * h0 * 2^k,
+    // stored at grid + k * n^3, its cells at cells + k * (n-1)^3
+    int32_t levels;
+    float h0;
+    int32_t ilo[RT_MAX_LEVELS][3];
+    void* scratch;      // one level, for rt_cascade_recenter
+    int64_t scratch_bytes;
+};
+
+// geometry of cascade level k as the queries see it (float, rounded once each)
+struct CascLevel {
+    float lo[3], hi[3];
+    float ih, h, eps_hit, eps_min;
 };
 
 // Everything one trace kernel needs, passed by value.
@@ -93,6 +106,9 @@ struct TraceArgs {
     int32_t max_steps;
     int32_t mode, any_hit, refine_root;
     float m_near, m_far;
+    int32_t levels;        // 0: one grid; > 0: a cascade read through its cell copy
+    int64_t level_cells;   // cells per cascade level
+    CascLevel lv[RT_MAX_LEVELS];
     const float4* rays;
     rt_hit* hits;
     int64_t n;
@@ -116,6 +132,10 @@ const rt_tuning& rt_current_tuning();
 // or the plain grid (a copy is used only if rt_sdf_prepare has built it)
 inline void rt_apply_layout(TraceArgs& a, const rt_tuning& tu)
 {
+    if (a.levels > 0) {  // a cascade has only its cell copy
+        a.pairs = nullptr;
+        return;
+    }
     if (tu.grid_layout != RT_LAYOUT_CELLS) a.cells = nullptr;
     if (tu.grid_layout != RT_LAYOUT_PAIRS) a.pairs = nullptr;
 }
@@ -137,4 +157,8 @@ rt_status rt_build_wide(rt_scene* sc, const int2* child, const int2* range, cons
                         const float4* node_hi, const float4* leaf_lo, const float4* leaf_hi, float pad,
                         cudaStream_t s);
 rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s);
-void rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, const rt_split_params* p);
+rt_status rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, const rt_split_params* p);
+void rt_cascade_geometry(const rt_sdf* sdf, int k, float lo[3], float hi[3], float* h, float* ih);
+rt_status rt_launch_cascade_bake(const rt_scene* sc, const rt_sdf* sdf, int k, int32_t method, const void* keep,
+                                 const int32_t shift[3], cudaStream_t s);
+rt_status rt_launch_cascade_cells(const rt_sdf* sdf, int k, cudaStream_t s);

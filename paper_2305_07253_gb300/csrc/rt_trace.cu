@@ -53,7 +53,7 @@ __device__ __forceinline__ void trace_one(const TraceArgs& a, int64_t i, Counts&
             h.t = (a.refine_root && !isnan(m.t_prev)) ? refine<L>(a, o, d, m.t_prev, m.t) : m.t;
         }
     } else {
-        const Split s = make_split(a, tmin, tmax);
+        const Split s = make_split(a, o, d, tmin, tmax);
         if (a.any_hit) {
             if (s.field) {
                 March m = sdf_march<COUNT, L>(a, o, d, s.t1, s.t2, flags, cnt);
@@ -137,7 +137,7 @@ __device__ __forceinline__ bool stage_segment(const TraceArgs& a, int kind, int6
         tb = tmax;
         return true;
     }
-    const Split s = make_split(a, tmin, tmax);
+    const Split s = make_split(a, o, d, tmin, tmax);
     if (kind == ST_BVH_NEAR) { ta = tmin; tb = s.t1; return s.near_bvh; }
     if (kind == ST_BVH_FAR) { ta = s.t2; tb = tmax; return s.far_bvh; }
     ta = s.t1;
@@ -367,6 +367,8 @@ rt_status launch_stage(const TraceArgs& a, const StageArgs& st, const rt_tuning&
             RT_FIELD_CASE(GL_CELLS_F16)
             RT_FIELD_CASE(GL_PAIRS_F32)
             RT_FIELD_CASE(GL_PAIRS_F16)
+            RT_FIELD_CASE(GL_CASC_F32)
+            RT_FIELD_CASE(GL_CASC_F16)
 #undef RT_FIELD_CASE
         }
     } else if (a.wnodes) {
@@ -466,7 +468,9 @@ void launch_simple(const TraceArgs& a, int L, unsigned nb, int block, cudaStream
     case GL_CELLS_F32: k_trace<C, GL_CELLS_F32, W><<<nb, block, 0, s>>>(a); break;
     case GL_CELLS_F16: k_trace<C, GL_CELLS_F16, W><<<nb, block, 0, s>>>(a); break;
     case GL_PAIRS_F32: k_trace<C, GL_PAIRS_F32, W><<<nb, block, 0, s>>>(a); break;
-    default: k_trace<C, GL_PAIRS_F16, W><<<nb, block, 0, s>>>(a); break;
+    case GL_PAIRS_F16: k_trace<C, GL_PAIRS_F16, W><<<nb, block, 0, s>>>(a); break;
+    case GL_CASC_F32: k_trace<C, GL_CASC_F32, W><<<nb, block, 0, s>>>(a); break;
+    default: k_trace<C, GL_CASC_F16, W><<<nb, block, 0, s>>>(a); break;
     }
 }
 
@@ -584,7 +588,8 @@ extern "C" rt_status rt_trace_combined_noalloc(const rt_scene* sc, const rt_sdf*
     if (st != RT_OK) return st;
 
     TraceArgs a;
-    rt_fill_trace_args(a, p->mode == RT_MODE_SDF ? nullptr : sc, p->mode == RT_MODE_BVH ? nullptr : sdf, p);
+    st = rt_fill_trace_args(a, p->mode == RT_MODE_SDF ? nullptr : sc, p->mode == RT_MODE_BVH ? nullptr : sdf, p);
+    if (st != RT_OK) return st;
     a.rays = reinterpret_cast<const float4*>(rays);
     a.hits = hits;
     a.n = n;

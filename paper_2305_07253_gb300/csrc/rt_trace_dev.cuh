@@ -414,10 +414,13 @@ __device__ __forceinline__ bool bvh_segment(const TraceArgs& a, float3 o, float3
 // layout or type branches: the caller's plain grid (float32 / float16) or the
 // library's cell-corner copy (float32 / float16).
 enum GridLayout { GL_PLAIN_F32 = 0, GL_PLAIN_F16 = 1, GL_CELLS_F32 = 2, GL_CELLS_F16 = 3, GL_PAIRS_F32 = 4,
-                  GL_PAIRS_F16 = 5 };
+                  GL_PAIRS_F16 = 5, GL_CASC_F32 = 6, GL_CASC_F16 = 7 };
+
+__host__ __device__ constexpr bool is_cascade(int L) { return L == GL_CASC_F32 || L == GL_CASC_F16; }
 
 __host__ __device__ __forceinline__ int grid_layout_of(const TraceArgs& a)
 {
+    if (a.levels > 0) return GL_CASC_F32 + (a.grid_f16 ? 1 : 0);
     return (a.cells ? 2 : (a.pairs ? 4 : 0)) + (a.grid_f16 ? 1 : 0);
 }
 
@@ -536,6 +539,80 @@ __device__ __forceinline__ float trilinear(const TraceArgs& a, float px, float p
     return lerp_rn(c.f[2], c0, c1);
 }
 
+// ---------------------------------------------------------------------------
+// cascade (Section 3, "Distance Field Generation"): the finest level whose
+// closed box holds p (the coarsest outside all boxes; a NaN point is outside
+// every box); trilinear sample of that level from its cells
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int casc_level(const TraceArgs& a, float px, float py, float pz)
+{
+    int k = 0;
+    for (; k < a.levels - 1; ++k) {
+        const CascLevel& v = a.lv[k];
+        if (px >= v.lo[0] && px <= v.hi[0] && py >= v.lo[1] && py <= v.hi[1] && pz >= v.lo[2] && pz <= v.hi[2])
+            break;
+    }
+    return k;
+}
+
+template <int L>
+__device__ __forceinline__ float casc_trilinear(const TraceArgs& a, int k, float px, float py, float pz)
+{
+    const CascLevel& lv = a.lv[k];
+    const float p[3] = {px, py, pz};
+    const float top = (float)(a.gn[0] - 1);
+    int i0[3];
+    float f[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        float u = __fmul_rn(__fsub_rn(p[ax], lv.lo[ax]), lv.ih);
+        u = fminf(fmaxf(u, 0.f), top);
+        int ii = (int)floorf(u);
+        if (ii > a.gn[0] - 2) ii = a.gn[0] - 2;
+        f[ax] = __fsub_rn(u, (float)ii);
+        i0[ax] = ii;
+    }
+    const int64_t idx = k * a.level_cells + cell_slot(i0[0], i0[1], i0[2], a.gn[0], a.gn[0]);
+    float v[8];
+    if (L == GL_CASC_F16) {
+        uint4 q = __ldg(reinterpret_cast<const uint4*>(a.cells) + idx);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            __half2 h2 = *reinterpret_cast<const __half2*>(&w[j]);
+            v[2 * j] = __low2float(h2);
+            v[2 * j + 1] = __high2float(h2);
+        }
+    } else {
+        ldg8(reinterpret_cast<const float*>(a.cells) + 8 * idx, v);
+    }
+    float c00 = lerp_rn(f[0], v[0], v[1]);
+    float c10 = lerp_rn(f[0], v[2], v[3]);
+    float c01 = lerp_rn(f[0], v[4], v[5]);
+    float c11 = lerp_rn(f[0], v[6], v[7]);
+    float c0 = lerp_rn(f[1], c00, c10);
+    float c1 = lerp_rn(f[1], c01, c11);
+    return lerp_rn(f[2], c0, c1);
+}
+
+// field value and the hit / minimum-step thresholds at p: one grid, or the
+// level of a cascade that holds p (thresholds scale with its voxel)
+template <int L>
+__device__ __forceinline__ float field_at(const TraceArgs& a, float px, float py, float pz, float& eps_hit,
+                                          float& eps_min)
+{
+    if constexpr (is_cascade(L)) {
+        const int k = casc_level(a, px, py, pz);
+        eps_hit = a.lv[k].eps_hit;
+        eps_min = a.lv[k].eps_min;
+        return casc_trilinear<L>(a, k, px, py, pz);
+    } else {
+        eps_hit = a.eps_hit;
+        eps_min = a.eps_min;
+        return trilinear<L>(a, px, py, pz);
+    }
+}
+
 __device__ __forceinline__ bool clip_grid(const TraceArgs& a, float3 o, float3 d, float& ta, float& tb)
 {
     const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
@@ -566,10 +643,11 @@ template <int L>
 __device__ __forceinline__ int march_step(const TraceArgs& a, float3 o, float3 d, float& t, float tb, float& t_prev)
 {
     float px = __fmaf_rn(t, d.x, o.x), py = __fmaf_rn(t, d.y, o.y), pz = __fmaf_rn(t, d.z, o.z);
-    float phi = trilinear<L>(a, px, py, pz);
-    if (phi < a.eps_hit) return 1;
+    float eps_hit, eps_min;
+    float phi = field_at<L>(a, px, py, pz, eps_hit, eps_min);
+    if (phi < eps_hit) return 1;
     t_prev = t;
-    t = __fadd_rn(t, fmaxf(phi, a.eps_min));
+    t = __fadd_rn(t, fmaxf(phi, eps_min));
     return t > tb ? 2 : 0;
 }
 
@@ -602,24 +680,29 @@ __device__ __forceinline__ float refine(const TraceArgs& a, float3 o, float3 d, 
     float lo = t_prev, hi = t;
     for (int it = 0; it < 24; ++it) {
         float mid = 0.5f * (lo + hi);
-        float phi = trilinear<L>(a, __fmaf_rn(mid, d.x, o.x), __fmaf_rn(mid, d.y, o.y), __fmaf_rn(mid, d.z, o.z));
-        if (phi < a.eps_hit) hi = mid; else lo = mid;
+        float eps_hit, eps_min;
+        float phi = field_at<L>(a, __fmaf_rn(mid, d.x, o.x), __fmaf_rn(mid, d.y, o.y), __fmaf_rn(mid, d.z, o.z),
+                                eps_hit, eps_min);
+        if (phi < eps_hit) hi = mid; else lo = mid;
     }
     return 0.5f * (lo + hi);
 }
 
-// Split points of Eq. 2 (Section 3): t_1 = clamp(t_min + m_near h, t_min, t_max),
-// t_2 = clamp(t_max - m_far h, t_1, t_max).
+// Split points of Eq. 2 (Section 3): t_1 = clamp(t_min + m_near h_1, t_min, t_max),
+// t_2 = clamp(t_max - m_far h_2, t_1, t_max).  One grid: h_1 = h_2 = its
+// largest voxel edge.  Cascade: the voxel at the start point o + t_min d and at
+// the end point o + t_max d (Section 3, "GI & Shadow Rays").
 struct Split {
     float t1, t2;
     bool near_bvh, field, far_bvh;
 };
 
-__device__ __forceinline__ Split make_split(int mode, float m_near, float m_far, float hsplit, float tmin, float tmax)
+__device__ __forceinline__ Split make_split(int mode, float m_near, float m_far, float h_near, float h_far,
+                                            float tmin, float tmax)
 {
     Split s;
-    s.t1 = fminf(fmaxf(__fmaf_rn(m_near, hsplit, tmin), tmin), tmax);
-    s.t2 = fminf(fmaxf(__fmaf_rn(-m_far, hsplit, tmax), s.t1), tmax);
+    s.t1 = fminf(fmaxf(__fmaf_rn(m_near, h_near, tmin), tmin), tmax);
+    s.t2 = fminf(fmaxf(__fmaf_rn(-m_far, h_far, tmax), s.t1), tmax);
     s.near_bvh = m_near > 0.f;
     if (mode == RT_MODE_SPLIT1) {
         s.field = (m_near == 0.f) || (s.t1 < tmax);
@@ -632,9 +715,23 @@ __device__ __forceinline__ Split make_split(int mode, float m_near, float m_far,
     return s;
 }
 
-__device__ __forceinline__ Split make_split(const TraceArgs& a, float tmin, float tmax)
+// voxel edges that set t_1 and t_2 for the query (o, d, t_min, t_max)
+__device__ __forceinline__ void split_voxels(const TraceArgs& a, float3 o, float3 d, float tmin, float tmax,
+                                             float& h_near, float& h_far)
 {
-    return make_split(a.mode, a.m_near, a.m_far, a.hsplit, tmin, tmax);
+    if (a.levels > 0) {
+        h_near = a.lv[casc_level(a, __fmaf_rn(tmin, d.x, o.x), __fmaf_rn(tmin, d.y, o.y), __fmaf_rn(tmin, d.z, o.z))].h;
+        h_far = a.lv[casc_level(a, __fmaf_rn(tmax, d.x, o.x), __fmaf_rn(tmax, d.y, o.y), __fmaf_rn(tmax, d.z, o.z))].h;
+    } else {
+        h_near = h_far = a.hsplit;
+    }
+}
+
+__device__ __forceinline__ Split make_split(const TraceArgs& a, float3 o, float3 d, float tmin, float tmax)
+{
+    float hn, hf;
+    split_voxels(a, o, d, tmin, tmax, hn, hf);
+    return make_split(a.mode, a.m_near, a.m_far, hn, hf, tmin, tmax);
 }
 
 // Eq. 1 is defined for real o, d and t_min <= t_max; anything else has no intersection

@@ -144,3 +144,69 @@ def test_bad_split_params_rejected(rtlib):
     assert rtlib.rt_trace_sdf(out, None, 0, ctypes.byref(good), None, None) == 0
     rtlib.rt_sdf_destroy.argtypes = [ctypes.c_void_p]
     rtlib.rt_sdf_destroy(out)
+
+
+def test_cascade_arguments_and_geometry_without_a_gpu(rtlib):
+    """rt_cascade_create checks its arguments on the host, places every level
+    where the checker's cascade places it, and a trace on a cascade without its
+    cell copy is refused before any device work."""
+    import numpy as np
+
+    import oracle as O
+    import paper_2305_07253_gb300 as rq
+    rtlib.rt_last_error.restype = ctypes.c_char_p
+    rtlib.rt_cascade_create.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
+    rtlib.rt_cascade_level.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    rtlib.rt_sdf_destroy.argtypes = [ctypes.c_void_p]
+    out = ctypes.c_void_p()
+    c3 = (ctypes.c_float * 3)(1.25, -0.5, 7.0)
+    good = ctypes.c_void_p(256)
+    assert rtlib.rt_cascade_create(good, 0, 0, 64, 0.1, c3, ctypes.byref(out)) == 1  # no levels
+    assert rtlib.rt_cascade_create(good, 0, 9, 64, 0.1, c3, ctypes.byref(out)) == 1  # > RT_MAX_LEVELS
+    assert rtlib.rt_cascade_create(good, 0, 5, 1, 0.1, c3, ctypes.byref(out)) == 1   # n < 2
+    assert rtlib.rt_cascade_create(good, 0, 5, 64, 0.0, c3, ctypes.byref(out)) == 1  # h0 = 0
+    assert rtlib.rt_cascade_create(ctypes.c_void_p(260), 0, 5, 64, 0.1, c3, ctypes.byref(out)) == 1
+    far = (ctypes.c_float * 3)(1e6, 0, 0)
+    assert rtlib.rt_cascade_create(good, 0, 5, 64, 0.1, far, ctypes.byref(out)) == 1
+    assert b"2^22" in rtlib.rt_last_error()
+    nanc = (ctypes.c_float * 3)(float("nan"), 0, 0)
+    assert rtlib.rt_cascade_create(good, 0, 5, 64, 0.1, nanc, ctypes.byref(out)) == 1
+
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        c = rng.uniform(-40, 40, size=3).astype(np.float32)
+        n = int(rng.integers(2, 130))
+        L = int(rng.integers(1, 9))
+        h0 = np.float32(rng.uniform(0.01, 0.5))
+        cc = (ctypes.c_float * 3)(*c.tolist())
+        assert rtlib.rt_cascade_create(good, 0, L, n, float(h0), cc, ctypes.byref(out)) == 0
+        ref = O.Cascade(c.astype(np.float64), float(h0), n, L, values=np.zeros((L, n, n, n)))
+        for k in range(L):
+            ilo = (ctypes.c_int32 * 3)()
+            h = ctypes.c_float()
+            assert rtlib.rt_cascade_level(out, k, ilo, ctypes.byref(h)) == 0
+            want_ilo, want_h = ref.level(k)
+            assert list(ilo) == want_ilo.tolist()
+            assert h.value == np.float32(want_h)
+        assert rtlib.rt_cascade_level(out, L, ilo, ctypes.byref(h)) == 1
+        rtlib.rt_sdf_destroy(out)
+
+    # a cascade is read through its cell copy: tracing before bake/prepare is refused
+    assert rtlib.rt_cascade_create(good, 0, 3, 16, 0.25, c3, ctypes.byref(out)) == 0
+    rtlib.rt_trace_sdf.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p]
+    prm = rq.split_params()
+    assert rtlib.rt_trace_sdf(out, ctypes.c_void_p(512), 4, ctypes.byref(prm), ctypes.c_void_p(1024), None) == 1
+    assert b"cell copy" in rtlib.rt_last_error()
+    # and rt_cascade_level on a single grid is refused
+    lo = (ctypes.c_float * 3)(0, 0, 0)
+    hi = (ctypes.c_float * 3)(1, 1, 1)
+    n4 = (ctypes.c_int32 * 3)(4, 4, 4)
+    single = ctypes.c_void_p()
+    rtlib.rt_sdf_create.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+    assert rtlib.rt_sdf_create(good, 0, lo, hi, n4, ctypes.byref(single)) == 0
+    assert rtlib.rt_cascade_level(single, 0, ilo, ctypes.byref(h)) == 1
+    rtlib.rt_sdf_destroy(single)
+    rtlib.rt_sdf_destroy(out)
