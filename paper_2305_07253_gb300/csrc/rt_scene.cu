@@ -1,7 +1,10 @@
 // Triangle acceleration structure: a linear BVH (LBVH).
 //
 //   1. per-triangle bounds and centroids, scene bounds by atomic min/max
-//   2. 63-bit Morton code of each centroid (21 bits per axis)
+//   2. 63-bit Morton code of each centroid (21 bits per axis); bit 63 marks a
+//      large triangle (box wider than a quarter of the scene), so that the
+//      root splits the large triangles (room walls, floors) from the rest and
+//      their wide boxes do not enlarge the nodes of the compact geometry
 //   3. sort (code, triangle) pairs (CUB radix sort, a library sort primitive)
 //   4. internal nodes by the split search of Karras, "Maximizing Parallelism
 //      in the Construction of BVHs, Octrees, and k-d Trees" (HPG 2012):
@@ -27,6 +30,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kMaxWalk = 256;  // bound on any leaf-to-root walk (the stack holds 64)
+constexpr float kLargeFrac = 0.25f;  // a triangle wider than this share of the scene is "large"
 
 __device__ __forceinline__ int f2ord(float f)
 {
@@ -70,7 +74,8 @@ __global__ void k_tri_bounds(const float* V, const int32_t* F, int64_t nt, float
         float lo[3] = {fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y), fminf(fminf(a.z, b.z), c.z)};
         float hi[3] = {fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y), fmaxf(fmaxf(a.z, b.z), c.z)};
         float cc[3] = {0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2])};
-        cen[t] = make_float4(cc[0], cc[1], cc[2], 0.f);
+        const float ext = fmaxf(fmaxf(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
+        cen[t] = make_float4(cc[0], cc[1], cc[2], ext);
         for (int k = 0; k < 3; ++k) {
             atomicMin(&s[k], f2ord(lo[k]));
             atomicMax(&s[3 + k], f2ord(hi[k]));
@@ -110,7 +115,10 @@ __global__ void k_morton(const float4* cen, int64_t nt, const int* bounds, uint6
         u = fminf(fmaxf(u, 0.f), 1.f);
         q[k] = (uint64_t)fminf(u * 2097152.0f, 2097151.0f);
     }
-    keys[t] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+    float scene_ext = 0.f;
+    for (int k = 0; k < 3; ++k) scene_ext = fmaxf(scene_ext, ord2f(bounds[3 + k]) - ord2f(bounds[k]));
+    const uint64_t large = c.w > kLargeFrac * scene_ext ? (1ull << 63) : 0ull;
+    keys[t] = large | (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
     vals[t] = (int32_t)t;
 }
 
@@ -364,10 +372,10 @@ rt_status rt_build_scene(const float* V, int64_t nv, const int32_t* F, int64_t n
 
     size_t tmp_bytes = 0;
     RT_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys.as<uint64_t>(), keys2.as<uint64_t>(),
-                                                vals.as<int32_t>(), vals2.as<int32_t>(), (int)nt, 0, 63, s));
+                                                vals.as<int32_t>(), vals2.as<int32_t>(), (int)nt, 0, 64, s));
     ALLOC(tmp, tmp_bytes);
     RT_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, keys.as<uint64_t>(), keys2.as<uint64_t>(),
-                                                vals.as<int32_t>(), vals2.as<int32_t>(), (int)nt, 0, 63, s));
+                                                vals.as<int32_t>(), vals2.as<int32_t>(), (int)nt, 0, 64, s));
     const uint64_t* skeys = keys2.as<uint64_t>();
     const int32_t* order = vals2.as<int32_t>();
 
