@@ -343,7 +343,8 @@ extern "C" rt_status rt_cascade_recenter(const rt_scene* sc, rt_sdf* sdf, const 
         if (st != RT_OK) return st;
     }
     int32_t count = 0;
-    for (int k = 0; k < sdf->levels; ++k) {
+    // coarsest first: a level baked whole is bounded by the next coarser one at its new place
+    for (int k = sdf->levels - 1; k >= 0; --k) {
         int32_t shift[3];
         bool same = true, far = false;
         for (int a = 0; a < 3; ++a) {

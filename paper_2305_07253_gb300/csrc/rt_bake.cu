@@ -114,6 +114,21 @@ struct BakeArgs {
     // `keep` (the level before the move) wherever that lies inside the level
     const void* keep;
     int32_t shift[3];
+    // Sub-lattice pass: when sub > 0 the threads enumerate only the samples
+    // whose indices are multiples of `sub` (a first pass that seeds the bounds).
+    int32_t sub;
+    // Bound source: a lattice of samples whose exact values are already known.
+    // A sample at absolute lattice index a (a = ilo + i on a cascade level,
+    // a = i otherwise) takes the source sample j = clamp(round(a / bratio) -
+    // bilo, 0, bjmax), stored at element j * bstride of bsrc (per axis), and
+    // searches only within |phi(source)| + |p - source|, since the distance
+    // function is 1-Lipschitz.  The nearest triangle found is the same as
+    // without the bound.  bsrc null: no bound.
+    const void* bsrc;
+    int32_t bratio, bstride;
+    int32_t bilo[3], bjmax[3];
+    int32_t bself;  // 1: the source is this grid's own sub-lattice: relative indices
+                    // (a = i), and its samples are skipped (baked by the first pass)
 };
 
 __device__ __forceinline__ float3 sample_pos(const BakeArgs& b, int64_t i)
@@ -183,12 +198,49 @@ __device__ __forceinline__ float box_d2(float lx, float hx, float ly, float hy, 
     return dx * dx + dy * dy + dz * dz;
 }
 
-__global__ void __launch_bounds__(kBakeBlock) k_bake_bvh(const BakeArgs b)
+__device__ __forceinline__ float load_value(const void* g, int32_t f16, int64_t i)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.count || take_kept(b, i)) return;
-    const float3 p = sample_pos(b, i);
-    Nearest nb = {__int_as_float(0x7f800000), -1, 0x7fffffff};
+    return f16 ? __half2float(reinterpret_cast<const __half*>(g)[i]) : reinterpret_cast<const float*>(g)[i];
+}
+
+__device__ __forceinline__ int64_t floordiv(int64_t x, int64_t y)  // y > 0
+{
+    return x >= 0 ? x / y : -((-x + y - 1) / y);
+}
+
+// upper bound on the distance at sample (ix, iy, iz) from the bound source
+__device__ __forceinline__ float distance_bound(const BakeArgs& b, int64_t ix, int64_t iy, int64_t iz)
+{
+    if (!b.bsrc) return __int_as_float(0x7f800000);
+    const int64_t ii[3] = {ix, iy, iz};
+    int64_t el = 0, stride = 1;
+    float d2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t abs_i = (b.lattice && !b.bself ? b.ilo[a] : 0) + ii[a];
+        int64_t j = floordiv(2 * abs_i + b.bratio, 2 * (int64_t)b.bratio) - b.bilo[a];  // round(abs_i / bratio)
+        j = j < 0 ? 0 : (j > b.bjmax[a] ? b.bjmax[a] : j);
+        const float gap = (float)(abs_i - (j + b.bilo[a]) * b.bratio) * b.h[a];
+        d2 += gap * gap;
+        el += j * b.bstride * stride;
+        stride *= b.n[a];
+    }
+    const float phi = fabsf(load_value(b.bsrc, b.f16, el));
+    // generous margin for the rounding of the stored value (float16 included)
+    return (phi + sqrtf(d2)) * 1.002f + 1e-6f;
+}
+
+__device__ __forceinline__ bool on_sublattice(const BakeArgs& b, int64_t ix, int64_t iy, int64_t iz)
+{
+    return ix % b.bstride == 0 && iy % b.bstride == 0 && iz % b.bstride == 0 && ix / b.bstride <= b.bjmax[0] &&
+           iy / b.bstride <= b.bjmax[1] && iz / b.bstride <= b.bjmax[2];
+}
+
+// nearest triangle to p among those closer than sqrt(d2_start) (BVH-pruned);
+// k = -1 when there is none
+__device__ __forceinline__ Nearest nearest_bvh(const BakeArgs& b, float3 p, float d2_start)
+{
+    Nearest nb = {d2_start, -1, 0x7fffffff};
     int stack[RT_STACK_DEPTH];
     float sd[RT_STACK_DEPTH];
     int sp = 0;
@@ -221,6 +273,26 @@ __global__ void __launch_bounds__(kBakeBlock) k_bake_bvh(const BakeArgs b)
         }
         if (!more) break;
     }
+    return nb;
+}
+
+__global__ void __launch_bounds__(kBakeBlock) k_bake_bvh(const BakeArgs b)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = t;
+    if (b.sub > 0) {  // enumerate the sub-lattice only
+        const int64_t mx = (b.n[0] - 1) / b.sub + 1, my = (b.n[1] - 1) / b.sub + 1, mz = (b.n[2] - 1) / b.sub + 1;
+        if (t >= mx * my * mz) return;
+        const int64_t jx = t % mx, jy = (t / mx) % my, jz = t / (mx * my);
+        i = jx * b.sub + (int64_t)b.n[0] * (jy * b.sub + (int64_t)b.n[1] * (jz * b.sub));
+    }
+    if (i >= b.count || take_kept(b, i)) return;
+    const int64_t ix = i % b.n[0], iy = (i / b.n[0]) % b.n[1], iz = i / ((int64_t)b.n[0] * b.n[1]);
+    if (b.bself && on_sublattice(b, ix, iy, iz)) return;
+    const float3 p = sample_pos(b, i);
+    const float bound = distance_bound(b, ix, iy, iz);
+    Nearest nb = nearest_bvh(b, p, bound * bound);
+    if (nb.k < 0 && bound < __int_as_float(0x7f800000)) nb = nearest_bvh(b, p, __int_as_float(0x7f800000));
     store(b, i, signed_distance(p, nb, b.tris, b.pn));
 }
 
@@ -335,15 +407,44 @@ rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s)
     return RT_OK;
 }
 
-static rt_status launch_bake_args(BakeArgs& b, int32_t method, cudaStream_t s)
+constexpr int kSubStride = 4;  // first-pass sub-lattice of a bounded bake
+
+static rt_status launch_one(const BakeArgs& b, int32_t method, cudaStream_t s)
 {
-    if (method == RT_BAKE_AUTO) method = (double)b.count * (double)b.n_tris <= 17179869184.0 ? RT_BAKE_BRUTE : RT_BAKE_BVH;
-    const int64_t blocks = (b.count + kBakeBlock - 1) / kBakeBlock;
+    int64_t threads = b.count;
+    if (b.sub > 0)
+        threads = (int64_t)((b.n[0] - 1) / b.sub + 1) * ((b.n[1] - 1) / b.sub + 1) * ((b.n[2] - 1) / b.sub + 1);
+    const int64_t blocks = (threads + kBakeBlock - 1) / kBakeBlock;
     if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "grid too large for one launch");
     if (method == RT_BAKE_BRUTE) k_bake_brute<<<(unsigned)blocks, kBakeBlock, 0, s>>>(b);
     else k_bake_bvh<<<(unsigned)blocks, kBakeBlock, 0, s>>>(b);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
+}
+
+// BVH bake in two passes over the same grid: the stride-4 sub-lattice first,
+// then every other sample bounded by its nearest sub-lattice sample
+static rt_status launch_two_pass(BakeArgs b, cudaStream_t s)
+{
+    b.sub = kSubStride;
+    b.bsrc = nullptr;
+    rt_status st = launch_one(b, RT_BAKE_BVH, s);
+    if (st != RT_OK) return st;
+    b.sub = 0;
+    b.bsrc = b.grid;
+    b.bratio = b.bstride = kSubStride;
+    for (int a = 0; a < 3; ++a) {
+        b.bilo[a] = 0;
+        b.bjmax[a] = (b.n[a] - 1) / kSubStride;
+    }
+    b.bself = 1;
+    return launch_one(b, RT_BAKE_BVH, s);
+}
+
+static int32_t pick_method(const BakeArgs& b, int32_t method)
+{
+    if (method == RT_BAKE_AUTO) method = (double)b.count * (double)b.n_tris <= 17179869184.0 ? RT_BAKE_BRUTE : RT_BAKE_BVH;
+    return method;
 }
 
 rt_status rt_launch_cascade_bake(const rt_scene* sc, const rt_sdf* sdf, int k, int32_t method, const void* keep,
@@ -368,13 +469,31 @@ rt_status rt_launch_cascade_bake(const rt_scene* sc, const rt_sdf* sdf, int k, i
         b.shift[a] = shift ? shift[a] : 0;
     }
     b.keep = keep;
-    return launch_bake_args(b, method, s);
+    method = pick_method(b, method);
+    if (method == RT_BAKE_BRUTE) return launch_one(b, method, s);
+    b.bratio = 1;
+    b.bstride = 1;
+    for (int a = 0; a < 3; ++a) b.bjmax[a] = (int32_t)n - 1;
+    if (keep) {
+        // rolling update: new samples are bounded by the nearest kept sample
+        b.bsrc = keep;
+        for (int a = 0; a < 3; ++a) b.bilo[a] = sdf->ilo[k][a] - b.shift[a];
+        return launch_one(b, method, s);
+    }
+    if (k + 1 < sdf->levels) {
+        // bounded by the next coarser level (baked or moved before this one)
+        b.bsrc = static_cast<const char*>(sdf->grid) + (k + 1) * n * n * n * esz;
+        b.bratio = 2;
+        for (int a = 0; a < 3; ++a) b.bilo[a] = sdf->ilo[k + 1][a];
+        return launch_one(b, method, s);
+    }
+    return launch_two_pass(b, s);
 }
 
 rt_status rt_launch_bake(const rt_scene* sc, const rt_sdf* sdf, int32_t method, cudaStream_t s)
 {
     if (sdf->levels > 0) {
-        for (int k = 0; k < sdf->levels; ++k) {
+        for (int k = sdf->levels - 1; k >= 0; --k) {  // coarsest first: each level bounds the next finer one
             rt_status st = rt_launch_cascade_bake(sc, sdf, k, method, nullptr, nullptr, s);
             if (st != RT_OK) return st;
         }
@@ -395,5 +514,7 @@ rt_status rt_launch_bake(const rt_scene* sc, const rt_sdf* sdf, int32_t method, 
         b.n[k] = sdf->n[k];
         b.count *= sdf->n[k];
     }
-    return launch_bake_args(b, method, s);
+    method = pick_method(b, method);
+    if (method == RT_BAKE_BRUTE) return launch_one(b, method, s);
+    return launch_two_pass(b, s);
 }
