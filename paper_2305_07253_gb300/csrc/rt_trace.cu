@@ -236,8 +236,11 @@ __global__ void k_stage_bvh(const TraceArgs a, const StageArgs st)
 
 // 40 registers: 12 resident blocks of 128 threads per SM; more march chains in
 // flight hide more of the cell-load latency (measured: 0.596 vs 0.616 ms field-only)
+#ifndef RT_FIELD_REGS
+#define RT_FIELD_REGS 40
+#endif
 template <bool COUNT, int L>
-__global__ void __maxnreg__(40) k_stage_field(const TraceArgs a, const StageArgs st)
+__global__ void __maxnreg__(RT_FIELD_REGS) k_stage_field(const TraceArgs a, const StageArgs st)
 {
     const unsigned n_in = st.first ? (unsigned)a.n : *st.in_count;
     Counts cnt = {0, 0, 0, 0};
