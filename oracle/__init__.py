@@ -15,7 +15,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "march.inc", "oracle.h")]
+_SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "march.inc", "dfgen.inc", "oracle.h")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -81,6 +81,12 @@ def lib():
             L.or_cascade_level_grid.restype = i32
             L.or_cascade_level_of.argtypes = [P, P, i64, i32, P]
             L.or_trace_combined_cascade.argtypes = [P, P, P, i64, P, i32, i32, P, P]
+            L.or_df_sites.argtypes = [P, P, P, P, i32, i32, P]
+            L.or_df_field.argtypes = [P, P, P, P]
+            L.or_tri_box_overlap.argtypes = [P, P, P, P, P]
+            L.or_tri_box_overlap.restype = ctypes.c_int
+            L.or_tri_dist2_f.argtypes = [P, P, P, P]
+            L.or_tri_dist2_f.restype = ctypes.c_float
             _lib = L
     return _lib
 
@@ -275,6 +281,72 @@ class Cascade:
         out = np.zeros(P.shape[0], dtype=np.int32)
         lib().or_cascade_level_of(self.h, _ptr(P), P.shape[0], int(precision), _ptr(out))
         return out
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def tri_box_overlap(c, hs, a, b, cc) -> bool:
+    """Single precision separating-axis test of triangle (a, b, cc) against the
+    box of centre c and half sizes hs (touching counts)."""
+    args = [_f32(x) for x in (c, hs, a, b, cc)]
+    return bool(lib().or_tri_box_overlap(*[_ptr(x) for x in args]))
+
+
+def tri_dist2_f(p, a, b, c) -> float:
+    args = [_f32(x) for x in (p, a, b, c)]
+    return float(lib().or_tri_dist2_f(*[_ptr(x) for x in args]))
+
+
+def _level_grid(grid, k=None):
+    """(or_grid pointer, number of samples, n) of a Grid, or of level k of a Cascade."""
+    if isinstance(grid, Cascade):
+        g = ctypes.c_void_p()
+        ilo = np.zeros(3, dtype=np.int64)
+        h = ctypes.c_double(0.0)
+        if not lib().or_cascade_level_grid(grid.h, int(k), _ptr(ilo), ctypes.byref(h), ctypes.byref(g)):
+            raise IndexError(k)
+        return g, grid.n ** 3, (grid.n, grid.n, grid.n)
+    n = tuple(int(v) for v in grid.n)
+    return ctypes.c_void_p(grid.h), int(np.prod(n)), n
+
+
+def df_sites(bvh: BVH, grid, stage: int = 3, nthreads: int | None = None):
+    """Sites (triangle index per sample, -1 for none) of the paper's field build
+    after `stage` (1 voxelisation, 2 jump flooding, 3 sweeps).  One grid: an
+    array of n0*n1*n2; a cascade: (levels, n^3), built coarsest level first, each
+    level seeded also from the next coarser one."""
+    if isinstance(grid, Cascade):
+        out = np.zeros((grid.levels, grid.n ** 3), dtype=np.int32)
+        for k in reversed(range(grid.levels)):
+            g, _, _ = _level_grid(grid, k)
+            coarse, gc = (None, None)
+            if k + 1 < grid.levels:
+                coarse = _ptr(out[k + 1])
+                gc, _, _ = _level_grid(grid, k + 1)
+            lib().or_df_sites(bvh.h, g, coarse, gc, int(stage), nthreads or default_threads(), _ptr(out[k]))
+        return out
+    g, count, _ = _level_grid(grid)
+    out = np.zeros(count, dtype=np.int32)
+    lib().or_df_sites(bvh.h, g, None, None, int(stage), nthreads or default_threads(), _ptr(out))
+    return out
+
+
+def df_field(bvh: BVH, grid, sites) -> np.ndarray:
+    """Signed distance from each sample to its site triangle (fp64)."""
+    if isinstance(grid, Cascade):
+        out = np.zeros((grid.levels, grid.n ** 3))
+        for k in range(grid.levels):
+            g, _, _ = _level_grid(grid, k)
+            s = np.ascontiguousarray(sites[k], dtype=np.int32)
+            lib().or_df_field(bvh.h, g, _ptr(s), _ptr(out[k]))
+        return out
+    g, count, _ = _level_grid(grid)
+    s = np.ascontiguousarray(sites, dtype=np.int32).reshape(-1)
+    out = np.zeros(count)
+    lib().or_df_field(bvh.h, g, _ptr(s), _ptr(out))
+    return out
 
 
 def make_params(mode=1, any_hit=False, m_near=2.0, m_far=2.0, max_steps=256, hit_eps_vox=0.01,

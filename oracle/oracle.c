@@ -1157,3 +1157,8 @@ void or_sdf_root_adjoint(const or_grid* g, const float* rays, int64_t nr, const 
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* the paper's field build: voxelisation, jump flooding, sweeping             */
+/* ------------------------------------------------------------------------ */
+#include "dfgen.inc"

@@ -112,6 +112,20 @@ void or_trace_combined_cascade(const or_bvh* b, const or_cascade* c, const float
                                const or_params* p, int32_t precision, int32_t nthreads, or_hit* hits,
                                double* t12);
 
+/* The paper's field build (Section 3, "Distance Field Generation"):
+ * conservative voxelisation, jump flooding, axis sweeps (dfgen.inc states the
+ * steps).  or_df_sites writes the site (triangle index, -1 for none) of every
+ * sample of g after step `stage` (1 voxelisation, 2 jump flooding, 3 sweeps);
+ * coarse / gc: the sites and grid of the next coarser cascade level (NULL
+ * otherwise).  or_df_field: signed distance (double) from each sample to its
+ * site triangle.  or_tri_box_overlap and or_tri_dist2_f expose the single
+ * precision triangle/box test and point/triangle squared distance. */
+void or_df_sites(const or_bvh* b, const or_grid* g, const int32_t* coarse, const or_grid* gc, int32_t stage,
+                 int32_t nthreads, int32_t* sites);
+void or_df_field(const or_bvh* b, const or_grid* g, const int32_t* sites, double* phi);
+int or_tri_box_overlap(const float c[3], const float hs[3], const float a[3], const float b[3], const float cc[3]);
+float or_tri_dist2_f(const float p[3], const float a[3], const float b[3], const float c[3]);
+
 /* Trilinear value and gradient of the grid interpolant at points (fp64). */
 void or_grid_sample(const or_grid* g, const double* P, int64_t np, double* phi, double* grad);
 
