@@ -113,7 +113,7 @@ typedef struct {
 
 enum { RT_MODE_BVH = 0, RT_MODE_SPLIT1 = 1, RT_MODE_SPLIT2 = 2, RT_MODE_SDF = 3 };
 enum { RT_GRID_F32 = 0, RT_GRID_F16 = 1 };
-enum { RT_BAKE_AUTO = 0, RT_BAKE_BRUTE = 1, RT_BAKE_BVH = 2 };
+enum { RT_BAKE_AUTO = 0, RT_BAKE_BRUTE = 1, RT_BAKE_BVH = 2, RT_BAKE_JFA = 3 };
 
 typedef struct rt_scene rt_scene;
 typedef struct rt_sdf rt_sdf;
@@ -183,8 +183,35 @@ rt_status rt_sdf_prepare(rt_sdf* sdf, void* stream);
  * grid pointer given to rt_sdf_create.  On a cascade (rt_cascade_create) every
  * level is baked at its lattice points (ilo_k + i) * h_k, each coordinate
  * rounded once from that product, so that a level moved by rt_cascade_recenter
- * holds the same values as one baked at its new place. */
+ * holds the same values as one baked at its new place.
+ * RT_BAKE_JFA is the paper's build instead (Section 3, "Distance Field
+ * Generation"): conservative voxelisation, jump flooding and sweeping give
+ * every sample a site triangle (see rt_sdf_sites), and the value is the signed
+ * distance to that triangle.  It equals the exact bake where the site is the
+ * nearest triangle and is larger elsewhere; triangles outside the grid's box
+ * (the coarsest level's on a cascade) are not seen.  The handle keeps the
+ * sites (4 bytes per sample) for rt_cascade_recenter, which then rebuilds each
+ * moved level the same way. */
 rt_status rt_sdf_bake(const rt_scene* scene, rt_sdf* sdf, int32_t method, void* stream);
+
+/* Site map of the paper's field build: for every sample of `sdf` (level
+ * after level on a cascade) the input index of its site triangle (-1: none)
+ * after step `stage` of the build:
+ *   1  conservative voxelisation: the sample's voxel box (side h (1 + 2^-8),
+ *      centred on the sample) meets the triangle (separating-axis test,
+ *      Akenine-Moller 2001); on a cascade level below the coarsest, the site of
+ *      the nearest sample of the next coarser level is a candidate too
+ *   2  jump flooding (Rong & Tan 2006): steps 2^(ceil(log2 n)-1) ... 1, each
+ *      sample taking the best site of itself and its 26 neighbours at offsets
+ *      {-k, 0, k}^3
+ *   3  sweeps along every grid line, +x, -x, +y, -y, +z, -z (the fast-sweeping
+ *      step), each sample taking the better of its site and the previous
+ *      sample's
+ * "Best" is the smallest (squared distance to the triangle, triangle index),
+ * evaluated in single precision with every operation rounded once.  Cascade
+ * levels are built coarsest first.  d_sites: caller memory, one int32 per
+ * sample.  The grid values are not touched.  Enqueued on `stream`. */
+rt_status rt_sdf_sites(const rt_scene* scene, const rt_sdf* sdf, int32_t stage, int32_t* d_sites, void* stream);
 
 #define RT_MAX_LEVELS 8
 
@@ -222,8 +249,10 @@ rt_status rt_cascade_create(const void* d_grid, int32_t dtype, int32_t levels, i
  * samples that the old and new lattices share (moved within its memory) and
  * fills only the new slices with the exact distance of rt_sdf_bake (BVH
  * method); a level that moved by n or more samples on an axis is baked
- * whole.  The cell-corner copy of each changed level is rebuilt.  The values
- * equal those of a full rt_sdf_bake at the new centre.  Enqueued on
+ * whole.  After an RT_BAKE_JFA bake, each moved level is rebuilt whole by the
+ * paper's build instead, seeded from the next coarser level's sites.  The
+ * cell-corner copy of each changed level is rebuilt.  The values equal those
+ * of a full rt_sdf_bake at the new centre (with the same method).  Enqueued on
  * `stream`; uses a device scratch of one level owned by the handle (allocated
  * on the first call).  *moved (nullable) receives the number of levels that
  * changed.  Errors: RT_ERR_INVALID_ARG (not a cascade, null or non-finite

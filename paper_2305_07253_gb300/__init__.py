@@ -29,7 +29,7 @@ MODE_BVH, MODE_SPLIT1, MODE_SPLIT2, MODE_SDF = range(4)
 TRACER_MISS, TRACER_BVH, TRACER_SDF = range(3)
 FLAG_STACK_OVERFLOW, FLAG_STEP_LIMIT, FLAG_ITER_LIMIT = 1, 2, 4
 GRID_F32, GRID_F16 = 0, 1
-BAKE_AUTO, BAKE_BRUTE, BAKE_BVH = 0, 1, 2
+BAKE_AUTO, BAKE_BRUTE, BAKE_BVH, BAKE_JFA = 0, 1, 2, 3
 
 KERNEL_WAVEFRONT, KERNEL_SIMPLE = 0, 1
 LAYOUT_CELLS, LAYOUT_PLAIN, LAYOUT_PAIRS = 0, 1, 2
@@ -38,7 +38,8 @@ EXPORTS = ("rt_scene_build", "rt_scene_info_get", "rt_scene_destroy", "rt_sdf_cr
            "rt_sdf_prepare", "rt_sdf_bake", "rt_trace_bvh", "rt_trace_sdf", "rt_trace_combined",
            "rt_trace_combined_counted", "rt_trace_combined_timed", "rt_trace_combined_noalloc",
            "rt_trace_combined_backward", "rt_trace_batches", "rt_set_tuning", "rt_get_tuning",
-           "rt_cascade_create", "rt_cascade_recenter", "rt_cascade_level", "rt_last_error", "rt_version")
+           "rt_cascade_create", "rt_cascade_recenter", "rt_cascade_level", "rt_sdf_sites", "rt_last_error",
+           "rt_version")
 
 
 class RtError(RuntimeError):
@@ -113,6 +114,7 @@ def lib() -> ctypes.CDLL:
             "rt_cascade_create": [P, i32, i32, i32, ctypes.c_float, P, P],
             "rt_cascade_recenter": [P, P, P, P, P],
             "rt_cascade_level": [P, i32, P, P],
+            "rt_sdf_sites": [P, P, i32, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -259,6 +261,17 @@ def rt_cascade_recenter(scene: Scene, sdf: Sdf, center, stream=None) -> int:
     lo, hi = rt_cascade_box(sdf, sdf.levels - 1)
     sdf.lo, sdf.hi = tuple(lo), tuple(hi)
     return moved.value
+
+
+def rt_sdf_sites(scene: Scene, sdf: Sdf, stage: int = 3, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Site triangle (input index, -1 none) of every sample after step `stage` of
+    the paper's field build (1 voxelisation, 2 jump flooding, 3 sweeps): int32,
+    shaped like the grid tensor."""
+    if out is None:
+        out = torch.empty(sdf.grid.shape, dtype=torch.int32, device=sdf.grid.device)
+    assert out.dtype == torch.int32 and out.numel() == sdf.grid.numel()
+    _check(lib().rt_sdf_sites(scene.handle, sdf.handle, int(stage), _dptr(out), _stream(stream)))
+    return out
 
 
 def rt_sdf_bake(scene: Scene, sdf: Sdf, method: int = BAKE_AUTO, stream=None) -> None:

@@ -211,6 +211,7 @@ extern "C" rt_status rt_scene_destroy(rt_scene* sc)
     cudaFree(sc->nodes);
     cudaFree(sc->tris);
     cudaFree(sc->pn);
+    cudaFree(sc->slot);
     cudaFree(sc->wnodes);
     cudaFree(sc->wtris);
     delete sc;
@@ -258,6 +259,7 @@ extern "C" rt_status rt_sdf_destroy(rt_sdf* sdf)
     if (sdf->cells) cudaFree(sdf->cells);
     if (sdf->pairs) cudaFree(sdf->pairs);
     if (sdf->scratch) cudaFree(sdf->scratch);
+    if (sdf->sites) cudaFree(sdf->sites);
     delete sdf;
     return RT_OK;
 }
@@ -354,7 +356,7 @@ extern "C" rt_status rt_cascade_recenter(const rt_scene* sc, rt_sdf* sdf, const 
         }
         if (same) continue;
         const void* keep = nullptr;
-        if (!far) {
+        if (!far && sdf->bake_method != RT_BAKE_JFA) {
             if (!sdf->scratch) {
                 RT_CUDA_TRY(cudaMalloc(&sdf->scratch, (size_t)level_bytes));
                 sdf->scratch_bytes = level_bytes;
@@ -364,7 +366,10 @@ extern "C" rt_status rt_cascade_recenter(const rt_scene* sc, rt_sdf* sdf, const 
             keep = sdf->scratch;
         }
         for (int a = 0; a < 3; ++a) sdf->ilo[k][a] = ilo[k][a];
-        st = rt_launch_cascade_bake(sc, sdf, k, RT_BAKE_BVH, keep, shift, s);
+        if (sdf->bake_method == RT_BAKE_JFA && sdf->sites)
+            st = rt_launch_df_level(sc, sdf, k, sdf->sites, s);  // the paper's build, level rebuilt whole
+        else
+            st = rt_launch_cascade_bake(sc, sdf, k, RT_BAKE_BVH, keep, shift, s);
         if (st != RT_OK) return st;
         st = rt_launch_cascade_cells(sdf, k, s);
         if (st != RT_OK) return st;
@@ -388,15 +393,46 @@ extern "C" rt_status rt_sdf_prepare(rt_sdf* sdf, void* stream)
     return rt_launch_prepare(sdf, (cudaStream_t)stream);
 }
 
+static int64_t sample_count(const rt_sdf* sdf)
+{
+    return (int64_t)(sdf->levels > 0 ? sdf->levels : 1) * sdf->n[0] * sdf->n[1] * sdf->n[2];
+}
+
 extern "C" rt_status rt_sdf_bake(const rt_scene* sc, rt_sdf* sdf, int32_t method, void* stream)
 {
     if (!sc || !sdf) return rt_fail(RT_ERR_INVALID_ARG, "null scene or grid");
-    if (method < 0 || method > 2) return rt_fail(RT_ERR_INVALID_ARG, "bake method %d", method);
+    if (method < 0 || method > 3) return rt_fail(RT_ERR_INVALID_ARG, "bake method %d", method);
     rt_status st = device_matches(sc->device);
     if (st != RT_OK) return st;
-    st = rt_launch_bake(sc, sdf, method, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (method == RT_BAKE_JFA) {
+        const int64_t count = sample_count(sdf);
+        if (!sdf->sites || sdf->sites_count != count) {
+            if (sdf->sites) cudaFree(sdf->sites);
+            sdf->sites = nullptr;
+            sdf->sites_count = 0;
+            RT_CUDA_TRY(cudaMalloc(&sdf->sites, (size_t)count * sizeof(int32_t)));
+            sdf->sites_count = count;
+        }
+        st = rt_launch_df_sites(sc, sdf, 3, sdf->sites, s);
+        if (st == RT_OK) st = rt_launch_df_field(sc, sdf, sdf->sites, s);
+    } else {
+        st = rt_launch_bake(sc, sdf, method, s);
+    }
     if (st != RT_OK) return st;
-    return rt_launch_prepare(sdf, (cudaStream_t)stream);
+    sdf->bake_method = method;
+    return rt_launch_prepare(sdf, s);
+}
+
+extern "C" rt_status rt_sdf_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t stage, int32_t* d_sites,
+                                  void* stream)
+{
+    if (!sc || !sdf || !d_sites) return rt_fail(RT_ERR_INVALID_ARG, "null argument");
+    if (stage < 1 || stage > 3) return rt_fail(RT_ERR_INVALID_ARG, "stage %d not in 1..3", stage);
+    if (((uintptr_t)d_sites & 3u) != 0) return rt_fail(RT_ERR_INVALID_ARG, "site buffer not 4-byte aligned");
+    rt_status st = device_matches(sc->device);
+    if (st != RT_OK) return st;
+    return rt_launch_df_sites(sc, sdf, stage, d_sites, (cudaStream_t)stream);
 }
 
 static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,

@@ -1,0 +1,531 @@
+// The paper's distance-field build (Section 3, "Distance Field Generation"):
+// the triangles are voxelised, the voxelisation is turned into a distance
+// field by jump flooding, and fast sweeping refines it.  The paper names the
+// three steps only; the steps taken here:
+//
+//   1. Conservative voxelisation.  Sample s owns the voxel box of side
+//      h (1 + 2^-8) centred on it.  Every triangle is tested (separating axes,
+//      Akenine-Moller, JGT 2001) against the voxels its bounds can reach, one
+//      thread per (triangle, voxel) pair after a prefix sum over the
+//      triangles; an overlapping triangle is a candidate site of the sample.
+//      The best candidate wins through a 64-bit atomicMin on (squared
+//      distance bits, triangle index).  On a cascade level below the
+//      coarsest, the site of the nearest sample of the next coarser level is a
+//      candidate too.
+//   2. Jump flooding (Rong & Tan, I3D 2006): steps k = 2^(ceil(log2 n)-1) ...
+//      1; each sample takes the best of the sites of itself and its 26
+//      neighbours at offsets in {-k, 0, k}^3, from the previous step.
+//   3. Fast sweeping as axis sweeps, +x, -x, +y, -y, +z, -z: one thread per
+//      grid line carries the best site along the line.
+//   4. The field value is the signed distance to the site triangle (the
+//      exact bake's closest point and pseudonormal sign).
+//
+// "Best" is the smallest (squared distance from the sample to the site's
+// triangle, triangle index).  Every operation of steps 1-3 is rounded once
+// (explicit intrinsics), so the sites are those of the CPU checker's single
+// precision build, bit for bit.
+#include <cub/device/device_scan.cuh>
+
+#include "rt_bake_dev.cuh"
+#include "rt_trace_dev.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+// ---------------------------------------------------------------------------
+// single precision geometry, each operation rounded once
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dot3r(const float* a, const float* b)
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(a[0], b[0]), __fmul_rn(a[1], b[1])), __fmul_rn(a[2], b[2]));
+}
+
+// squared distance from p to triangle abc (Ericson's Voronoi regions)
+__device__ float tri_d2_rn(const float* p, const float* a, const float* b, const float* c)
+{
+    float ab[3], ac[3], ap[3], q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        ab[k] = __fsub_rn(b[k], a[k]);
+        ac[k] = __fsub_rn(c[k], a[k]);
+        ap[k] = __fsub_rn(p[k], a[k]);
+    }
+    const float d1 = dot3r(ab, ap), d2 = dot3r(ac, ap);
+    if (d1 <= 0.f && d2 <= 0.f) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) q[k] = a[k];
+    } else {
+        float bp[3], cp[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            bp[k] = __fsub_rn(p[k], b[k]);
+            cp[k] = __fsub_rn(p[k], c[k]);
+        }
+        const float d3 = dot3r(ab, bp), d4 = dot3r(ac, bp);
+        const float vc = __fsub_rn(__fmul_rn(d1, d4), __fmul_rn(d3, d2));
+        const float d5 = dot3r(ab, cp), d6 = dot3r(ac, cp);
+        const float vb = __fsub_rn(__fmul_rn(d5, d2), __fmul_rn(d1, d6));
+        const float va = __fsub_rn(__fmul_rn(d3, d6), __fmul_rn(d5, d4));
+        if (d3 >= 0.f && d4 <= d3) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) q[k] = b[k];
+        } else if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+            const float s = __fdiv_rn(d1, __fsub_rn(d1, d3));
+#pragma unroll
+            for (int k = 0; k < 3; ++k) q[k] = __fadd_rn(a[k], __fmul_rn(s, ab[k]));
+        } else if (d6 >= 0.f && d5 <= d6) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) q[k] = c[k];
+        } else if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+            const float s = __fdiv_rn(d2, __fsub_rn(d2, d6));
+#pragma unroll
+            for (int k = 0; k < 3; ++k) q[k] = __fadd_rn(a[k], __fmul_rn(s, ac[k]));
+        } else if (va <= 0.f && __fsub_rn(d4, d3) >= 0.f && __fsub_rn(d5, d6) >= 0.f) {
+            const float s = __fdiv_rn(__fsub_rn(d4, d3), __fadd_rn(__fsub_rn(d4, d3), __fsub_rn(d5, d6)));
+#pragma unroll
+            for (int k = 0; k < 3; ++k) q[k] = __fadd_rn(b[k], __fmul_rn(s, __fsub_rn(c[k], b[k])));
+        } else {
+            const float den = __fdiv_rn(1.f, __fadd_rn(__fadd_rn(va, vb), vc));
+            const float v = __fmul_rn(vb, den), w = __fmul_rn(vc, den);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) q[k] = __fadd_rn(__fadd_rn(a[k], __fmul_rn(ab[k], v)), __fmul_rn(ac[k], w));
+        }
+    }
+    const float pq[3] = {__fsub_rn(p[0], q[0]), __fsub_rn(p[1], q[1]), __fsub_rn(p[2], q[2])};
+    return dot3r(pq, pq);
+}
+
+__device__ __forceinline__ bool axis_separates(const float* ax, const float* v0, const float* v1, const float* v2,
+                                               const float* hs)
+{
+    const float p0 = dot3r(ax, v0), p1 = dot3r(ax, v1), p2 = dot3r(ax, v2);
+    const float lo = fminf(fminf(p0, p1), p2), hi = fmaxf(fmaxf(p0, p1), p2);
+    const float r = __fadd_rn(__fadd_rn(__fmul_rn(hs[0], fabsf(ax[0])), __fmul_rn(hs[1], fabsf(ax[1]))),
+                              __fmul_rn(hs[2], fabsf(ax[2])));
+    return lo > r || hi < -r;
+}
+
+// triangle / box overlap by separating axes (touching counts)
+__device__ bool tri_box(const float* c, const float* hs, const float* A, const float* B, const float* C)
+{
+    float v0[3], v1[3], v2[3], e[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v0[k] = __fsub_rn(A[k], c[k]);
+        v1[k] = __fsub_rn(B[k], c[k]);
+        v2[k] = __fsub_rn(C[k], c[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e[0][k] = __fsub_rn(v1[k], v0[k]);
+        e[1][k] = __fsub_rn(v2[k], v1[k]);
+        e[2][k] = __fsub_rn(v0[k], v2[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float ax[3] = {0.f, 0.f, 0.f};
+        ax[k] = 1.f;
+        if (axis_separates(ax, v0, v1, v2, hs)) return false;
+    }
+    const float n[3] = {__fsub_rn(__fmul_rn(e[0][1], e[1][2]), __fmul_rn(e[0][2], e[1][1])),
+                        __fsub_rn(__fmul_rn(e[0][2], e[1][0]), __fmul_rn(e[0][0], e[1][2])),
+                        __fsub_rn(__fmul_rn(e[0][0], e[1][1]), __fmul_rn(e[0][1], e[1][0]))};
+    if (axis_separates(n, v0, v1, v2, hs)) return false;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float ax0[3] = {0.f, -e[j][2], e[j][1]};
+        const float ax1[3] = {e[j][2], 0.f, -e[j][0]};
+        const float ax2[3] = {-e[j][1], e[j][0], 0.f};
+        if (axis_separates(ax0, v0, v1, v2, hs) || axis_separates(ax1, v0, v1, v2, hs) ||
+            axis_separates(ax2, v0, v1, v2, hs))
+            return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// grid geometry (one grid, or one cascade level)
+// ---------------------------------------------------------------------------
+struct DfGrid {
+    int32_t n[3];
+    int32_t lattice;
+    int32_t ilo[3];
+    float lo[3], h[3], hs[3];
+    double origin[3], hd[3];  // for the conservative sample range of a triangle
+    int64_t count;
+};
+
+__device__ __forceinline__ void df_pos(const DfGrid& g, int64_t i, int64_t j, int64_t k, float* p)
+{
+    const int64_t ii[3] = {i, j, k};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        p[a] = g.lattice ? __fmul_rn((float)(g.ilo[a] + ii[a]), g.h[a]) : __fmaf_rn((float)ii[a], g.h[a], g.lo[a]);
+}
+
+struct Tris {
+    const float4* tris;   // leaf order, 3 per triangle
+    const int32_t* slot;  // input index -> leaf position
+    int64_t n;
+};
+
+__device__ __forceinline__ void tri_verts(const Tris& T, int32_t t, float* A, float* B, float* C)
+{
+    const int64_t k = 3 * (int64_t)__ldg(T.slot + t);
+    const float4 a = __ldg(T.tris + k), b = __ldg(T.tris + k + 1), c = __ldg(T.tris + k + 2);
+    A[0] = a.x; A[1] = a.y; A[2] = a.z;
+    B[0] = b.x; B[1] = b.y; B[2] = b.z;
+    C[0] = c.x; C[1] = c.y; C[2] = c.z;
+}
+
+__device__ __forceinline__ float site_d2(const Tris& T, const float* p, int32_t t)
+{
+    float A[3], B[3], C[3];
+    tri_verts(T, t, A, B, C);
+    return tri_d2_rn(p, A, B, C);
+}
+
+// keep the better of (cur, cur_d2) and candidate t
+__device__ __forceinline__ void site_consider(const Tris& T, const float* p, int32_t t, int32_t& cur, float& cur_d2)
+{
+    if (t < 0 || t == cur) return;
+    const float d2 = site_d2(T, p, t);
+    if (cur < 0 || d2 < cur_d2 || (d2 == cur_d2 && t < cur)) {
+        cur = t;
+        cur_d2 = d2;
+    }
+}
+
+// samples whose voxels the triangle's bounds may reach (one sample of margin)
+__device__ __forceinline__ bool tri_range(const DfGrid& g, const float* A, const float* B, const float* C,
+                                          int64_t r0[3], int64_t r1[3])
+{
+    bool empty = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double lo_t = (double)fminf(fminf(A[a], B[a]), C[a]) - g.hs[a];
+        const double hi_t = (double)fmaxf(fmaxf(A[a], B[a]), C[a]) + g.hs[a];
+        int64_t x0 = (int64_t)floor((lo_t - g.origin[a]) / g.hd[a]) - 1;
+        int64_t x1 = (int64_t)ceil((hi_t - g.origin[a]) / g.hd[a]) + 1;
+        x0 = x0 < 0 ? 0 : x0;
+        x1 = x1 > g.n[a] - 1 ? g.n[a] - 1 : x1;
+        r0[a] = x0;
+        r1[a] = x1;
+        empty = empty || x0 > x1;
+    }
+    return !empty;
+}
+
+__global__ void k_df_count(const DfGrid g, const Tris T, uint64_t* counts)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T.n) return;
+    float A[3], B[3], C[3];
+    tri_verts(T, (int32_t)t, A, B, C);
+    int64_t r0[3], r1[3];
+    counts[t] = tri_range(g, A, B, C, r0, r1) ? (uint64_t)((r1[0] - r0[0] + 1) * (r1[1] - r0[1] + 1) *
+                                                          (r1[2] - r0[2] + 1))
+                                              : 0ull;
+}
+
+// one thread per (triangle, voxel) pair: the triangle is found by binary search in the offsets
+__global__ void k_df_voxelise(const DfGrid g, const Tris T, const uint64_t* offsets, const uint64_t* counts,
+                              unsigned long long* keys)
+{
+    const uint64_t total = T.n > 0 ? offsets[T.n - 1] + counts[T.n - 1] : 0;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = T.n;  // the last triangle with offsets[t] <= w
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (offsets[mid] <= w) lo = mid; else hi = mid;
+        }
+        const int32_t t = (int32_t)lo;
+        float A[3], B[3], C[3];
+        tri_verts(T, t, A, B, C);
+        int64_t r0[3], r1[3];
+        tri_range(g, A, B, C, r0, r1);
+        const int64_t local = (int64_t)(w - offsets[t]);
+        const int64_t sx = r1[0] - r0[0] + 1, sy = r1[1] - r0[1] + 1;
+        const int64_t i = r0[0] + local % sx, j = r0[1] + (local / sx) % sy, k = r0[2] + local / (sx * sy);
+        float p[3];
+        df_pos(g, i, j, k, p);
+        if (!tri_box(p, g.hs, A, B, C)) continue;
+        const float d2 = tri_d2_rn(p, A, B, C);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (uint32_t)t;
+        atomicMin(keys + i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k), key);
+    }
+}
+
+__device__ __forceinline__ int64_t floordiv(int64_t x, int64_t y)  // y > 0
+{
+    return x >= 0 ? x / y : -((-x + y - 1) / y);
+}
+
+// sites from the voxelisation; on a cascade level also the coarser level's site
+__global__ void k_df_seed(const DfGrid g, const Tris T, const unsigned long long* keys, const int32_t* coarse,
+                          const DfGrid gc, int32_t* sites)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.count) return;
+    const unsigned long long key = keys[s];
+    int32_t cur = key == ~0ull ? -1 : (int32_t)(key & 0xffffffffull);
+    float cd2 = __uint_as_float((uint32_t)(key >> 32));
+    if (coarse) {
+        const int64_t ii[3] = {s % g.n[0], (s / g.n[0]) % g.n[1], s / ((int64_t)g.n[0] * g.n[1])};
+        int64_t jc[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int64_t j = floordiv(g.ilo[a] + ii[a] + 1, 2) - gc.ilo[a];
+            jc[a] = j < 0 ? 0 : (j > gc.n[a] - 1 ? gc.n[a] - 1 : j);
+        }
+        float p[3];
+        df_pos(g, ii[0], ii[1], ii[2], p);
+        site_consider(T, p, coarse[jc[0] + (int64_t)gc.n[0] * (jc[1] + (int64_t)gc.n[1] * jc[2])], cur, cd2);
+    }
+    sites[s] = cur;
+}
+
+__global__ void k_df_jfa(const DfGrid g, const Tris T, const int32_t* in, int32_t* out, int32_t step)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.count) return;
+    const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int64_t i = s % nx, j = (s / nx) % ny, k = s / (nx * ny);
+    float p[3];
+    df_pos(g, i, j, k, p);
+    int32_t best = -1;
+    float bd2 = 0.f;
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int64_t z = k + dz * step;
+        if (z < 0 || z >= nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int64_t y = j + dy * step;
+            if (y < 0 || y >= ny) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int64_t x = i + dx * step;
+                if (x < 0 || x >= nx) continue;
+                site_consider(T, p, __ldg(in + x + nx * (y + ny * z)), best, bd2);
+            }
+        }
+    }
+    out[s] = best;
+}
+
+// one thread per grid line along `axis`, walking in direction dir (+1 / -1)
+__global__ void k_df_sweep(const DfGrid g, const Tris T, int32_t* sites, int axis, int dir)
+{
+    const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
+    const int64_t n[3] = {g.n[0], g.n[1], g.n[2]};
+    const int64_t stride[3] = {1, n[0], n[0] * n[1]};
+    const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= n[oa] * n[ob]) return;
+    const int64_t ua = line % n[oa], ub = line / n[oa];
+    const int64_t base = ua * stride[oa] + ub * stride[ob];
+    int32_t prev = sites[base + (dir > 0 ? 0 : n[axis] - 1) * stride[axis]];
+    for (int64_t step = 1; step < n[axis]; ++step) {
+        const int64_t q = dir > 0 ? step : n[axis] - 1 - step;
+        const int64_t s = base + q * stride[axis];
+        int64_t ii[3];
+        ii[axis] = q;
+        ii[oa] = ua;
+        ii[ob] = ub;
+        float p[3];
+        df_pos(g, ii[0], ii[1], ii[2], p);
+        int32_t cur = sites[s];
+        float cd2 = cur >= 0 ? site_d2(T, p, cur) : 0.f;
+        site_consider(T, p, prev, cur, cd2);
+        sites[s] = cur;
+        prev = cur;
+    }
+}
+
+// signed distance to the site triangle (the exact bake's closest point and sign)
+__global__ void k_df_field(const DfGrid g, const Tris T, const float4* pn, const int32_t* sites, void* grid,
+                           int32_t f16)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.count) return;
+    const int32_t t = sites[s];
+    float v = __int_as_float(0x7f800000);
+    if (t >= 0) {
+        float pp[3];
+        df_pos(g, s % g.n[0], (s / g.n[0]) % g.n[1], s / ((int64_t)g.n[0] * g.n[1]), pp);
+        const float3 p = make_float3(pp[0], pp[1], pp[2]);
+        const int32_t k = __ldg(T.slot + t);
+        rtbake::Nearest nb = {__int_as_float(0x7f800000), -1, 0x7fffffff};
+        rtbake::consider(nb, p, T.tris, k);
+        v = rtbake::signed_distance(p, nb, T.tris, pn);
+    }
+    if (f16) reinterpret_cast<__half*>(grid)[s] = __float2half_rn(v);
+    else reinterpret_cast<float*>(grid)[s] = v;
+}
+
+// geometry of the single grid, or of cascade level k
+DfGrid df_grid(const rt_sdf* sdf, int k)
+{
+    DfGrid g;
+    memset(&g, 0, sizeof(g));
+    g.count = 1;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = sdf->n[a];
+        g.count *= sdf->n[a];
+    }
+    if (sdf->levels > 0) {
+        const float hk = ldexpf(sdf->h0, k);
+        g.lattice = 1;
+        for (int a = 0; a < 3; ++a) {
+            g.ilo[a] = sdf->ilo[k][a];
+            g.h[a] = hk;
+            g.origin[a] = (double)sdf->ilo[k][a] * (double)hk;
+        }
+    } else {
+        for (int a = 0; a < 3; ++a) {
+            g.lo[a] = sdf->lo[a];
+            g.h[a] = sdf->h[a];
+            g.origin[a] = sdf->lo[a];
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        volatile float half = 0.5f * g.h[a];
+        volatile float grow = g.h[a] * (1.f / 512.f);
+        g.hs[a] = half + grow;
+        g.hd[a] = g.h[a];
+    }
+    return g;
+}
+
+unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+// steps 1..stage for one grid (or level k); sites: g.count entries (device)
+rt_status df_sites_one(const rt_scene* sc, const rt_sdf* sdf, int k, const int32_t* coarse, int32_t stage,
+                       int32_t* sites, cudaStream_t s)
+{
+    const DfGrid g = df_grid(sdf, k);
+    DfGrid gc;
+    memset(&gc, 0, sizeof(gc));
+    if (coarse) gc = df_grid(sdf, k + 1);
+    const Tris T = {sc->tris, sc->slot, sc->n_tris};
+    if (g.count > 0x7fffffffLL * (int64_t)kBlock) return rt_fail(RT_ERR_INVALID_ARG, "grid too large");
+
+    // scratch: keys, the other site buffer, per-triangle counts and offsets, scan temp
+    size_t scan_bytes = 0;
+    RT_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, (const uint64_t*)nullptr, (uint64_t*)nullptr,
+                                              (int)T.n, s));
+    const size_t keys_bytes = (size_t)g.count * 8, tmp_bytes = (size_t)g.count * 4, tri_bytes = (size_t)T.n * 8;
+    const size_t total = keys_bytes + tmp_bytes + 2 * tri_bytes + scan_bytes + 4 * 256;
+    char* base = nullptr;
+    RT_CUDA_TRY(cudaMallocAsync((void**)&base, total, s));
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off = 0;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + off);
+    off = align(off + keys_bytes);
+    int32_t* tmp = reinterpret_cast<int32_t*>(base + off);
+    off = align(off + tmp_bytes);
+    uint64_t* counts = reinterpret_cast<uint64_t*>(base + off);
+    off = align(off + tri_bytes);
+    uint64_t* offsets = reinterpret_cast<uint64_t*>(base + off);
+    off = align(off + tri_bytes);
+    void* scan_tmp = base + off;
+
+    rt_status st = RT_OK;
+    cudaError_t e = cudaMemsetAsync(keys, 0xff, keys_bytes, s);
+    if (e != cudaSuccess) st = rt_cuda_fail(e, "cudaMemsetAsync");
+    if (st == RT_OK && T.n > 0) {
+        k_df_count<<<blocks_for(T.n), kBlock, 0, s>>>(g, T, counts);
+        e = cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, counts, offsets, (int)T.n, s);
+        if (e != cudaSuccess) st = rt_cuda_fail(e, "cub::DeviceScan::ExclusiveSum");
+        if (st == RT_OK) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            k_df_voxelise<<<(unsigned)(sms > 0 ? sms * 8 : 1024), kBlock, 0, s>>>(g, T, offsets, counts, keys);
+        }
+    }
+    if (st == RT_OK) k_df_seed<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, keys, coarse, gc, sites);
+    if (st == RT_OK && stage >= 2) {
+        int64_t nmax = g.n[0] > g.n[1] ? g.n[0] : g.n[1];
+        if (g.n[2] > nmax) nmax = g.n[2];
+        int64_t step = 1;
+        while (2 * step < nmax) step *= 2;
+        int32_t* a = sites;
+        int32_t* b = tmp;
+        for (; step >= 1; step /= 2) {
+            k_df_jfa<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, a, b, (int32_t)step);
+            int32_t* t = a;
+            a = b;
+            b = t;
+        }
+        if (a != sites) {
+            e = cudaMemcpyAsync(sites, a, (size_t)g.count * 4, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) st = rt_cuda_fail(e, "cudaMemcpyAsync");
+        }
+    }
+    if (st == RT_OK && stage >= 3) {
+        for (int axis = 0; axis < 3; ++axis) {
+            const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
+            const int64_t lines = (int64_t)g.n[oa] * g.n[ob];
+            for (int dir = 1; dir >= -1; dir -= 2) k_df_sweep<<<blocks_for(lines), kBlock, 0, s>>>(g, T, sites, axis, dir);
+        }
+    }
+    if (st == RT_OK) {
+        e = cudaGetLastError();
+        if (e != cudaSuccess) st = rt_cuda_fail(e, "field build launch");
+    }
+    e = cudaFreeAsync(base, s);
+    if (st == RT_OK && e != cudaSuccess) st = rt_cuda_fail(e, "cudaFreeAsync");
+    return st;
+}
+
+}  // namespace
+
+// Sites of every sample after step `stage` (1..3), coarsest cascade level first
+// (each level seeded also from the next coarser level's sites).  d_sites holds
+// levels * n^3 (or n0 n1 n2) entries.
+rt_status rt_launch_df_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t stage, int32_t* d_sites, cudaStream_t s)
+{
+    if (sdf->levels > 0) {
+        const int64_t per = (int64_t)sdf->n[0] * sdf->n[1] * sdf->n[2];
+        for (int k = sdf->levels - 1; k >= 0; --k) {
+            const int32_t* coarse = k + 1 < sdf->levels ? d_sites + (k + 1) * per : nullptr;
+            rt_status st = df_sites_one(sc, sdf, k, coarse, stage, d_sites + k * per, s);
+            if (st != RT_OK) return st;
+        }
+        return RT_OK;
+    }
+    return df_sites_one(sc, sdf, 0, nullptr, stage, d_sites, s);
+}
+
+// the field values from the sites (all levels of a cascade)
+rt_status rt_launch_df_field(const rt_scene* sc, const rt_sdf* sdf, const int32_t* d_sites, cudaStream_t s)
+{
+    const Tris T = {sc->tris, sc->slot, sc->n_tris};
+    const int levels = sdf->levels > 0 ? sdf->levels : 1;
+    const int64_t esz = sdf->dtype == RT_GRID_F16 ? 2 : 4;
+    for (int k = 0; k < levels; ++k) {
+        const DfGrid g = df_grid(sdf, k);
+        char* grid = static_cast<char*>(const_cast<void*>(sdf->grid)) + k * g.count * esz;
+        k_df_field<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, sc->pn, d_sites + k * g.count, grid,
+                                                        sdf->dtype == RT_GRID_F16);
+    }
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+// one cascade level rebuilt whole (rolling update): sites of level k from the
+// next coarser level's stored sites, then the field of that level
+rt_status rt_launch_df_level(const rt_scene* sc, const rt_sdf* sdf, int k, int32_t* d_sites, cudaStream_t s)
+{
+    const int64_t per = (int64_t)sdf->n[0] * sdf->n[1] * sdf->n[2];
+    const int32_t* coarse = k + 1 < sdf->levels ? d_sites + (k + 1) * per : nullptr;
+    rt_status st = df_sites_one(sc, sdf, k, coarse, 3, d_sites + k * per, s);
+    if (st != RT_OK) return st;
+    const Tris T = {sc->tris, sc->slot, sc->n_tris};
+    const DfGrid g = df_grid(sdf, k);
+    const int64_t esz = sdf->dtype == RT_GRID_F16 ? 2 : 4;
+    char* grid = static_cast<char*>(const_cast<void*>(sdf->grid)) + k * per * esz;
+    k_df_field<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, sc->pn, d_sites + k * per, grid, sdf->dtype == RT_GRID_F16);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}

@@ -18,6 +18,7 @@
 //   wtris  : 48 B per triangle in wide-leaf order (each node's leaf triangles contiguous)
 //   pn     : 112 B per triangle in leaf order: face normal, 3 edge and 3 vertex
 //            pseudonormals (float4 each), read only by the distance bake
+//   slot   : 4 B per triangle: input index -> leaf-order position (field build)
 //   grid   : caller memory, dense n0*n1*n2 float32 or float16, x fastest
 //   cells  : optional library copy of the grid with the 8 corners of every cell
 //            stored together (32 B float32 / 16 B float16 per cell, cells x
@@ -56,6 +57,7 @@ struct rt_scene {
     BNode* nodes;
     float4* tris;   // 3 per triangle
     float4* pn;     // 7 per triangle
+    int32_t* slot;  // input triangle index -> position in leaf order
     WNode* wnodes;  // null when the wide tree is not available
     float4* wtris;  // 3 per triangle
     int64_t n_wnodes;
@@ -81,6 +83,9 @@ struct rt_sdf {
     int32_t ilo[RT_MAX_LEVELS][3];
     void* scratch;      // one level, for rt_cascade_recenter
     int64_t scratch_bytes;
+    int32_t bake_method;  // method of the last rt_sdf_bake (RT_BAKE_JFA: sites kept)
+    int32_t* sites;       // site triangle of every sample after a field build (RT_BAKE_JFA)
+    int64_t sites_count;
 };
 
 // geometry of cascade level k as the queries see it (float, rounded once each)
@@ -162,3 +167,6 @@ void rt_cascade_geometry(const rt_sdf* sdf, int k, float lo[3], float hi[3], flo
 rt_status rt_launch_cascade_bake(const rt_scene* sc, const rt_sdf* sdf, int k, int32_t method, const void* keep,
                                  const int32_t shift[3], cudaStream_t s);
 rt_status rt_launch_cascade_cells(const rt_sdf* sdf, int k, cudaStream_t s);
+rt_status rt_launch_df_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t stage, int32_t* d_sites, cudaStream_t s);
+rt_status rt_launch_df_field(const rt_scene* sc, const rt_sdf* sdf, const int32_t* d_sites, cudaStream_t s);
+rt_status rt_launch_df_level(const rt_scene* sc, const rt_sdf* sdf, int k, int32_t* d_sites, cudaStream_t s);

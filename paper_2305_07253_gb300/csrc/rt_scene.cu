@@ -231,11 +231,13 @@ __global__ void k_pack_nodes(const int2* child, int64_t n_int, const float4* lea
     out[i] = b;
 }
 
-__global__ void k_pack_tris(const float* V, const int32_t* F, const int32_t* order, int64_t n, float4* out)
+__global__ void k_pack_tris(const float* V, const int32_t* F, const int32_t* order, int64_t n, float4* out,
+                            int32_t* slot)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int32_t t = order[k];
+    slot[t] = (int32_t)k;
     float3 a = load_vert(V, F[3 * (int64_t)t]), b = load_vert(V, F[3 * (int64_t)t + 1]),
            c = load_vert(V, F[3 * (int64_t)t + 2]);
     out[3 * k] = make_float4(a.x, a.y, a.z, __int_as_float(t));
@@ -417,13 +419,15 @@ rt_status rt_build_scene(const float* V, int64_t nv, const int32_t* F, int64_t n
     RT_CUDA_TRY(cudaMalloc(&sc->nodes, (size_t)(nt > 1 ? nt - 1 : 1) * sizeof(BNode)));
     RT_CUDA_TRY(cudaMalloc(&sc->tris, (size_t)nt * 3 * sizeof(float4)));
     RT_CUDA_TRY(cudaMalloc(&sc->pn, (size_t)nt * 7 * sizeof(float4)));
-    sc->bytes = (int64_t)((nt > 1 ? nt - 1 : 1) * sizeof(BNode) + nt * 3 * sizeof(float4) + nt * 7 * sizeof(float4));
+    RT_CUDA_TRY(cudaMalloc(&sc->slot, (size_t)nt * sizeof(int32_t)));
+    sc->bytes = (int64_t)((nt > 1 ? nt - 1 : 1) * sizeof(BNode) + nt * 3 * sizeof(float4) + nt * 7 * sizeof(float4) +
+                          nt * sizeof(int32_t));
     if (nt > 1) {
         k_pack_nodes<<<grid_for(nt - 1), kBlock, 0, s>>>(child.as<int2>(), nt - 1, llo.as<float4>(), lhi.as<float4>(),
                                                           nlo.as<float4>(), nhi.as<float4>(), pad, sc->nodes);
         RT_CUDA_TRY(cudaGetLastError());
     }
-    k_pack_tris<<<grid_for(nt), kBlock, 0, s>>>(V, F, order, nt, sc->tris);
+    k_pack_tris<<<grid_for(nt), kBlock, 0, s>>>(V, F, order, nt, sc->tris, sc->slot);
     RT_CUDA_TRY(cudaGetLastError());
     {
         rt_status ws = rt_build_wide(sc, child.as<int2>(), nrange.as<int2>(), nlo.as<float4>(), nhi.as<float4>(),
