@@ -345,7 +345,11 @@ extern "C" rt_status rt_cascade_recenter(const rt_scene* sc, rt_sdf* sdf, const 
         if (st != RT_OK) return st;
     }
     int32_t count = 0;
-    // coarsest first: a level baked whole is bounded by the next coarser one at its new place
+    const bool jfa = sdf->bake_method == RT_BAKE_JFA && sdf->sites;
+    int rebuilt[RT_MAX_LEVELS];
+    int n_rebuilt = 0;
+    // coarsest first: a level baked whole is bounded (exact bake) or seeded (the
+    // paper's build) by the next coarser one at its new place
     for (int k = sdf->levels - 1; k >= 0; --k) {
         int32_t shift[3];
         bool same = true, far = false;
@@ -356,7 +360,7 @@ extern "C" rt_status rt_cascade_recenter(const rt_scene* sc, rt_sdf* sdf, const 
         }
         if (same) continue;
         const void* keep = nullptr;
-        if (!far && sdf->bake_method != RT_BAKE_JFA) {
+        if (!far && !jfa) {
             if (!sdf->scratch) {
                 RT_CUDA_TRY(cudaMalloc(&sdf->scratch, (size_t)level_bytes));
                 sdf->scratch_bytes = level_bytes;
@@ -366,14 +370,20 @@ extern "C" rt_status rt_cascade_recenter(const rt_scene* sc, rt_sdf* sdf, const 
             keep = sdf->scratch;
         }
         for (int a = 0; a < 3; ++a) sdf->ilo[k][a] = ilo[k][a];
-        if (sdf->bake_method == RT_BAKE_JFA && sdf->sites)
-            st = rt_launch_df_level(sc, sdf, k, sdf->sites, s);  // the paper's build, level rebuilt whole
-        else
-            st = rt_launch_cascade_bake(sc, sdf, k, RT_BAKE_BVH, keep, shift, s);
+        ++count;
+        if (jfa) {  // the paper's build: moved levels are rebuilt whole, together, below
+            rebuilt[n_rebuilt++] = k;
+            continue;
+        }
+        st = rt_launch_cascade_bake(sc, sdf, k, RT_BAKE_BVH, keep, shift, s);
         if (st != RT_OK) return st;
         st = rt_launch_cascade_cells(sdf, k, s);
         if (st != RT_OK) return st;
-        ++count;
+    }
+    if (n_rebuilt > 0) {
+        st = rt_launch_df_levels(sc, sdf, rebuilt, n_rebuilt, sdf->sites, s);
+        for (int l = 0; l < n_rebuilt && st == RT_OK; ++l) st = rt_launch_cascade_cells(sdf, rebuilt[l], s);
+        if (st != RT_OK) return st;
     }
     float lo[3], hi[3], h, ih;
     rt_cascade_geometry(sdf, sdf->levels - 1, lo, hi, &h, &ih);

@@ -5,9 +5,9 @@
 //
 //   1. Conservative voxelisation.  Sample s owns the voxel box of side
 //      h (1 + 2^-8) centred on it.  Every triangle is tested (separating axes,
-//      Akenine-Moller, JGT 2001) against the voxels its bounds can reach, one
-//      thread per (triangle, voxel) pair after a prefix sum over the
-//      triangles; an overlapping triangle is a candidate site of the sample.
+//      Akenine-Moller, JGT 2001) against the voxels its bounds can reach: one
+//      thread per triangle when they are few, one block per triangle when they
+//      are many; an overlapping triangle is a candidate site of the sample.
 //      The best candidate wins through a 64-bit atomicMin on (squared
 //      distance bits, triangle index).  On a cascade level below the
 //      coarsest, the site of the nearest sample of the next coarser level is a
@@ -24,8 +24,6 @@
 // triangle, triangle index).  Every operation of steps 1-3 is rounded once
 // (explicit intrinsics), so the sites are those of the CPU checker's single
 // precision build, bit for bit.
-#include <cub/device/device_scan.cuh>
-
 #include "rt_bake_dev.cuh"
 #include "rt_trace_dev.cuh"
 
@@ -152,7 +150,9 @@ struct DfGrid {
     int32_t lattice;
     int32_t ilo[3];
     float lo[3], h[3], hs[3];
-    double origin[3], hd[3];  // for the conservative sample range of a triangle
+    // conservative sample range of a triangle: origin, 1/h and a margin of a
+    // small fraction of a voxel (much more than the rounding of the positions)
+    float origin_f[3], ih_f[3], margin[3];
     int64_t count;
 };
 
@@ -197,64 +197,88 @@ __device__ __forceinline__ void site_consider(const Tris& T, const float* p, int
     }
 }
 
-// samples whose voxels the triangle's bounds may reach (one sample of margin)
+// samples whose voxels the triangle's bounds may reach: the range is widened by
+// a small fraction of a voxel, far more than the rounding of the sample
+// positions, and the separating-axis test decides
 __device__ __forceinline__ bool tri_range(const DfGrid& g, const float* A, const float* B, const float* C,
                                           int64_t r0[3], int64_t r1[3])
 {
     bool empty = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double lo_t = (double)fminf(fminf(A[a], B[a]), C[a]) - g.hs[a];
-        const double hi_t = (double)fmaxf(fmaxf(A[a], B[a]), C[a]) + g.hs[a];
-        int64_t x0 = (int64_t)floor((lo_t - g.origin[a]) / g.hd[a]) - 1;
-        int64_t x1 = (int64_t)ceil((hi_t - g.origin[a]) / g.hd[a]) + 1;
-        x0 = x0 < 0 ? 0 : x0;
-        x1 = x1 > g.n[a] - 1 ? g.n[a] - 1 : x1;
+        const float lo_t = fminf(fminf(A[a], B[a]), C[a]) - g.hs[a];
+        const float hi_t = fmaxf(fmaxf(A[a], B[a]), C[a]) + g.hs[a];
+        const float x0f = ceilf((lo_t - g.origin_f[a] - g.margin[a]) * g.ih_f[a]);
+        const float x1f = floorf((hi_t - g.origin_f[a] + g.margin[a]) * g.ih_f[a]);
+        // clamp in float first: far-away triangles give values beyond the int range
+        const int64_t x0 = (int64_t)fmaxf(x0f, 0.f);
+        const int64_t x1 = (int64_t)fminf(x1f, (float)(g.n[a] - 1));
         r0[a] = x0;
         r1[a] = x1;
-        empty = empty || x0 > x1;
+        empty = empty || x0 > x1 || x1f < 0.f || x0f > (float)(g.n[a] - 1);
     }
     return !empty;
 }
 
-__global__ void k_df_count(const DfGrid g, const Tris T, uint64_t* counts)
+// test one (triangle, sample) pair and keep the better site of the sample
+__device__ __forceinline__ void vox_pair(const DfGrid& g, int32_t t, const float* A, const float* B, const float* C,
+                                         int64_t i, int64_t j, int64_t k, unsigned long long* keys)
+{
+    float p[3];
+    df_pos(g, i, j, k, p);
+    if (!tri_box(p, g.hs, A, B, C)) return;
+    const float d2 = tri_d2_rn(p, A, B, C);
+    const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (uint32_t)t;
+    atomicMin(keys + i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k), key);
+}
+
+constexpr int64_t kSmallPairs = 64;  // a thread tests a triangle's voxels itself up to this many
+
+// the grids voxelised by one pass over the triangles (all levels of a cascade at once)
+struct VoxPass {
+    DfGrid g[RT_MAX_LEVELS];
+    unsigned long long* keys[RT_MAX_LEVELS];
+    int32_t count;
+};
+
+// one thread per triangle and level: small ranges are tested here, large ones
+// listed (triangle, level) for k_df_vox_big
+__global__ void k_df_vox_small(const VoxPass vp, const Tris T, int2* big, unsigned* n_big)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T.n) return;
     float A[3], B[3], C[3];
     tri_verts(T, (int32_t)t, A, B, C);
-    int64_t r0[3], r1[3];
-    counts[t] = tri_range(g, A, B, C, r0, r1) ? (uint64_t)((r1[0] - r0[0] + 1) * (r1[1] - r0[1] + 1) *
-                                                          (r1[2] - r0[2] + 1))
-                                              : 0ull;
+    for (int l = 0; l < vp.count; ++l) {
+        const DfGrid& g = vp.g[l];
+        int64_t r0[3], r1[3];
+        if (!tri_range(g, A, B, C, r0, r1)) continue;
+        const int64_t count = (r1[0] - r0[0] + 1) * (r1[1] - r0[1] + 1) * (r1[2] - r0[2] + 1);
+        if (count > kSmallPairs) {
+            big[atomicAdd(n_big, 1u)] = make_int2((int)t, l);
+            continue;
+        }
+        for (int64_t k = r0[2]; k <= r1[2]; ++k)
+            for (int64_t j = r0[1]; j <= r1[1]; ++j)
+                for (int64_t i = r0[0]; i <= r1[0]; ++i) vox_pair(g, (int32_t)t, A, B, C, i, j, k, vp.keys[l]);
+    }
 }
 
-// one thread per (triangle, voxel) pair: the triangle is found by binary search in the offsets
-__global__ void k_df_voxelise(const DfGrid g, const Tris T, const uint64_t* offsets, const uint64_t* counts,
-                              unsigned long long* keys)
+// one block per listed (triangle, level), threads over its voxels
+__global__ void k_df_vox_big(const VoxPass vp, const Tris T, const int2* big, const unsigned* n_big)
 {
-    const uint64_t total = T.n > 0 ? offsets[T.n - 1] + counts[T.n - 1] : 0;
-    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total;
-         w += (uint64_t)gridDim.x * blockDim.x) {
-        int64_t lo = 0, hi = T.n;  // the last triangle with offsets[t] <= w
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (offsets[mid] <= w) lo = mid; else hi = mid;
-        }
-        const int32_t t = (int32_t)lo;
+    const unsigned nb = *n_big;
+    for (unsigned b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int2 e = big[b];
+        const DfGrid& g = vp.g[e.y];
         float A[3], B[3], C[3];
-        tri_verts(T, t, A, B, C);
+        tri_verts(T, e.x, A, B, C);
         int64_t r0[3], r1[3];
         tri_range(g, A, B, C, r0, r1);
-        const int64_t local = (int64_t)(w - offsets[t]);
         const int64_t sx = r1[0] - r0[0] + 1, sy = r1[1] - r0[1] + 1;
-        const int64_t i = r0[0] + local % sx, j = r0[1] + (local / sx) % sy, k = r0[2] + local / (sx * sy);
-        float p[3];
-        df_pos(g, i, j, k, p);
-        if (!tri_box(p, g.hs, A, B, C)) continue;
-        const float d2 = tri_d2_rn(p, A, B, C);
-        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (uint32_t)t;
-        atomicMin(keys + i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k), key);
+        const int64_t count = sx * sy * (r1[2] - r0[2] + 1);
+        for (int64_t w = threadIdx.x; w < count; w += blockDim.x)
+            vox_pair(g, e.x, A, B, C, r0[0] + w % sx, r0[1] + (w / sx) % sy, r0[2] + w / (sx * sy), vp.keys[e.y]);
     }
 }
 
@@ -313,7 +337,12 @@ __global__ void k_df_jfa(const DfGrid g, const Tris T, const int32_t* in, int32_
     out[s] = best;
 }
 
-// one thread per grid line along `axis`, walking in direction dir (+1 / -1)
+// one thread per grid line along `axis`, walking in direction dir (+1 / -1).
+// The line's sites are read eight at a time (independent loads in flight
+// together); each is the value before this sweep reaches it, as in the
+// sequential sweep, since the sweep only writes samples it has passed.
+constexpr int kSweepChunk = 8;
+
 __global__ void k_df_sweep(const DfGrid g, const Tris T, int32_t* sites, int axis, int dir)
 {
     const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
@@ -323,21 +352,35 @@ __global__ void k_df_sweep(const DfGrid g, const Tris T, int32_t* sites, int axi
     if (line >= n[oa] * n[ob]) return;
     const int64_t ua = line % n[oa], ub = line / n[oa];
     const int64_t base = ua * stride[oa] + ub * stride[ob];
-    int32_t prev = sites[base + (dir > 0 ? 0 : n[axis] - 1) * stride[axis]];
-    for (int64_t step = 1; step < n[axis]; ++step) {
-        const int64_t q = dir > 0 ? step : n[axis] - 1 - step;
-        const int64_t s = base + q * stride[axis];
-        int64_t ii[3];
-        ii[axis] = q;
-        ii[oa] = ua;
-        ii[ob] = ub;
-        float p[3];
-        df_pos(g, ii[0], ii[1], ii[2], p);
-        int32_t cur = sites[s];
-        float cd2 = cur >= 0 ? site_d2(T, p, cur) : 0.f;
-        site_consider(T, p, prev, cur, cd2);
-        sites[s] = cur;
-        prev = cur;
+    const int64_t len = n[axis];
+    int32_t prev = sites[base + (dir > 0 ? 0 : len - 1) * stride[axis]];
+    for (int64_t c0 = 1; c0 < len; c0 += kSweepChunk) {
+        int32_t buf[kSweepChunk];
+#pragma unroll
+        for (int u = 0; u < kSweepChunk; ++u) {
+            const int64_t step = c0 + u;
+            const int64_t q = dir > 0 ? step : len - 1 - step;
+            buf[u] = step < len ? sites[base + q * stride[axis]] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kSweepChunk; ++u) {
+            const int64_t step = c0 + u;
+            if (step >= len) break;
+            int32_t cur = buf[u];
+            if (prev >= 0 && prev != cur) {  // otherwise nothing can change
+                const int64_t q = dir > 0 ? step : len - 1 - step;
+                int64_t ii[3];
+                ii[axis] = q;
+                ii[oa] = ua;
+                ii[ob] = ub;
+                float p[3];
+                df_pos(g, ii[0], ii[1], ii[2], p);
+                float cd2 = cur >= 0 ? site_d2(T, p, cur) : 0.f;
+                site_consider(T, p, prev, cur, cd2);
+                sites[base + q * stride[axis]] = cur;
+            }
+            prev = cur;
+        }
     }
 }
 
@@ -372,49 +415,50 @@ DfGrid df_grid(const rt_sdf* sdf, int k)
         g.n[a] = sdf->n[a];
         g.count *= sdf->n[a];
     }
+    double origin[3];
     if (sdf->levels > 0) {
         const float hk = ldexpf(sdf->h0, k);
         g.lattice = 1;
         for (int a = 0; a < 3; ++a) {
             g.ilo[a] = sdf->ilo[k][a];
             g.h[a] = hk;
-            g.origin[a] = (double)sdf->ilo[k][a] * (double)hk;
+            origin[a] = (double)sdf->ilo[k][a] * (double)hk;
         }
     } else {
         for (int a = 0; a < 3; ++a) {
             g.lo[a] = sdf->lo[a];
             g.h[a] = sdf->h[a];
-            g.origin[a] = sdf->lo[a];
+            origin[a] = sdf->lo[a];
         }
     }
     for (int a = 0; a < 3; ++a) {
         volatile float half = 0.5f * g.h[a];
         volatile float grow = g.h[a] * (1.f / 512.f);
         g.hs[a] = half + grow;
-        g.hd[a] = g.h[a];
+        g.ih_f[a] = 1.0f / g.h[a];
+        g.margin[a] = (float)(1e-2 * g.h[a] + 1e-5 * (fabs(origin[a]) + g.n[a] * (double)g.h[a]));
+        g.origin_f[a] = (float)origin[a];
     }
     return g;
 }
 
 unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-// steps 1..stage for one grid (or level k); sites: g.count entries (device)
-rt_status df_sites_one(const rt_scene* sc, const rt_sdf* sdf, int k, const int32_t* coarse, int32_t stage,
-                       int32_t* sites, cudaStream_t s)
+// Steps 1..stage for the levels `lv[0..nl)` (0 for a single grid), given in
+// the order they are built: each level's seeding reads the sites of level+1,
+// which must be final by then.  All levels are voxelised in one pass over the
+// triangles.  sites_of(k): device array of level k's sites.
+rt_status df_build(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t stage, int32_t* d_sites,
+                   cudaStream_t s)
 {
-    const DfGrid g = df_grid(sdf, k);
-    DfGrid gc;
-    memset(&gc, 0, sizeof(gc));
-    if (coarse) gc = df_grid(sdf, k + 1);
     const Tris T = {sc->tris, sc->slot, sc->n_tris};
-    if (g.count > 0x7fffffffLL * (int64_t)kBlock) return rt_fail(RT_ERR_INVALID_ARG, "grid too large");
+    const int64_t per = (int64_t)sdf->n[0] * sdf->n[1] * sdf->n[2];
+    if (per > 0x7fffffffLL * (int64_t)kBlock) return rt_fail(RT_ERR_INVALID_ARG, "grid too large");
+    const int cascade_levels = sdf->levels;
 
-    // scratch: keys, the other site buffer, per-triangle counts and offsets, scan temp
-    size_t scan_bytes = 0;
-    RT_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, (const uint64_t*)nullptr, (uint64_t*)nullptr,
-                                              (int)T.n, s));
-    const size_t keys_bytes = (size_t)g.count * 8, tmp_bytes = (size_t)g.count * 4, tri_bytes = (size_t)T.n * 8;
-    const size_t total = keys_bytes + tmp_bytes + 2 * tri_bytes + scan_bytes + 4 * 256;
+    // scratch: keys of every listed level, one spare site buffer, the large-triangle list
+    const size_t keys_bytes = (size_t)per * 8 * nl, tmp_bytes = (size_t)per * 4, big_bytes = (size_t)T.n * 8 * nl;
+    const size_t total = keys_bytes + tmp_bytes + big_bytes + 4 * 256;
     char* base = nullptr;
     RT_CUDA_TRY(cudaMallocAsync((void**)&base, total, s));
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -423,50 +467,68 @@ rt_status df_sites_one(const rt_scene* sc, const rt_sdf* sdf, int k, const int32
     off = align(off + keys_bytes);
     int32_t* tmp = reinterpret_cast<int32_t*>(base + off);
     off = align(off + tmp_bytes);
-    uint64_t* counts = reinterpret_cast<uint64_t*>(base + off);
-    off = align(off + tri_bytes);
-    uint64_t* offsets = reinterpret_cast<uint64_t*>(base + off);
-    off = align(off + tri_bytes);
-    void* scan_tmp = base + off;
+    int2* big = reinterpret_cast<int2*>(base + off);
+    off = align(off + big_bytes);
+    unsigned* n_big = reinterpret_cast<unsigned*>(base + off);
 
     rt_status st = RT_OK;
     cudaError_t e = cudaMemsetAsync(keys, 0xff, keys_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n_big, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) st = rt_cuda_fail(e, "cudaMemsetAsync");
+
+    // 1. voxelisation of all listed levels
     if (st == RT_OK && T.n > 0) {
-        k_df_count<<<blocks_for(T.n), kBlock, 0, s>>>(g, T, counts);
-        e = cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, counts, offsets, (int)T.n, s);
-        if (e != cudaSuccess) st = rt_cuda_fail(e, "cub::DeviceScan::ExclusiveSum");
-        if (st == RT_OK) {
-            int dev = 0, sms = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            k_df_voxelise<<<(unsigned)(sms > 0 ? sms * 8 : 1024), kBlock, 0, s>>>(g, T, offsets, counts, keys);
+        VoxPass vp;
+        memset(&vp, 0, sizeof(vp));
+        vp.count = nl;
+        for (int l = 0; l < nl; ++l) {
+            vp.g[l] = df_grid(sdf, lv[l]);
+            vp.keys[l] = keys + (size_t)l * per;
         }
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        k_df_vox_small<<<blocks_for(T.n), kBlock, 0, s>>>(vp, T, big, n_big);
+        k_df_vox_big<<<(unsigned)(sms > 0 ? sms * 4 : 512), kBlock, 0, s>>>(vp, T, big, n_big);
     }
-    if (st == RT_OK) k_df_seed<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, keys, coarse, gc, sites);
-    if (st == RT_OK && stage >= 2) {
-        int64_t nmax = g.n[0] > g.n[1] ? g.n[0] : g.n[1];
-        if (g.n[2] > nmax) nmax = g.n[2];
-        int64_t step = 1;
-        while (2 * step < nmax) step *= 2;
-        int32_t* a = sites;
-        int32_t* b = tmp;
-        for (; step >= 1; step /= 2) {
-            k_df_jfa<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, a, b, (int32_t)step);
-            int32_t* t = a;
-            a = b;
-            b = t;
+    // per level: seeding, jump flooding, sweeps
+    for (int l = 0; l < nl && st == RT_OK; ++l) {
+        const int k = lv[l];
+        int32_t* sites = d_sites + (int64_t)k * per;
+        const DfGrid g = df_grid(sdf, k);
+        DfGrid gc;
+        memset(&gc, 0, sizeof(gc));
+        const int32_t* coarse = nullptr;
+        if (cascade_levels > 0 && k + 1 < cascade_levels) {
+            gc = df_grid(sdf, k + 1);
+            coarse = d_sites + (int64_t)(k + 1) * per;
         }
-        if (a != sites) {
-            e = cudaMemcpyAsync(sites, a, (size_t)g.count * 4, cudaMemcpyDeviceToDevice, s);
-            if (e != cudaSuccess) st = rt_cuda_fail(e, "cudaMemcpyAsync");
+        k_df_seed<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, keys + (size_t)l * per, coarse, gc, sites);
+        if (stage >= 2) {
+            int64_t nmax = g.n[0] > g.n[1] ? g.n[0] : g.n[1];
+            if (g.n[2] > nmax) nmax = g.n[2];
+            int64_t step = 1;
+            while (2 * step < nmax) step *= 2;
+            int32_t* a = sites;
+            int32_t* b = tmp;
+            for (; step >= 1; step /= 2) {
+                k_df_jfa<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, a, b, (int32_t)step);
+                int32_t* t = a;
+                a = b;
+                b = t;
+            }
+            if (a != sites) {
+                e = cudaMemcpyAsync(sites, a, (size_t)g.count * 4, cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) st = rt_cuda_fail(e, "cudaMemcpyAsync");
+            }
         }
-    }
-    if (st == RT_OK && stage >= 3) {
-        for (int axis = 0; axis < 3; ++axis) {
-            const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
-            const int64_t lines = (int64_t)g.n[oa] * g.n[ob];
-            for (int dir = 1; dir >= -1; dir -= 2) k_df_sweep<<<blocks_for(lines), kBlock, 0, s>>>(g, T, sites, axis, dir);
+        if (st == RT_OK && stage >= 3) {
+            for (int axis = 0; axis < 3; ++axis) {
+                const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
+                const int64_t lines = (int64_t)g.n[oa] * g.n[ob];
+                for (int dir = 1; dir >= -1; dir -= 2)
+                    k_df_sweep<<<(unsigned)((lines + 63) / 64), 64, 0, s>>>(g, T, sites, axis, dir);
+            }
         }
     }
     if (st == RT_OK) {
@@ -485,16 +547,10 @@ rt_status df_sites_one(const rt_scene* sc, const rt_sdf* sdf, int k, const int32
 // levels * n^3 (or n0 n1 n2) entries.
 rt_status rt_launch_df_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t stage, int32_t* d_sites, cudaStream_t s)
 {
-    if (sdf->levels > 0) {
-        const int64_t per = (int64_t)sdf->n[0] * sdf->n[1] * sdf->n[2];
-        for (int k = sdf->levels - 1; k >= 0; --k) {
-            const int32_t* coarse = k + 1 < sdf->levels ? d_sites + (k + 1) * per : nullptr;
-            rt_status st = df_sites_one(sc, sdf, k, coarse, stage, d_sites + k * per, s);
-            if (st != RT_OK) return st;
-        }
-        return RT_OK;
-    }
-    return df_sites_one(sc, sdf, 0, nullptr, stage, d_sites, s);
+    int lv[RT_MAX_LEVELS];
+    const int nl = sdf->levels > 0 ? sdf->levels : 1;
+    for (int l = 0; l < nl; ++l) lv[l] = nl - 1 - l;  // coarsest first
+    return df_build(sc, sdf, lv, nl, stage, d_sites, s);
 }
 
 // the field values from the sites (all levels of a cascade)
@@ -513,19 +569,25 @@ rt_status rt_launch_df_field(const rt_scene* sc, const rt_sdf* sdf, const int32_
     return RT_OK;
 }
 
-// one cascade level rebuilt whole (rolling update): sites of level k from the
-// next coarser level's stored sites, then the field of that level
-rt_status rt_launch_df_level(const rt_scene* sc, const rt_sdf* sdf, int k, int32_t* d_sites, cudaStream_t s)
+// the listed cascade levels rebuilt whole (rolling update), in the order given
+// (coarsest first), each seeded from the next coarser level's stored sites;
+// then their field values
+rt_status rt_launch_df_levels(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t* d_sites,
+                              cudaStream_t s)
 {
-    const int64_t per = (int64_t)sdf->n[0] * sdf->n[1] * sdf->n[2];
-    const int32_t* coarse = k + 1 < sdf->levels ? d_sites + (k + 1) * per : nullptr;
-    rt_status st = df_sites_one(sc, sdf, k, coarse, 3, d_sites + k * per, s);
+    if (nl <= 0) return RT_OK;
+    rt_status st = df_build(sc, sdf, lv, nl, 3, d_sites, s);
     if (st != RT_OK) return st;
     const Tris T = {sc->tris, sc->slot, sc->n_tris};
-    const DfGrid g = df_grid(sdf, k);
+    const int64_t per = (int64_t)sdf->n[0] * sdf->n[1] * sdf->n[2];
     const int64_t esz = sdf->dtype == RT_GRID_F16 ? 2 : 4;
-    char* grid = static_cast<char*>(const_cast<void*>(sdf->grid)) + k * per * esz;
-    k_df_field<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, sc->pn, d_sites + k * per, grid, sdf->dtype == RT_GRID_F16);
+    for (int l = 0; l < nl; ++l) {
+        const int k = lv[l];
+        const DfGrid g = df_grid(sdf, k);
+        char* grid = static_cast<char*>(const_cast<void*>(sdf->grid)) + k * per * esz;
+        k_df_field<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, sc->pn, d_sites + k * per, grid,
+                                                        sdf->dtype == RT_GRID_F16);
+    }
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }

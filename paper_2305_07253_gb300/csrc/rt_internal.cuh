@@ -169,4 +169,5 @@ rt_status rt_launch_cascade_bake(const rt_scene* sc, const rt_sdf* sdf, int k, i
 rt_status rt_launch_cascade_cells(const rt_sdf* sdf, int k, cudaStream_t s);
 rt_status rt_launch_df_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t stage, int32_t* d_sites, cudaStream_t s);
 rt_status rt_launch_df_field(const rt_scene* sc, const rt_sdf* sdf, const int32_t* d_sites, cudaStream_t s);
-rt_status rt_launch_df_level(const rt_scene* sc, const rt_sdf* sdf, int k, int32_t* d_sites, cudaStream_t s);
+rt_status rt_launch_df_levels(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t* d_sites,
+                              cudaStream_t s);
