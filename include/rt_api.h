@@ -260,6 +260,29 @@ rt_status rt_cascade_create(const void* d_grid, int32_t dtype, int32_t levels, i
 rt_status rt_cascade_recenter(const rt_scene* scene, rt_sdf* sdf, const float center[3], void* stream,
                               int32_t* moved);
 
+/* The combined query of rt_trace_combined for rays and hit records in host
+ * memory: the rays are copied to d_rays, traced, and the records copied back
+ * to h_hits, in `chunks` pieces (0: 4; 1..64; from 3 pieces on, the first and
+ * last are half as large as the others) pipelined over two copy streams and
+ * up to four compute streams owned by the library, so that the upload of one
+ * piece, the traces of the previous ones and the download of the one before
+ * overlap.  The
+ * paper's queries start on the GPU (Section 3); this call serves callers whose
+ * rays live in host memory.
+ *   h_rays, h_hits  host memory of n rays / records; page-locked memory
+ *                   (cudaHostAlloc, torch pin_memory) is needed for the copies
+ *                   to overlap, pageable memory works but serialises them
+ *   d_rays, d_hits  device memory of n rays / records (caller-owned staging)
+ * Enqueued behind the work already on `stream`; when the call returns, all of
+ * its work is ordered before later work on `stream`, and h_hits is complete
+ * once `stream` is synchronised.  Overlapping calls on different streams share
+ * the library's copy streams (they serialise there, results stay correct).
+ * Errors as rt_trace_combined, plus RT_ERR_INVALID_ARG for a null host buffer
+ * or chunks outside 0..64. */
+rt_status rt_trace_combined_host(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* h_rays, int64_t n,
+                                 const rt_split_params* params, rt_hit* h_hits, rt_ray* d_rays, rt_hit* d_hits,
+                                 int32_t chunks, void* stream);
+
 /* Geometry of level k of a cascade: lattice origin ilo[3] and voxel edge *h.
  * Errors: RT_ERR_INVALID_ARG when sdf is not a cascade or k is out of range. */
 rt_status rt_cascade_level(const rt_sdf* sdf, int32_t k, int32_t ilo[3], float* h);

@@ -38,7 +38,7 @@ EXPORTS = ("rt_scene_build", "rt_scene_info_get", "rt_scene_destroy", "rt_sdf_cr
            "rt_sdf_prepare", "rt_sdf_bake", "rt_trace_bvh", "rt_trace_sdf", "rt_trace_combined",
            "rt_trace_combined_counted", "rt_trace_combined_timed", "rt_trace_combined_noalloc",
            "rt_trace_combined_backward", "rt_trace_batches", "rt_set_tuning", "rt_get_tuning",
-           "rt_cascade_create", "rt_cascade_recenter", "rt_cascade_level", "rt_sdf_sites", "rt_last_error",
+           "rt_cascade_create", "rt_cascade_recenter", "rt_cascade_level", "rt_sdf_sites", "rt_trace_combined_host", "rt_last_error",
            "rt_version")
 
 
@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
             "rt_cascade_recenter": [P, P, P, P, P],
             "rt_cascade_level": [P, i32, P, P],
             "rt_sdf_sites": [P, P, i32, P, P],
+            "rt_trace_combined_host": [P, P, P, i64, P, P, P, P, i32, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -423,14 +424,18 @@ def hit_fields(hits: torch.Tensor) -> dict:
 
 def trace_combined_from_host(scene: Scene | None, sdf: Sdf | None, rays_host: torch.Tensor, params: rt_split_params,
                              hits_host: torch.Tensor, rays_dev: torch.Tensor, hits_dev: torch.Tensor,
-                             stream=None) -> torch.Tensor:
-    """Host-to-host query: copy pinned host rays to the device, trace, copy the hit
-    records back into pinned host memory.  The caller synchronises the stream."""
-    s = torch.cuda.current_stream() if stream is None else stream
-    with torch.cuda.stream(s):
-        rays_dev.copy_(rays_host, non_blocking=True)
-        rt_trace_combined(scene, sdf, rays_dev, params, hits_dev, stream=s)
-        hits_host.copy_(hits_dev, non_blocking=True)
+                             chunks: int = 0, stream=None) -> torch.Tensor:
+    """Host-to-host query (rt_trace_combined_host): pinned host rays in, hit records
+    out into pinned host memory, the copies of one chunk overlapping the trace of
+    the next.  rays_dev / hits_dev are the device staging buffers.  The caller
+    synchronises the stream before reading hits_host."""
+    assert not rays_host.is_cuda and not hits_host.is_cuda
+    assert rays_host.is_contiguous() and hits_host.is_contiguous()
+    n = rays_host.shape[0]
+    _check(lib().rt_trace_combined_host(scene.handle if scene else None, sdf.handle if sdf else None,
+                                        ctypes.c_void_p(rays_host.data_ptr()), n, ctypes.byref(params),
+                                        ctypes.c_void_p(hits_host.data_ptr()), _dptr(rays_dev), _dptr(hits_dev),
+                                        int(chunks), _stream(stream)))
     return hits_host
 
 

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "rt_internal.cuh"
@@ -525,6 +526,94 @@ extern "C" rt_status rt_trace_combined(const rt_scene* sc, const rt_sdf* sdf, co
                                        const rt_split_params* params, rt_hit* hits, void* stream)
 {
     return trace_common(sc, sdf, rays, n, params, hits, nullptr, stream);
+}
+
+// copy streams and events of the host-to-host pipeline, per device
+namespace {
+constexpr int kMaxChunks = 64;
+constexpr int kComputeStreams = 4;
+struct HostPipe {
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaStream_t comp[kComputeStreams] = {};
+    cudaEvent_t start = nullptr, done = nullptr;
+    cudaEvent_t ev_in[kMaxChunks] = {}, ev_tr[kMaxChunks] = {};
+    bool ready = false;
+};
+std::mutex g_pipe_mu;
+HostPipe g_pipe[64];
+
+rt_status host_pipe(HostPipe*& out)
+{
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return rt_fail(RT_ERR_INVALID_ARG, "device %d out of range", dev);
+    HostPipe& p = g_pipe[dev];
+    if (!p.ready) {
+        RT_CUDA_TRY(cudaStreamCreateWithFlags(&p.in, cudaStreamNonBlocking));
+        RT_CUDA_TRY(cudaStreamCreateWithFlags(&p.out, cudaStreamNonBlocking));
+        for (int c = 0; c < kComputeStreams; ++c) RT_CUDA_TRY(cudaStreamCreateWithFlags(&p.comp[c], cudaStreamNonBlocking));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming));
+        for (int c = 0; c < kMaxChunks; ++c) {
+            RT_CUDA_TRY(cudaEventCreateWithFlags(&p.ev_in[c], cudaEventDisableTiming));
+            RT_CUDA_TRY(cudaEventCreateWithFlags(&p.ev_tr[c], cudaEventDisableTiming));
+        }
+        p.ready = true;
+    }
+    out = &p;
+    return RT_OK;
+}
+}  // namespace
+
+extern "C" rt_status rt_trace_combined_host(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* h_rays, int64_t n,
+                                            const rt_split_params* params, rt_hit* h_hits, rt_ray* d_rays,
+                                            rt_hit* d_hits, int32_t chunks, void* stream)
+{
+    rt_status st = check_params(params);
+    if (st != RT_OK) return st;
+    st = check_io(d_rays, n, d_hits);
+    if (st != RT_OK) return st;
+    if (n > 0 && (!h_rays || !h_hits)) return rt_fail(RT_ERR_INVALID_ARG, "null host ray or hit buffer");
+    if (chunks < 0 || chunks > kMaxChunks) return rt_fail(RT_ERR_INVALID_ARG, "chunks %d not in 0..%d", chunks, kMaxChunks);
+    if (n == 0) return RT_OK;
+    if (chunks == 0) chunks = 4;
+    if (chunks > n) chunks = (int32_t)n;
+    // the library's copy streams are shared by all callers on this device
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    HostPipe* p = nullptr;
+    st = host_pipe(p);
+    if (st != RT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    RT_CUDA_TRY(cudaEventRecord(p->start, s));
+    RT_CUDA_TRY(cudaStreamWaitEvent(p->in, p->start, 0));
+    RT_CUDA_TRY(cudaStreamWaitEvent(p->out, p->start, 0));
+    // pieces are traced on alternating compute streams: the tail of one piece's
+    // persistent stage kernels (its slowest queries) overlaps the next piece
+    const int ncomp = chunks < kComputeStreams ? chunks : kComputeStreams;
+    for (int c = 0; c < ncomp; ++c) RT_CUDA_TRY(cudaStreamWaitEvent(p->comp[c], p->start, 0));
+    // the first and last pieces are half as large as the others: the pipeline
+    // fills (first upload) and drains (last download) sooner
+    const int64_t weight_total = chunks >= 3 ? 2 * (int64_t)chunks - 2 : chunks;
+    int64_t done_w = 0;
+    for (int c = 0; c < chunks; ++c) {
+        const int64_t w = (chunks >= 3 && (c == 0 || c == chunks - 1)) ? 1 : (chunks >= 3 ? 2 : 1);
+        const int64_t b = n * done_w / weight_total;
+        done_w += w;
+        const int64_t m = n * done_w / weight_total - b;
+        if (m <= 0) continue;
+        cudaStream_t cs = p->comp[c % ncomp];
+        RT_CUDA_TRY(cudaMemcpyAsync(d_rays + b, h_rays + b, (size_t)m * sizeof(rt_ray), cudaMemcpyHostToDevice, p->in));
+        RT_CUDA_TRY(cudaEventRecord(p->ev_in[c], p->in));
+        RT_CUDA_TRY(cudaStreamWaitEvent(cs, p->ev_in[c], 0));
+        st = trace_common(sc, sdf, d_rays + b, m, params, d_hits + b, nullptr, cs);
+        if (st != RT_OK) return st;
+        RT_CUDA_TRY(cudaEventRecord(p->ev_tr[c], cs));
+        RT_CUDA_TRY(cudaStreamWaitEvent(p->out, p->ev_tr[c], 0));
+        RT_CUDA_TRY(cudaMemcpyAsync(h_hits + b, d_hits + b, (size_t)m * sizeof(rt_hit), cudaMemcpyDeviceToHost, p->out));
+    }
+    RT_CUDA_TRY(cudaEventRecord(p->done, p->out));
+    RT_CUDA_TRY(cudaStreamWaitEvent(s, p->done, 0));
+    return RT_OK;
 }
 
 extern "C" rt_status rt_trace_combined_counted(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
