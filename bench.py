@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="set up, then run only warmup+steps launches of the --only traces (for ncu); prints timings")
     ap.add_argument("--only", default="all", choices=["all", "combined", "bvh", "sdf"])
-    ap.add_argument("--workload", default="frame", choices=["frame", "batching", "fit", "precision", "ao", "cascade"],
+    ap.add_argument("--out", default="gpurun_out/ao_images", help="output folder of --workload ao-images")
+    ap.add_argument("--workload", default="frame", choices=["frame", "batching", "fit", "precision", "ao", "cascade", "ao-images"],
                     help="frame: the 1080p GI headline; batching: 8 frames of mixed primary/shadow/AO/GI "
                          "batches; fit: gradient fit of a noisy 128^3 grid; precision: float16 vs float32 "
                          "512^3 grid on the 8.2 M-triangle scene")
@@ -862,6 +863,89 @@ def run_cascade(args):
     print(json.dumps(line), flush=True)
 
 
+def _write_png(path, img):
+    """8-bit greyscale PNG of a (h, w) array in [0, 1]."""
+    import struct
+    import zlib
+    a = (np.clip(img, 0.0, 1.0) * 255.0 + 0.5).astype(np.uint8)
+    h, w = a.shape
+    raw = b"".join(b"\x00" + a[y].tobytes() for y in range(h))
+
+    def chunk(tag, data):
+        return struct.pack(">I", len(data)) + tag + data + struct.pack(">I", zlib.crc32(tag + data) & 0xffffffff)
+    with open(path, "wb") as f:
+        f.write(b"\x89PNG\r\n\x1a\n" + chunk(b"IHDR", struct.pack(">IIBBBBB", w, h, 8, 0, 0, 0, 0)) +
+                chunk(b"IDAT", zlib.compress(raw, 6)) + chunk(b"IEND", b""))
+
+
+def run_ao_images(args):
+    """AO images (the image form of the paper's Fig. 2): per pixel the surface
+    point the camera sees (primary rays, triangles), spp cosine rays to t_ao,
+    AO = share that escapes; with triangles only, the combined query (m = 2) and
+    the field only, on the dense exact grid and on the paper's 5 x 64^3 cascade.
+    Writes the images and |AO - AO(triangles only)| x 4 error images as PNG to
+    --out, prints the mean errors."""
+    import torch
+
+    import paper_2305_07253_gb300 as rq
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    s = S.make_scene("frame")
+    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
+    W, H, spp, t_ao = 960, 540, 16, 2.0
+    prim_rays = R.primary_rays(s, W, H)
+    hits = rq.hit_fields(rq.rt_trace_bvh(scene, torch.from_numpy(prim_rays).to(dev)))
+    t = hits["t"].cpu().numpy().astype(np.float64)
+    prim = hits["prim"].cpu().numpy()
+    seen = np.isfinite(t)
+    o = prim_rays[:, 0:3].astype(np.float64)
+    d = prim_rays[:, 4:7].astype(np.float64)
+    V = s.verts.astype(np.float64)
+    F = s.tris
+    p = o + np.where(seen, t, 0.0)[:, None] * d
+    tri = np.where(seen, prim, 0)
+    nrm = np.cross(V[F[tri, 1]] - V[F[tri, 0]], V[F[tri, 2]] - V[F[tri, 0]])
+    nrm /= np.maximum(np.linalg.norm(nrm, axis=1, keepdims=True), 1e-30)
+    nrm *= np.where(np.einsum("ij,ij->i", nrm, d) > 0, -1.0, 1.0)[:, None]  # facing the camera
+    ao_rays = torch.from_numpy(R.ao_rays(p, nrm, np.full(p.shape[0], spp, dtype=np.int64), 44, t_ao,
+                                         1e-3 * s.diagonal)).to(dev)
+    # pixel of every primary ray (the rays come in 8x8 screen tiles)
+    py, px = np.mgrid[0:H, 0:W]
+    order = R._tile_order(px.ravel(), py.ravel(), W)
+    pix_y, pix_x = py.ravel()[order], px.ravel()[order]
+    n = W * H
+    dense = torch.empty((256, 256, 256), dtype=torch.float32, device=dev)
+    sdf_dense = rq.rt_sdf_create(dense, s.lo, s.hi)
+    rq.rt_sdf_bake(scene, sdf_dense, rq.BAKE_BVH)
+    cg = torch.empty((5, 64, 64, 64), dtype=torch.float32, device=dev)
+    sdf_c = rq.rt_cascade_create(cg, 0.1, np.asarray(s.camera.eye, dtype=np.float32))
+    rq.rt_sdf_bake(scene, sdf_c, rq.BAKE_JFA)
+    forms = {"triangles": (None, rq.split_params(mode=rq.MODE_BVH)),
+             "combined_dense": (sdf_dense, rq.split_params(mode=rq.MODE_SPLIT1, m_near=M_MIDDLE)),
+             "field_dense": (sdf_dense, rq.split_params(mode=rq.MODE_SDF)),
+             "combined_cascade": (sdf_c, rq.split_params(mode=rq.MODE_SPLIT1, m_near=M_MIDDLE)),
+             "field_cascade": (sdf_c, rq.split_params(mode=rq.MODE_SDF))}
+    os.makedirs(args.out, exist_ok=True)
+    out, ref = {}, None
+    for name, (sdf, prm) in forms.items():
+        h = rq.rt_trace_combined(scene, sdf, ao_rays, prm)
+        ao = 1.0 - (h[:, 4] > 0).float().reshape(n, spp).mean(dim=1).cpu().numpy()
+        ao[~seen] = 1.0
+        img = np.ones((H, W))
+        img[pix_y, pix_x] = ao
+        _write_png(os.path.join(args.out, f"ao_{name}.png"), img)
+        if ref is None:
+            ref = img
+        else:
+            err = np.abs(img - ref)
+            _write_png(os.path.join(args.out, f"ao_err_{name}.png"), 4.0 * err)
+            out[name] = {"mean_abs_dAO": float(err.mean()), "share_off_0.1": float((err > 0.1).mean())}
+    print(json.dumps({"metric": "AO images vs triangles only", "config": {"workload": "frame-ao-images", "width": W,
+                                                                         "height": H, "spp": spp, "t_ao": t_ao},
+                      "images": sorted(os.listdir(args.out)), "errors": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -876,6 +960,8 @@ def main():
         run_ao(args)
     elif args.workload == "cascade":
         run_cascade(args)
+    elif args.workload == "ao-images":
+        run_ao_images(args)
     else:
         run_ours(args)
 
