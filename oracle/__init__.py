@@ -83,6 +83,7 @@ def lib():
             L.or_trace_combined_cascade.argtypes = [P, P, P, i64, P, i32, i32, P, P]
             L.or_df_sites.argtypes = [P, P, P, P, i32, i32, P]
             L.or_df_field.argtypes = [P, P, P, P]
+            L.or_df_sweep.argtypes = [P, P, P]
             L.or_tri_box_overlap.argtypes = [P, P, P, P, P]
             L.or_tri_box_overlap.restype = ctypes.c_int
             L.or_tri_dist2_f.argtypes = [P, P, P, P]
@@ -316,8 +317,11 @@ def df_sites(bvh: BVH, grid, stage: int = 3, nthreads: int | None = None):
     """Sites (triangle index per sample, -1 for none) of the paper's field build
     after `stage` (1 voxelisation, 2 jump flooding, 3 sweeps).  One grid: an
     array of n0*n1*n2; a cascade: (levels, n^3), built coarsest level first, each
-    level seeded also from the next coarser one."""
+    level seeded also from the next coarser one's sites after its jump flooding,
+    and swept after all levels are flooded."""
     if isinstance(grid, Cascade):
+        # coarsest level first, each seeded from the coarser level's sites after
+        # jump flooding (or after voxelisation for stage 1); then the sweeps of all levels
         out = np.zeros((grid.levels, grid.n ** 3), dtype=np.int32)
         for k in reversed(range(grid.levels)):
             g, _, _ = _level_grid(grid, k)
@@ -325,7 +329,12 @@ def df_sites(bvh: BVH, grid, stage: int = 3, nthreads: int | None = None):
             if k + 1 < grid.levels:
                 coarse = _ptr(out[k + 1])
                 gc, _, _ = _level_grid(grid, k + 1)
-            lib().or_df_sites(bvh.h, g, coarse, gc, int(stage), nthreads or default_threads(), _ptr(out[k]))
+            lib().or_df_sites(bvh.h, g, coarse, gc, int(min(stage, 2)), nthreads or default_threads(),
+                              _ptr(out[k]))
+        if stage >= 3:
+            for k in range(grid.levels):
+                g, _, _ = _level_grid(grid, k)
+                lib().or_df_sweep(bvh.h, g, _ptr(out[k]))
         return out
     g, count, _ = _level_grid(grid)
     out = np.zeros(count, dtype=np.int32)
