@@ -425,8 +425,10 @@ extern "C" rt_status rt_sdf_bake(const rt_scene* sc, rt_sdf* sdf, int32_t method
             RT_CUDA_TRY(cudaMalloc(&sdf->sites, (size_t)count * sizeof(int32_t)));
             sdf->sites_count = count;
         }
-        st = rt_launch_df_sites(sc, sdf, 3, sdf->sites, s);
-        if (st == RT_OK) st = rt_launch_df_field(sc, sdf, sdf->sites, s);
+        int lv[RT_MAX_LEVELS];
+        const int nl = sdf->levels > 0 ? sdf->levels : 1;
+        for (int l = 0; l < nl; ++l) lv[l] = nl - 1 - l;  // coarsest first
+        st = rt_launch_df_levels(sc, sdf, lv, nl, sdf->sites, s);
     } else {
         st = rt_launch_bake(sc, sdf, method, s);
     }

@@ -311,6 +311,11 @@ __global__ void k_df_seed(const DfGrid g, const Tris T, const unsigned long long
     sites[s] = cur;
 }
 
+// Neighbours mostly carry the same few sites: the distances of the last few
+// distinct candidates are kept, so each is evaluated once per sample.  The
+// result is the same minimum.
+constexpr int kSiteCache = 4;
+
 __global__ void k_df_jfa(const DfGrid g, const Tris T, const int32_t* in, int32_t* out, int32_t step)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -321,6 +326,9 @@ __global__ void k_df_jfa(const DfGrid g, const Tris T, const int32_t* in, int32_
     df_pos(g, i, j, k, p);
     int32_t best = -1;
     float bd2 = 0.f;
+    int32_t seen[kSiteCache];
+#pragma unroll
+    for (int c = 0; c < kSiteCache; ++c) seen[c] = -1;
     for (int dz = -1; dz <= 1; ++dz) {
         const int64_t z = k + dz * step;
         if (z < 0 || z >= nz) continue;
@@ -330,7 +338,16 @@ __global__ void k_df_jfa(const DfGrid g, const Tris T, const int32_t* in, int32_
             for (int dx = -1; dx <= 1; ++dx) {
                 const int64_t x = i + dx * step;
                 if (x < 0 || x >= nx) continue;
-                site_consider(T, p, __ldg(in + x + nx * (y + ny * z)), best, bd2);
+                const int32_t t = __ldg(in + x + nx * (y + ny * z));
+                if (t < 0) continue;
+                bool hit = false;
+#pragma unroll
+                for (int c = 0; c < kSiteCache; ++c) hit = hit || seen[c] == t;
+                if (hit) continue;  // already evaluated at this sample
+#pragma unroll
+                for (int c = kSiteCache - 1; c > 0; --c) seen[c] = seen[c - 1];
+                seen[0] = t;
+                site_consider(T, p, t, best, bd2);
             }
         }
     }
@@ -343,13 +360,26 @@ __global__ void k_df_jfa(const DfGrid g, const Tris T, const int32_t* in, int32_
 // sequential sweep, since the sweep only writes samples it has passed.
 constexpr int kSweepChunk = 8;
 
-__global__ void k_df_sweep(const DfGrid g, const Tris T, int32_t* sites, int axis, int dir)
+// the grids swept by one launch (all levels of a cascade at once)
+struct SweepPass {
+    DfGrid g[RT_MAX_LEVELS];
+    int32_t* sites[RT_MAX_LEVELS];
+    int64_t first_line[RT_MAX_LEVELS + 1];  // prefix sums of the levels' line counts
+    int32_t count;
+};
+
+__global__ void k_df_sweep(const SweepPass sp, const Tris T, int axis, int dir)
 {
     const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= sp.first_line[sp.count]) return;
+    int l = 0;
+    while (l + 1 < sp.count && t >= sp.first_line[l + 1]) ++l;
+    const DfGrid& g = sp.g[l];
+    int32_t* sites = sp.sites[l];
+    const int64_t line = t - sp.first_line[l];
     const int64_t n[3] = {g.n[0], g.n[1], g.n[2]};
     const int64_t stride[3] = {1, n[0], n[0] * n[1]};
-    const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (line >= n[oa] * n[ob]) return;
     const int64_t ua = line % n[oa], ub = line / n[oa];
     const int64_t base = ua * stride[oa] + ub * stride[ob];
     const int64_t len = n[axis];
@@ -445,11 +475,14 @@ DfGrid df_grid(const rt_sdf* sdf, int k)
 unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
 // Steps 1..stage for the levels `lv[0..nl)` (0 for a single grid), given in
-// the order they are built: each level's seeding reads the sites of level+1,
-// which must be final by then.  All levels are voxelised in one pass over the
-// triangles.  sites_of(k): device array of level k's sites.
-rt_status df_build(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t stage, int32_t* d_sites,
-                   cudaStream_t s)
+// the order they are built (coarsest first).  All levels are voxelised in one
+// pass over the triangles; then each level is seeded (on a cascade also from
+// the next coarser level's sites in `jfa`) and flooded, leaving its sites in
+// `jfa`; the final sites go to `out` after the sweeps of all levels, which
+// run together.  jfa, out: one int32 per sample of every level (indexed by
+// level), device.
+rt_status df_build(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t stage, int32_t* jfa,
+                   int32_t* out, cudaStream_t s)
 {
     const Tris T = {sc->tris, sc->slot, sc->n_tris};
     const int64_t per = (int64_t)sdf->n[0] * sdf->n[1] * sdf->n[2];
@@ -491,17 +524,17 @@ rt_status df_build(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl,
         k_df_vox_small<<<blocks_for(T.n), kBlock, 0, s>>>(vp, T, big, n_big);
         k_df_vox_big<<<(unsigned)(sms > 0 ? sms * 4 : 512), kBlock, 0, s>>>(vp, T, big, n_big);
     }
-    // per level: seeding, jump flooding, sweeps
+    // 2. per level, coarsest first: seeding and jump flooding
     for (int l = 0; l < nl && st == RT_OK; ++l) {
         const int k = lv[l];
-        int32_t* sites = d_sites + (int64_t)k * per;
+        int32_t* sites = jfa + (int64_t)k * per;
         const DfGrid g = df_grid(sdf, k);
         DfGrid gc;
         memset(&gc, 0, sizeof(gc));
         const int32_t* coarse = nullptr;
         if (cascade_levels > 0 && k + 1 < cascade_levels) {
             gc = df_grid(sdf, k + 1);
-            coarse = d_sites + (int64_t)(k + 1) * per;
+            coarse = jfa + (int64_t)(k + 1) * per;
         }
         k_df_seed<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, keys + (size_t)l * per, coarse, gc, sites);
         if (stage >= 2) {
@@ -522,13 +555,26 @@ rt_status df_build(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl,
                 if (e != cudaSuccess) st = rt_cuda_fail(e, "cudaMemcpyAsync");
             }
         }
-        if (st == RT_OK && stage >= 3) {
-            for (int axis = 0; axis < 3; ++axis) {
-                const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
-                const int64_t lines = (int64_t)g.n[oa] * g.n[ob];
-                for (int dir = 1; dir >= -1; dir -= 2)
-                    k_df_sweep<<<(unsigned)((lines + 63) / 64), 64, 0, s>>>(g, T, sites, axis, dir);
+        if (st == RT_OK && out != jfa) {
+            e = cudaMemcpyAsync(out + (int64_t)k * per, sites, (size_t)g.count * 4, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) st = rt_cuda_fail(e, "cudaMemcpyAsync");
+        }
+    }
+    // 3. the sweeps of all listed levels, six launches
+    if (st == RT_OK && stage >= 3) {
+        for (int axis = 0; axis < 3; ++axis) {
+            const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
+            SweepPass sp;
+            memset(&sp, 0, sizeof(sp));
+            sp.count = nl;
+            for (int l = 0; l < nl; ++l) {
+                sp.g[l] = df_grid(sdf, lv[l]);
+                sp.sites[l] = out + (int64_t)lv[l] * per;
+                sp.first_line[l + 1] = sp.first_line[l] + (int64_t)sp.g[l].n[oa] * sp.g[l].n[ob];
             }
+            const int64_t lines = sp.first_line[nl];
+            for (int dir = 1; dir >= -1; dir -= 2)
+                k_df_sweep<<<(unsigned)((lines + 63) / 64), 64, 0, s>>>(sp, T, axis, dir);
         }
     }
     if (st == RT_OK) {
@@ -540,44 +586,9 @@ rt_status df_build(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl,
     return st;
 }
 
-}  // namespace
-
-// Sites of every sample after step `stage` (1..3), coarsest cascade level first
-// (each level seeded also from the next coarser level's sites).  d_sites holds
-// levels * n^3 (or n0 n1 n2) entries.
-rt_status rt_launch_df_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t stage, int32_t* d_sites, cudaStream_t s)
+rt_status field_values(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, const int32_t* sites,
+                       cudaStream_t s)
 {
-    int lv[RT_MAX_LEVELS];
-    const int nl = sdf->levels > 0 ? sdf->levels : 1;
-    for (int l = 0; l < nl; ++l) lv[l] = nl - 1 - l;  // coarsest first
-    return df_build(sc, sdf, lv, nl, stage, d_sites, s);
-}
-
-// the field values from the sites (all levels of a cascade)
-rt_status rt_launch_df_field(const rt_scene* sc, const rt_sdf* sdf, const int32_t* d_sites, cudaStream_t s)
-{
-    const Tris T = {sc->tris, sc->slot, sc->n_tris};
-    const int levels = sdf->levels > 0 ? sdf->levels : 1;
-    const int64_t esz = sdf->dtype == RT_GRID_F16 ? 2 : 4;
-    for (int k = 0; k < levels; ++k) {
-        const DfGrid g = df_grid(sdf, k);
-        char* grid = static_cast<char*>(const_cast<void*>(sdf->grid)) + k * g.count * esz;
-        k_df_field<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, sc->pn, d_sites + k * g.count, grid,
-                                                        sdf->dtype == RT_GRID_F16);
-    }
-    RT_CUDA_TRY(cudaGetLastError());
-    return RT_OK;
-}
-
-// the listed cascade levels rebuilt whole (rolling update), in the order given
-// (coarsest first), each seeded from the next coarser level's stored sites;
-// then their field values
-rt_status rt_launch_df_levels(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t* d_sites,
-                              cudaStream_t s)
-{
-    if (nl <= 0) return RT_OK;
-    rt_status st = df_build(sc, sdf, lv, nl, 3, d_sites, s);
-    if (st != RT_OK) return st;
     const Tris T = {sc->tris, sc->slot, sc->n_tris};
     const int64_t per = (int64_t)sdf->n[0] * sdf->n[1] * sdf->n[2];
     const int64_t esz = sdf->dtype == RT_GRID_F16 ? 2 : 4;
@@ -585,9 +596,46 @@ rt_status rt_launch_df_levels(const rt_scene* sc, const rt_sdf* sdf, const int* 
         const int k = lv[l];
         const DfGrid g = df_grid(sdf, k);
         char* grid = static_cast<char*>(const_cast<void*>(sdf->grid)) + k * per * esz;
-        k_df_field<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, sc->pn, d_sites + k * per, grid,
+        k_df_field<<<blocks_for(g.count), kBlock, 0, s>>>(g, T, sc->pn, sites + k * per, grid,
                                                         sdf->dtype == RT_GRID_F16);
     }
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
+}
+
+}  // namespace
+
+// Sites of every sample after step `stage` (1..3), coarsest cascade level first
+// (each level seeded also from the next coarser level's flooded sites).
+// d_sites holds levels * n^3 (or n0 n1 n2) entries.
+rt_status rt_launch_df_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t stage, int32_t* d_sites, cudaStream_t s)
+{
+    int lv[RT_MAX_LEVELS];
+    const int nl = sdf->levels > 0 ? sdf->levels : 1;
+    for (int l = 0; l < nl; ++l) lv[l] = nl - 1 - l;  // coarsest first
+    const int64_t count = (int64_t)nl * sdf->n[0] * sdf->n[1] * sdf->n[2];
+    int32_t* jfa = nullptr;
+    RT_CUDA_TRY(cudaMallocAsync((void**)&jfa, (size_t)count * 4, s));
+    rt_status st = df_build(sc, sdf, lv, nl, stage, jfa, d_sites, s);
+    cudaError_t e = cudaFreeAsync(jfa, s);
+    if (st == RT_OK && e != cudaSuccess) st = rt_cuda_fail(e, "cudaFreeAsync");
+    return st;
+}
+
+// The listed levels (all of them for a full build; the moved ones of a rolling
+// update), coarsest first: sites into `jfa_store` (kept by the handle: the
+// seeds of finer levels later), field values from the swept sites.
+rt_status rt_launch_df_levels(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t* jfa_store,
+                              cudaStream_t s)
+{
+    if (nl <= 0) return RT_OK;
+    const int levels = sdf->levels > 0 ? sdf->levels : 1;
+    const int64_t count = (int64_t)levels * sdf->n[0] * sdf->n[1] * sdf->n[2];
+    int32_t* out = nullptr;
+    RT_CUDA_TRY(cudaMallocAsync((void**)&out, (size_t)count * 4, s));
+    rt_status st = df_build(sc, sdf, lv, nl, 3, jfa_store, out, s);
+    if (st == RT_OK) st = field_values(sc, sdf, lv, nl, out, s);
+    cudaError_t e = cudaFreeAsync(out, s);
+    if (st == RT_OK && e != cudaSuccess) st = rt_cuda_fail(e, "cudaFreeAsync");
+    return st;
 }

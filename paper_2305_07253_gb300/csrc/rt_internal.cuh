@@ -84,7 +84,8 @@ struct rt_sdf {
     void* scratch;      // one level, for rt_cascade_recenter
     int64_t scratch_bytes;
     int32_t bake_method;  // method of the last rt_sdf_bake (RT_BAKE_JFA: sites kept)
-    int32_t* sites;       // site triangle of every sample after a field build (RT_BAKE_JFA)
+    int32_t* sites;       // flooded site of every sample after a field build (RT_BAKE_JFA): the
+                          // seeds of finer levels when a rolling update rebuilds them
     int64_t sites_count;
 };
 
@@ -168,6 +169,5 @@ rt_status rt_launch_cascade_bake(const rt_scene* sc, const rt_sdf* sdf, int k, i
                                  const int32_t shift[3], cudaStream_t s);
 rt_status rt_launch_cascade_cells(const rt_sdf* sdf, int k, cudaStream_t s);
 rt_status rt_launch_df_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t stage, int32_t* d_sites, cudaStream_t s);
-rt_status rt_launch_df_field(const rt_scene* sc, const rt_sdf* sdf, const int32_t* d_sites, cudaStream_t s);
-rt_status rt_launch_df_levels(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t* d_sites,
+rt_status rt_launch_df_levels(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t* jfa_store,
                               cudaStream_t s);
