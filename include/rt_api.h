@@ -148,6 +148,17 @@ rt_status rt_scene_build(const float* d_verts, int64_t n_verts, const int32_t* d
 rt_status rt_scene_info_get(const rt_scene* scene, rt_scene_info* info);
 rt_status rt_scene_destroy(rt_scene* scene);
 
+/* Copy of the binary BVH for inspection (tests, debugging, visualisation).
+ * d_nodes: n_nodes x 64 bytes (rt_scene_info.n_nodes), each node as 16 floats:
+ *   c0.lo.x c0.hi.x c0.lo.y c0.hi.y | c1.lo.x c1.hi.x c1.lo.y c1.hi.y |
+ *   c0.lo.z c0.hi.z c1.lo.z c1.hi.z | child0 child1 (int32) - -
+ * where a child >= 0 is an internal node and a child < 0 the leaf ~child, a
+ * position in the triangle array; node 0 is the root (a scene of one triangle
+ * has no node: its root is leaf 0).  d_tris: n_tris x 48 bytes, triangles in
+ * leaf order as v0.xyz, input index (int32 bits), v1.xyz, -, v2.xyz, -.  Both
+ * caller device memory; either may be null.  Enqueued on `stream`. */
+rt_status rt_scene_export(const rt_scene* scene, void* d_nodes, void* d_tris, void* stream);
+
 /* Describe a dense distance-field grid held in caller memory (not copied;
  * the memory must outlive the handle).  Samples sit at lo + (i,j,k)*h with
  * h = (hi - lo) / (n - 1) per axis, x fastest: value (i,j,k) is at element

@@ -38,7 +38,7 @@ EXPORTS = ("rt_scene_build", "rt_scene_info_get", "rt_scene_destroy", "rt_sdf_cr
            "rt_sdf_prepare", "rt_sdf_bake", "rt_trace_bvh", "rt_trace_sdf", "rt_trace_combined",
            "rt_trace_combined_counted", "rt_trace_combined_timed", "rt_trace_combined_noalloc",
            "rt_trace_combined_backward", "rt_trace_batches", "rt_set_tuning", "rt_get_tuning",
-           "rt_cascade_create", "rt_cascade_recenter", "rt_cascade_level", "rt_sdf_sites", "rt_trace_combined_host", "rt_last_error",
+           "rt_cascade_create", "rt_cascade_recenter", "rt_cascade_level", "rt_sdf_sites", "rt_trace_combined_host", "rt_scene_export", "rt_last_error",
            "rt_version")
 
 
@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
             "rt_cascade_level": [P, i32, P, P],
             "rt_sdf_sites": [P, P, i32, P, P],
             "rt_trace_combined_host": [P, P, P, i64, P, P, P, P, i32, P],
+            "rt_scene_export": [P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -199,6 +200,17 @@ class Sdf:
 
     def __del__(self):
         self.close()
+
+
+def rt_scene_export(scene: Scene, stream=None):
+    """(nodes float32 (n_nodes, 16), tris float32 (n_tris, 12)) copies of the
+    binary BVH; the int32 fields (children, input indices) are their bit patterns."""
+    inf = scene.info()
+    nodes = torch.empty((max(inf.n_nodes, 0), 16), dtype=torch.float32, device="cuda")
+    tris = torch.empty((inf.n_tris, 12), dtype=torch.float32, device="cuda")
+    _check(lib().rt_scene_export(scene.handle, _dptr(nodes) if nodes.numel() else None, _dptr(tris),
+                                 _stream(stream)))
+    return nodes, tris
 
 
 def rt_scene_build(verts: torch.Tensor, tris: torch.Tensor, stream=None) -> Scene:

@@ -206,6 +206,21 @@ extern "C" rt_status rt_scene_info_get(const rt_scene* sc, rt_scene_info* info)
     return RT_OK;
 }
 
+extern "C" rt_status rt_scene_export(const rt_scene* sc, void* d_nodes, void* d_tris, void* stream)
+{
+    if (!sc) return rt_fail(RT_ERR_INVALID_ARG, "scene is null");
+    rt_status st = device_matches(sc->device);
+    if (st != RT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_nodes && sc->n_tris > 1)
+        RT_CUDA_TRY(cudaMemcpyAsync(d_nodes, sc->nodes, (size_t)(sc->n_tris - 1) * sizeof(BNode),
+                                    cudaMemcpyDeviceToDevice, s));
+    if (d_tris)
+        RT_CUDA_TRY(cudaMemcpyAsync(d_tris, sc->tris, (size_t)sc->n_tris * 3 * sizeof(float4),
+                                    cudaMemcpyDeviceToDevice, s));
+    return RT_OK;
+}
+
 extern "C" rt_status rt_scene_destroy(rt_scene* sc)
 {
     if (!sc) return RT_OK;

@@ -492,3 +492,58 @@ def test_autotuner_picks_a_valid_tuning(tiny):
         assert all(now[k] == v for k, v in best.items())
     finally:
         rq.rt_set_tuning(prev)
+
+
+def _check_tree(nodes, tris, n_tris, max_depth, verts, F):
+    """Invariants of the exported binary BVH: every triangle is one leaf, every
+    child box holds all triangles below it, and no path is deeper than reported."""
+    n_nodes = nodes.shape[0]
+    child = nodes[:, 12:14].view(np.int32)
+    prim = tris[:, 3].view(np.int32)
+    assert sorted(prim.tolist()) == list(range(n_tris))
+    # triangle vertices in leaf order match the input mesh
+    V = verts.astype(np.float32)
+    np.testing.assert_array_equal(tris[:, 0:3], V[F[prim, 0]])
+    np.testing.assert_array_equal(tris[:, 4:7], V[F[prim, 1]])
+    np.testing.assert_array_equal(tris[:, 8:11], V[F[prim, 2]])
+    lo_t = np.minimum(np.minimum(tris[:, 0:3], tris[:, 4:7]), tris[:, 8:11])
+    hi_t = np.maximum(np.maximum(tris[:, 0:3], tris[:, 4:7]), tris[:, 8:11])
+    # bounds of every subtree, bottom-up over an explicit order (children first)
+    order, parent_seen = [], np.zeros(n_nodes, dtype=np.int64)
+    stack, depth = [(0, 1)], np.zeros(n_nodes, dtype=np.int64)
+    leaves_seen = 0
+    while stack:
+        nd, dpt = stack.pop()
+        order.append(nd)
+        depth[nd] = dpt
+        for c in child[nd]:
+            if c >= 0:
+                parent_seen[c] += 1
+                stack.append((int(c), dpt + 1))
+            else:
+                leaves_seen += 1
+                assert dpt <= max_depth  # internal nodes on the path, root included
+    assert leaves_seen == n_tris and len(order) == n_nodes
+    assert np.all(parent_seen[1:] == 1) and parent_seen[0] == 0
+    box_lo = np.full((n_nodes, 3), np.inf, dtype=np.float32)
+    box_hi = np.full((n_nodes, 3), -np.inf, dtype=np.float32)
+    for nd in reversed(order):
+        for side in (0, 1):
+            c = child[nd, side]
+            lo = lo_t[~c] if c < 0 else box_lo[c]
+            hi = hi_t[~c] if c < 0 else box_hi[c]
+            # the box stored for this child in the parent
+            sl = np.array([nodes[nd, 0 + 4 * side], nodes[nd, 2 + 4 * side], nodes[nd, 8 + 2 * side]])
+            sh = np.array([nodes[nd, 1 + 4 * side], nodes[nd, 3 + 4 * side], nodes[nd, 9 + 2 * side]])
+            assert np.all(sl <= lo) and np.all(sh >= hi), (nd, side)
+            box_lo[nd] = np.minimum(box_lo[nd], lo)
+            box_hi[nd] = np.maximum(box_hi[nd], hi)
+
+
+@pytest.mark.parametrize("which", ["tiny", "medium"])
+def test_exported_tree_is_a_valid_bvh(which, tiny, medium):
+    w = tiny if which == "tiny" else medium
+    rq = w.rq
+    nodes, tris = rq.rt_scene_export(w.scene)
+    inf = w.scene.info()
+    _check_tree(nodes.cpu().numpy(), tris.cpu().numpy(), inf.n_tris, inf.max_depth, w.s.verts, w.s.tris)
