@@ -163,6 +163,8 @@ rt_status rt_build_wide(rt_scene* sc, const int2* child, const int2* range, cons
                         const float4* node_hi, const float4* leaf_lo, const float4* leaf_hi, float pad,
                         cudaStream_t s);
 rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s);
+rt_status rt_treelet_optimise(int64_t nt, int passes, int2* child, int2* range, int32_t* par_i, int32_t* par_l,
+                              int32_t* order, float4* llo, float4* lhi, float4* nlo, float4* nhi, cudaStream_t s);
 rt_status rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf, const rt_split_params* p);
 void rt_cascade_geometry(const rt_sdf* sdf, int k, float lo[3], float hi[3], float* h, float* ih);
 rt_status rt_launch_cascade_bake(const rt_scene* sc, const rt_sdf* sdf, int k, int32_t method, const void* keep,

@@ -12,6 +12,8 @@
 //      prefix; duplicate codes are ordered by their position
 //   5. bottom-up bounds: every leaf walks to the root, the second thread to
 //      reach a node (atomic counter) merges its two children
+//   5b. treelet restructuring for surface-area cost (rt_treelet.cu), leaves
+//      renumbered depth-first
 //   6. pack 64-byte nodes (child boxes inline), 48-byte triangles in leaf
 //      order, and per-triangle pseudonormals for the distance bake
 //      (Baerentzen & Aanaes, "Signed distance computation using the angle
@@ -31,6 +33,7 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kMaxWalk = 256;  // bound on any leaf-to-root walk (the stack holds 64)
 constexpr float kLargeFrac = 0.25f;  // a triangle wider than this share of the scene is "large"
+constexpr int kTreeletPasses = 3;    // treelet restructuring passes over the Morton hierarchy
 
 __device__ __forceinline__ int f2ord(float f)
 {
@@ -379,7 +382,7 @@ rt_status rt_build_scene(const float* V, int64_t nv, const int32_t* F, int64_t n
     RT_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, keys.as<uint64_t>(), keys2.as<uint64_t>(),
                                                 vals.as<int32_t>(), vals2.as<int32_t>(), (int)nt, 0, 64, s));
     const uint64_t* skeys = keys2.as<uint64_t>();
-    const int32_t* order = vals2.as<int32_t>();
+    int32_t* order = vals2.as<int32_t>();
 
     RT_CUDA_TRY(cudaMemsetAsync(visit.p, 0, (nt > 1 ? nt - 1 : 1) * sizeof(int), s));
     RT_CUDA_TRY(cudaMemsetAsync(depth.p, 0, sizeof(int), s));
@@ -395,6 +398,12 @@ rt_status rt_build_scene(const float* V, int64_t nv, const int32_t* F, int64_t n
                                             par_l.as<int32_t>(), llo.as<float4>(), lhi.as<float4>(),
                                             nlo.as<float4>(), nhi.as<float4>(), visit.as<int>());
     RT_CUDA_TRY(cudaGetLastError());
+    if (nt > 2) {
+        rt_status ts = rt_treelet_optimise(nt, kTreeletPasses, child.as<int2>(), nrange.as<int2>(), par_i.as<int32_t>(),
+                                           par_l.as<int32_t>(), order, llo.as<float4>(), lhi.as<float4>(),
+                                           nlo.as<float4>(), nhi.as<float4>(), s);
+        if (ts != RT_OK) return ts;
+    }
     k_depth<<<grid_for(nt), kBlock, 0, s>>>(par_i.as<int32_t>(), par_l.as<int32_t>(), nt, depth.as<int>());
     RT_CUDA_TRY(cudaGetLastError());
 
