@@ -33,7 +33,10 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kMaxWalk = 256;  // bound on any leaf-to-root walk (the stack holds 64)
 constexpr float kLargeFrac = 0.25f;  // a triangle wider than this share of the scene is "large"
-constexpr int kTreeletPasses = 3;    // treelet restructuring passes over the Morton hierarchy
+#ifndef RT_TREELET_PASSES
+#define RT_TREELET_PASSES 3
+#endif
+constexpr int kTreeletPasses = RT_TREELET_PASSES;  // treelet restructuring passes over the Morton hierarchy
 
 __device__ __forceinline__ int f2ord(float f)
 {
