@@ -401,11 +401,14 @@ rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, c
                                      const float* d_grad_t, float* d_grad_grid, void* stream);
 
 /* Launch tuning of the trace kernels (process-wide; applies to later calls).
- *   kernel        RT_KERNEL_WAVEFRONT (default): persistent stage kernels, one
- *                 per sub-interval kind, with per-lane refill from a global
- *                 queue, so rays that switch tracer mid-query are regrouped
- *                 across the whole batch; RT_KERNEL_SIMPLE: one thread per
- *                 query runs all its sub-intervals.
+ *   kernel        RT_KERNEL_WAVEFRONT: persistent stage kernels, one per
+ *                 sub-interval kind, with per-lane refill from a global queue,
+ *                 so rays that switch tracer mid-query are regrouped across
+ *                 the whole batch; RT_KERNEL_SIMPLE: one thread per query runs
+ *                 all its sub-intervals; RT_KERNEL_AUTO (default): one thread
+ *                 per query for triangles-only calls (mode RT_MODE_BVH, or a
+ *                 split with m_near = +INFINITY), where there is nothing to
+ *                 regroup, the stage kernels otherwise.
  *   block         threads per block (multiple of 32, 32..1024)
  *   blocks_per_sm persistent grid = SMs x this (0: as many as fit)
  *   refill_min    triangle stages: a warp fetches new queries when at least
@@ -432,7 +435,7 @@ typedef struct {
     int32_t bvh_width;
 } rt_tuning;
 
-enum { RT_KERNEL_WAVEFRONT = 0, RT_KERNEL_SIMPLE = 1 };
+enum { RT_KERNEL_WAVEFRONT = 0, RT_KERNEL_SIMPLE = 1, RT_KERNEL_AUTO = 2 };
 enum { RT_LAYOUT_CELLS = 0, RT_LAYOUT_PLAIN = 1, RT_LAYOUT_PAIRS = 2 };
 
 rt_status rt_set_tuning(const rt_tuning* tuning);

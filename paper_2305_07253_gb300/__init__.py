@@ -31,7 +31,7 @@ FLAG_STACK_OVERFLOW, FLAG_STEP_LIMIT, FLAG_ITER_LIMIT = 1, 2, 4
 GRID_F32, GRID_F16 = 0, 1
 BAKE_AUTO, BAKE_BRUTE, BAKE_BVH, BAKE_JFA = 0, 1, 2, 3
 
-KERNEL_WAVEFRONT, KERNEL_SIMPLE = 0, 1
+KERNEL_WAVEFRONT, KERNEL_SIMPLE, KERNEL_AUTO = 0, 1, 2
 LAYOUT_CELLS, LAYOUT_PLAIN, LAYOUT_PAIRS = 0, 1, 2
 
 EXPORTS = ("rt_scene_build", "rt_scene_info_get", "rt_scene_destroy", "rt_sdf_create", "rt_sdf_destroy",

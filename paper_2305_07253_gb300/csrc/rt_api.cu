@@ -14,14 +14,14 @@
 static thread_local char g_err[512] = "";
 
 // process-wide launch tuning (see rt_set_tuning)
-static rt_tuning g_tuning = {RT_KERNEL_WAVEFRONT, 128, 0, 32, RT_LAYOUT_CELLS, 16, 2};
+static rt_tuning g_tuning = {RT_KERNEL_AUTO, 128, 0, 32, RT_LAYOUT_CELLS, 16, 2};
 
 const rt_tuning& rt_current_tuning() { return g_tuning; }
 
 extern "C" rt_status rt_set_tuning(const rt_tuning* t)
 {
     if (!t) return rt_fail(RT_ERR_INVALID_ARG, "tuning is null");
-    if (t->kernel != RT_KERNEL_WAVEFRONT && t->kernel != RT_KERNEL_SIMPLE)
+    if (t->kernel != RT_KERNEL_WAVEFRONT && t->kernel != RT_KERNEL_SIMPLE && t->kernel != RT_KERNEL_AUTO)
         return rt_fail(RT_ERR_INVALID_ARG, "kernel %d", t->kernel);
     if (t->block < 32 || t->block > 1024 || t->block % 32)
         return rt_fail(RT_ERR_INVALID_ARG, "block %d must be a multiple of 32 in [32, 1024]", t->block);

@@ -484,7 +484,12 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
     const rt_tuning& tu = rt_current_tuning();
     TraceArgs a = a0;
     rt_apply_layout(a, tu);
-    if (tu.kernel == RT_KERNEL_WAVEFRONT)
+    // AUTO: a triangles-only call (mode BVH, or a split with m_near = +inf, whose
+    // field sub-interval is empty for every query) has nothing to regroup
+    const bool triangles_only = a.mode == RT_MODE_BVH || ((a.mode == RT_MODE_SPLIT1 || a.mode == RT_MODE_SPLIT2) &&
+                                                          isinf(a.m_near) && a.m_near > 0.f);
+    const bool wavefront = tu.kernel == RT_KERNEL_WAVEFRONT || (tu.kernel == RT_KERNEL_AUTO && !triangles_only);
+    if (wavefront)
         return counted ? run_wavefront<true>(a, tu, s, timing) : run_wavefront<false>(a, tu, s, timing);
     const int64_t blocks = (a.n + tu.block - 1) / tu.block;
     if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "too many rays");
