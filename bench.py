@@ -243,6 +243,8 @@ def run_ours(args):
         if stage == "bvh_near":  # all rays in; hits written; the rest queued
             fwd = n_rays - n_bvh_hits
             return 32 * n_rays + 64 * nodes + 48 * tris + 24 * n_bvh_hits + 8 * fwd
+        if stage == "field_split" and name == "sdf":  # m = 0: no triangle stage, every ray in
+            return 32 * n_rays + step_bytes * steps + 24 * n_rays
         if stage == "field_split":  # queued rays in; every record written here
             fwd = n_rays - n_bvh_hits
             return (8 + 32) * fwd + step_bytes * steps + 24 * fwd

@@ -121,15 +121,12 @@ struct StageArgs {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-// Load a query and the bounds of this stage's sub-interval.  Returns false
-// when the sub-interval is not part of the query (or the query is invalid).
-__device__ __forceinline__ bool stage_segment(const TraceArgs& a, int kind, int64_t q, float3& o, float3& d,
-                                              float& ta, float& tb, bool& invalid)
+// The bounds of this stage's sub-interval of the query (o, d, t_min, t_max).
+// Returns false when the sub-interval is not part of the query (or the query
+// is invalid).
+__device__ __forceinline__ bool segment_bounds(const TraceArgs& a, int kind, float3 o, float3 d, float tmin,
+                                               float tmax, float& ta, float& tb, bool& invalid)
 {
-    const float4 r0 = __ldg(a.rays + 2 * q), r1 = __ldg(a.rays + 2 * q + 1);
-    o = make_float3(r0.x, r0.y, r0.z);
-    d = make_float3(r1.x, r1.y, r1.z);
-    const float tmin = r0.w, tmax = r1.w;
     invalid = !valid_query(o, d, tmin, tmax);
     if (invalid) return false;
     if (kind == ST_BVH_FULL || kind == ST_FIELD_FULL) {
@@ -143,6 +140,16 @@ __device__ __forceinline__ bool stage_segment(const TraceArgs& a, int kind, int6
     ta = s.t1;
     tb = s.t2;
     return s.field;
+}
+
+// Load query q and the bounds of this stage's sub-interval.
+__device__ __forceinline__ bool stage_segment(const TraceArgs& a, int kind, int64_t q, float3& o, float3& d,
+                                              float& ta, float& tb, bool& invalid)
+{
+    const float4 r0 = __ldg(a.rays + 2 * q), r1 = __ldg(a.rays + 2 * q + 1);
+    o = make_float3(r0.x, r0.y, r0.z);
+    d = make_float3(r1.x, r1.y, r1.z);
+    return segment_bounds(a, kind, o, d, r0.w, r1.w, ta, tb, invalid);
 }
 
 // Append the lanes with `fwd` set to the next stage's queue (one atomic per warp).
@@ -391,15 +398,22 @@ int stage_program(const TraceArgs& a, int kinds[3])
     switch (a.mode) {
     case RT_MODE_BVH: kinds[0] = ST_BVH_FULL; return 1;
     case RT_MODE_SDF: kinds[0] = ST_FIELD_FULL; return 1;
-    case RT_MODE_SPLIT1:
-        if (a.any_hit) { kinds[0] = ST_FIELD_SPLIT; kinds[1] = ST_BVH_NEAR; }
-        else { kinds[0] = ST_BVH_NEAR; kinds[1] = ST_FIELD_SPLIT; }
-        return 2;
-    default:
-        if (a.any_hit) { kinds[0] = ST_FIELD_SPLIT; kinds[1] = ST_BVH_NEAR; }
-        else { kinds[0] = ST_BVH_NEAR; kinds[1] = ST_FIELD_SPLIT; }
-        kinds[2] = ST_BVH_FAR;
-        return 3;
+    default: {
+        // a triangle sub-interval whose multiplier is 0 is empty for every query:
+        // its stage would only pass the queries on, so it is not launched (the
+        // neighbouring field stage then takes every query, or writes the final misses)
+        const bool near = a.m_near > 0.f, far = a.mode == RT_MODE_SPLIT2 && a.m_far > 0.f;
+        int n = 0;
+        if (a.any_hit) {
+            kinds[n++] = ST_FIELD_SPLIT;
+            if (near) kinds[n++] = ST_BVH_NEAR;
+        } else {
+            if (near) kinds[n++] = ST_BVH_NEAR;
+            kinds[n++] = ST_FIELD_SPLIT;
+        }
+        if (far) kinds[n++] = ST_BVH_FAR;
+        return n;
+    }
     }
 }
 

@@ -524,19 +524,37 @@ __device__ __forceinline__ void corners(const TraceArgs& a, const Cell& c, float
 
 __device__ __forceinline__ float lerp_rn(float f, float x, float y) { return __fmaf_rn(f, __fsub_rn(y, x), x); }
 
+// trilinear interpolation of the 8 corners (order as in corners()) at the cell fractions f
+__device__ __forceinline__ float interp8(const float f[3], const float v[8])
+{
+    float c00 = lerp_rn(f[0], v[0], v[1]);
+    float c10 = lerp_rn(f[0], v[2], v[3]);
+    float c01 = lerp_rn(f[0], v[4], v[5]);
+    float c11 = lerp_rn(f[0], v[6], v[7]);
+    float c0 = lerp_rn(f[1], c00, c10);
+    float c1 = lerp_rn(f[1], c01, c11);
+    return lerp_rn(f[2], c0, c1);
+}
+
+// the 8 corners of a 16-byte half-precision cell, held as 4 words in v[0..3], widened in place
+__device__ __forceinline__ void widen_f16_cell(float v[8])
+{
+    const uint32_t w[4] = {__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3])};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        __half2 h2 = *reinterpret_cast<const __half2*>(&w[k]);
+        v[2 * k] = __low2float(h2);
+        v[2 * k + 1] = __high2float(h2);
+    }
+}
+
 template <int L>
 __device__ __forceinline__ float trilinear(const TraceArgs& a, float px, float py, float pz)
 {
     Cell c = locate(a, px, py, pz);
     float v[8];
     corners<L>(a, c, v);
-    float c00 = lerp_rn(c.f[0], v[0], v[1]);
-    float c10 = lerp_rn(c.f[0], v[2], v[3]);
-    float c01 = lerp_rn(c.f[0], v[4], v[5]);
-    float c11 = lerp_rn(c.f[0], v[6], v[7]);
-    float c0 = lerp_rn(c.f[1], c00, c10);
-    float c1 = lerp_rn(c.f[1], c01, c11);
-    return lerp_rn(c.f[2], c0, c1);
+    return interp8(c.f, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -555,14 +573,13 @@ __device__ __forceinline__ int casc_level(const TraceArgs& a, float px, float py
     return k;
 }
 
-template <int L>
-__device__ __forceinline__ float casc_trilinear(const TraceArgs& a, int k, float px, float py, float pz)
+// the cell of level k that holds p (its index in the cell copy) and p's fractions in it
+__device__ __forceinline__ int64_t casc_locate(const TraceArgs& a, int k, float px, float py, float pz, float f[3])
 {
     const CascLevel& lv = a.lv[k];
     const float p[3] = {px, py, pz};
     const float top = (float)(a.gn[0] - 1);
     int i0[3];
-    float f[3];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         float u = __fmul_rn(__fsub_rn(p[ax], lv.lo[ax]), lv.ih);
@@ -572,27 +589,26 @@ __device__ __forceinline__ float casc_trilinear(const TraceArgs& a, int k, float
         f[ax] = __fsub_rn(u, (float)ii);
         i0[ax] = ii;
     }
-    const int64_t idx = k * a.level_cells + cell_slot(i0[0], i0[1], i0[2], a.gn[0], a.gn[0]);
+    return k * a.level_cells + cell_slot(i0[0], i0[1], i0[2], a.gn[0], a.gn[0]);
+}
+
+template <int L>
+__device__ __forceinline__ float casc_trilinear(const TraceArgs& a, int k, float px, float py, float pz)
+{
+    float f[3];
+    const int64_t idx = casc_locate(a, k, px, py, pz, f);
     float v[8];
     if (L == GL_CASC_F16) {
         uint4 q = __ldg(reinterpret_cast<const uint4*>(a.cells) + idx);
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            __half2 h2 = *reinterpret_cast<const __half2*>(&w[j]);
-            v[2 * j] = __low2float(h2);
-            v[2 * j + 1] = __high2float(h2);
-        }
+        v[0] = __uint_as_float(q.x);
+        v[1] = __uint_as_float(q.y);
+        v[2] = __uint_as_float(q.z);
+        v[3] = __uint_as_float(q.w);
+        widen_f16_cell(v);
     } else {
         ldg8(reinterpret_cast<const float*>(a.cells) + 8 * idx, v);
     }
-    float c00 = lerp_rn(f[0], v[0], v[1]);
-    float c10 = lerp_rn(f[0], v[2], v[3]);
-    float c01 = lerp_rn(f[0], v[4], v[5]);
-    float c11 = lerp_rn(f[0], v[6], v[7]);
-    float c0 = lerp_rn(f[1], c00, c10);
-    float c1 = lerp_rn(f[1], c01, c11);
-    return lerp_rn(f[2], c0, c1);
+    return interp8(f, v);
 }
 
 // field value and the hit / minimum-step thresholds at p: one grid, or the

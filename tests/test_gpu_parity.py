@@ -410,6 +410,29 @@ def test_timed_variant_reports_each_launch(tiny):
     assert torch.equal(a, c) and [x[0] for x in st] == ["all"]
 
 
+@pytest.mark.parametrize("any_hit", [False, True])
+def test_zero_multipliers_launch_no_triangle_stage(tiny, any_hit):
+    """m = 0 makes a triangle sub-interval empty for every query, so its stage is
+    not launched; the records equal the one-thread-per-query kernel's, which
+    evaluates every sub-interval."""
+    rq = tiny.rq
+    cases = [(dict(mode=rq.MODE_SPLIT1, m_near=0.0), ["field_split"]),
+             (dict(mode=rq.MODE_SPLIT2, m_near=0.0, m_far=2.0), ["field_split", "bvh_far"]),
+             (dict(mode=rq.MODE_SPLIT2, m_near=2.0, m_far=0.0),
+              ["field_split", "bvh_near"] if any_hit else ["bvh_near", "field_split"]),
+             (dict(mode=rq.MODE_SPLIT2, m_near=0.0, m_far=0.0), ["field_split"])]
+    for kw, stages in cases:
+        p = rq.split_params(any_hit=any_hit, **kw)
+        a, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
+        assert [x[0] for x in st] == stages, kw
+        prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
+        try:
+            b = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p)
+        finally:
+            rq.rt_set_tuning(prev)
+        assert torch.equal(a, b), kw
+
+
 def _mixed_batches(w, rq):
     s = w.s
     prim = R.primary_rays(s)
