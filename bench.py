@@ -54,7 +54,7 @@ def parse():
                     help="set up, then run only warmup+steps launches of the --only traces (for ncu); prints timings")
     ap.add_argument("--only", default="all", choices=["all", "combined", "bvh", "sdf"])
     ap.add_argument("--out", default="gpurun_out/ao_images", help="output folder of --workload ao-images")
-    ap.add_argument("--workload", default="frame", choices=["frame", "batching", "fit", "precision", "ao", "cascade", "ao-images", "dfbuild"],
+    ap.add_argument("--workload", default="frame", choices=["frame", "batching", "fit", "precision", "ao", "cascade", "ao-images", "dfbuild", "gather"],
                     help="frame: the 1080p GI headline; batching: 8 frames of mixed primary/shadow/AO/GI "
                          "batches; fit: gradient fit of a noisy 128^3 grid; precision: float16 vs float32 "
                          "512^3 grid on the 8.2 M-triangle scene")
@@ -331,7 +331,8 @@ def run_ours(args):
                      "traffic": traffic, "kernel": kernel_names.get(dom_stage, dom_stage) + ", combined m=2",
                      "algorithmic_bytes_per_launch": ab, "launch_ms": dom_ms, "peak_kind": f"of {peak_kind}",
                      "step": {"algorithmic_bytes": stage_bytes("combined", "all"),
-                              "GBps": stage_bytes("combined", "all") / (ms_mid * 1e-3) / 1e9}},
+                              "GBps": stage_bytes("combined", "all") / (ms_mid * 1e-3) / 1e9},
+                     "random_gather": gather_ceiling(rq, peak)},
         "e2e": {"value": world * n_rays / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(rays.nbytes),
                 "d2h_bytes_per_step": int(n_rays * 24), "ms_per_step": ms_e2e},
         "gpu_launches": K * len(stage_ms["combined"]),
@@ -387,6 +388,40 @@ def cpu_baseline(s, rays, gpu_hits, sample, reps):
           "sample": f"{len(idx)} of {rays.shape[0]} GI rays (evenly spaced), fp64 combined query m={M_MIDDLE}, "
                     f"grid values evaluated before timing, median of {max(1, reps)} passes", "seconds": dt}
     return cb, err
+
+
+def gather_ceiling(rq, peak, K=10, W=2):
+    """Rate of chains of dependent random 32-byte gathers over 2^24 cells (537 MB,
+    beyond the L2), one chain per thread at the field stage's occupancy (12 blocks
+    of 128 per SM), 64 gathers a chain: the access a march step makes, with no
+    locality.  Context for the field stage's fraction of the copy bandwidth."""
+    import torch
+    n_cells, steps = 1 << 24, 64
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks = sms * 12
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    cells = torch.rand(n_cells * 8, device="cuda", generator=g)
+    out = torch.empty(blocks * 128, dtype=torch.float32, device="cuda")
+    ms = _time_ms(lambda: rq.rt_gather_probe(cells, steps, blocks, out), K, W)
+    nbytes = blocks * 128 * steps * 32
+    del cells, out
+    gbps = nbytes / (ms * 1e-3) / 1e9
+    return {"useful_GBps": gbps, "frac": gbps / peak, "bytes_per_launch": nbytes, "launch_ms": ms,
+            "cells": n_cells, "chains": blocks * 128, "gathers_per_chain": steps}
+
+
+def run_gather(args):
+    """Only the gather probe (for a profiler): K timed launches after W."""
+    import torch
+    import paper_2305_07253_gb300 as rq
+    torch.cuda.set_device(0)
+    peak, peak_kind = peaks()
+    r = gather_ceiling(rq, peak, K=args.steps, W=args.warmup)
+    print(json.dumps({"metric": "dependent random 32-byte gathers, 537 MB", "value": r["useful_GBps"], "unit": "GB/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                      "dtype": "f32", "data": "synthetic", "peak_kind": f"of {peak_kind}", **r,
+                      "config": {"workload": "gather-probe-537MB"}}), flush=True)
 
 
 def run_reference(args):
@@ -985,6 +1020,8 @@ def main():
         run_cascade(args)
     elif args.workload == "ao-images":
         run_ao_images(args)
+    elif args.workload == "gather":
+        run_gather(args)
     elif args.workload == "dfbuild":
         run_dfbuild(args)
     else:

@@ -120,6 +120,18 @@ def test_argument_errors_without_a_gpu(rtlib):
     rtlib.rt_sdf_destroy(out)
 
 
+def test_gather_probe_arguments_without_a_gpu(rtlib):
+    rtlib.rt_last_error.restype = ctypes.c_char_p
+    f = rtlib.rt_gather_probe
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    buf, out = ctypes.c_void_p(4096), ctypes.c_void_p(8192)
+    assert f(None, 16, 4, 1, out, None) == 1 and b"null" in rtlib.rt_last_error()
+    assert f(ctypes.c_void_p(4112), 16, 4, 1, out, None) == 1 and b"32-byte" in rtlib.rt_last_error()
+    assert f(buf, 24, 4, 1, out, None) == 1 and b"power of two" in rtlib.rt_last_error()
+    assert f(buf, 16, 0, 1, out, None) == 1 and b"steps" in rtlib.rt_last_error()
+    assert f(buf, 16, 4, 0, out, None) == 1 and b"blocks" in rtlib.rt_last_error()
+
+
 def test_bad_split_params_rejected(rtlib):
     import paper_2305_07253_gb300 as rq
     out = ctypes.c_void_p()
