@@ -10,6 +10,7 @@
 #include <new>
 
 #include "rt_internal.cuh"
+#include "rt_trace_dev.cuh"
 
 static thread_local char g_err[512] = "";
 
@@ -136,8 +137,7 @@ rt_status rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf
             if (!sdf->cells)
                 return rt_fail(RT_ERR_INVALID_ARG, "cascade has no cell copy yet: call rt_sdf_bake or rt_sdf_prepare");
             a.levels = sdf->levels;
-            const int64_t c = sdf->n[0] - 1;
-            a.level_cells = c * c * c;
+            a.level_cells = rtdev::cell_count(sdf->n[0], sdf->n[0], sdf->n[0]);
             for (int k = 0; k < sdf->levels; ++k) {
                 CascLevel& v = a.lv[k];
                 rt_cascade_geometry(sdf, k, v.lo, v.hi, &v.h, &v.ih);

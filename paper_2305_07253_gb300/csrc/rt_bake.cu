@@ -274,7 +274,7 @@ rt_status rt_launch_cascade_cells(const rt_sdf* sdf, int k, cudaStream_t s)
     const int64_t count = (n - 1) * (n - 1) * (n - 1);
     const int64_t esz = sdf->dtype == RT_GRID_F16 ? 2 : 4;
     const void* grid = static_cast<const char*>(sdf->grid) + k * n * n * n * esz;
-    void* cells = static_cast<char*>(sdf->cells) + k * count * 8 * esz;
+    void* cells = static_cast<char*>(sdf->cells) + k * rtdev::cell_count((int)n, (int)n, (int)n) * 8 * esz;
     const int64_t blocks = (count + 255) / 256;
     k_cells<<<(unsigned)blocks, 256, 0, s>>>(grid, sdf->dtype == RT_GRID_F16, (int32_t)n, (int32_t)n, (int32_t)n,
                                              cells);
@@ -286,7 +286,8 @@ rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s)
 {
     if (sdf->levels > 0) {
         const int64_t n = sdf->n[0];
-        const int64_t bytes = sdf->levels * (n - 1) * (n - 1) * (n - 1) * (sdf->dtype == RT_GRID_F16 ? 16 : 32);
+        const int64_t bytes =
+            sdf->levels * rtdev::cell_count((int)n, (int)n, (int)n) * (sdf->dtype == RT_GRID_F16 ? 16 : 32);
         if (!sdf->cells || sdf->cells_bytes != bytes) {
             if (sdf->cells) cudaFree(sdf->cells);
             sdf->cells = nullptr;
@@ -317,7 +318,7 @@ rt_status rt_launch_prepare(rt_sdf* sdf, cudaStream_t s)
         RT_CUDA_TRY(cudaGetLastError());
     }
     const int64_t count = (int64_t)(sdf->n[0] - 1) * (sdf->n[1] - 1) * (sdf->n[2] - 1);
-    const int64_t bytes = count * (sdf->dtype == RT_GRID_F16 ? 16 : 32);
+    const int64_t bytes = rtdev::cell_count(sdf->n[0], sdf->n[1], sdf->n[2]) * (sdf->dtype == RT_GRID_F16 ? 16 : 32);
     if (!sdf->cells || sdf->cells_bytes != bytes) {
         if (sdf->cells) cudaFree(sdf->cells);
         sdf->cells = nullptr;
