@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="set up, then run only warmup+steps launches of the --only traces (for ncu); prints timings")
     ap.add_argument("--only", default="all", choices=["all", "combined", "bvh", "sdf"])
-    ap.add_argument("--out", default="gpurun_out/ao_images", help="output folder of --workload ao-images")
+    ap.add_argument("--out", default="ao_images", help="output folder of --workload ao-images")
     ap.add_argument("--workload", default="frame", choices=["frame", "batching", "fit", "precision", "ao", "cascade", "ao-images", "dfbuild", "gather"],
                     help="frame: the 1080p GI headline; batching: 8 frames of mixed primary/shadow/AO/GI "
                          "batches; fit: gradient fit of a noisy 128^3 grid; precision: float16 vs float32 "
