@@ -77,11 +77,16 @@ def interpolate(grid: torch.Tensor, lo, hi, p: torch.Tensor) -> torch.Tensor:
 
 
 def fit_grid(scene: Scene, sdf: Sdf, ray_batches, steps: int, lr: float, log_every: int = 0,
-             surface_weight: float = 1.0) -> list[FitStep]:
+             surface_weight: float = 1.0, surface: str = "square") -> list[FitStep]:
     """Adam on sdf.grid (a float32 CUDA tensor, updated in place).
 
     ray_batches: callable step -> (rays, t_triangles) with t_triangles the exact
-    triangle hit distances of those rays (inf on a miss)."""
+    triangle hit distances of those rays (inf on a miss).
+    surface: "square" penalises phi(p*)^2; "hinge" penalises max(phi(p*), 0)^2,
+    only the values that let a ray pass the surface (a march registers a hit
+    once phi drops below its small threshold)."""
+    if surface not in ("square", "hinge"):
+        raise ValueError(f"surface must be 'square' or 'hinge', not {surface!r}")
     grid = sdf.grid
     if grid.dtype != torch.float32:
         raise ValueError("fitting needs a float32 grid")
@@ -101,6 +106,8 @@ def fit_grid(scene: Scene, sdf: Sdf, ray_batches, steps: int, lr: float, log_eve
             hit = torch.isfinite(t_ref)
             p_star = rays[hit, 0:3] + t_ref[hit, None] * rays[hit, 4:7]
             phi = interpolate(grid, sdf.lo, sdf.hi, p_star)
+            if surface == "hinge":
+                phi = torch.clamp(phi, min=0.0)
             loss = loss + surface_weight * phi.pow(2).mean()
         loss.backward()
         opt.step()

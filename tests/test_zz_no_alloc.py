@@ -58,6 +58,10 @@ def test_noalloc_matches_allocating_entry_point_on_consecutive_calls(world):
         (R.gi_rays(s, 23456, 42, 0.5 * s.diagonal),
          rq.split_params(mode=rq.MODE_SPLIT2, m_near=2.0, m_far=3.0, any_hit=False)),
         (R.gi_rays(s, 777, 43, s.diagonal), rq.split_params(mode=rq.MODE_BVH, m_near=math.inf)),
+        # zero multipliers: no triangle stage before the field (one launch), or field then far triangles
+        (R.gi_rays(s, 5001, 44, s.diagonal), rq.split_params(mode=rq.MODE_SPLIT1, m_near=0.0)),
+        (R.gi_rays(s, 4099, 45, s.diagonal),
+         rq.split_params(mode=rq.MODE_SPLIT2, m_near=0.0, m_far=2.0, any_hit=True)),
     ]
     for rays, p in calls:
         rd = torch.from_numpy(rays).cuda()
