@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="set up, then run only warmup+steps launches of the --only traces (for ncu); prints timings")
     ap.add_argument("--only", default="all", choices=["all", "combined", "bvh", "sdf"])
-    ap.add_argument("--out", default="ao_images", help="output folder of --workload ao-images")
-    ap.add_argument("--workload", default="frame", choices=["frame", "batching", "fit", "precision", "ao", "cascade", "ao-images", "dfbuild", "gather"],
+    ap.add_argument("--out", default="images", help="output folder of --workload ao-images / gi-images")
+    ap.add_argument("--workload", default="frame", choices=["frame", "batching", "fit", "precision", "ao", "cascade", "ao-images", "gi-images", "dfbuild",
+                             "gather"],
                     help="frame: the 1080p GI headline; batching: 8 frames of mixed primary/shadow/AO/GI "
                          "batches; fit: gradient fit of a noisy 128^3 grid; precision: float16 vs float32 "
                          "512^3 grid on the 8.2 M-triangle scene")
@@ -997,6 +998,192 @@ def run_ao_images(args):
                       "images": sorted(os.listdir(args.out)), "errors": out}), flush=True)
 
 
+def _free_lights(s, count=4, below_ceiling=0.4, clearance=0.3):
+    """Point lights in free space under the ceiling: candidates on a grid, kept
+    when clear of every object's bounding sphere, the `count` nearest to the
+    quarter points of the room taken."""
+    room = np.asarray(s.room, dtype=np.float64)
+    xs = np.linspace(0.1, 0.9, 9)
+    cand = np.array([[x * room[0], room[1] - below_ceiling, z * room[2]] for x in xs for z in xs])
+    ok = np.ones(len(cand), dtype=bool)
+    for ob in s.objects:
+        ok &= np.linalg.norm(cand - np.asarray(ob.center), axis=1) > ob.radius + clearance
+    cand = cand[ok]
+    out = []
+    for qx, qz in ((0.25, 0.25), (0.75, 0.25), (0.25, 0.75), (0.75, 0.75))[:count]:
+        q = np.array([qx * room[0], room[1] - below_ceiling, qz * room[2]])
+        out.append(cand[np.argmin(np.linalg.norm(cand - q, axis=1))])
+    return np.array(out)
+
+
+def _field_normals(levels, y, d):
+    """Unit gradient of a field at points y (m, 3), flipped against the ray
+    directions d: central differences of the trilinear interpolant with half a
+    voxel.  levels: [(grid (n, n, n) x fastest, lo (3), hi (3))], finest first;
+    a point takes the finest level whose box holds it (the coarsest otherwise)."""
+    import torch
+    from paper_2305_07253_gb300 import fit as F
+    k_of = torch.full((y.shape[0],), len(levels) - 1, dtype=torch.long, device=y.device)
+    for k in range(len(levels) - 2, -1, -1):
+        lo = torch.tensor(levels[k][1], dtype=y.dtype, device=y.device)
+        hi = torch.tensor(levels[k][2], dtype=y.dtype, device=y.device)
+        k_of = torch.where(((y >= lo) & (y <= hi)).all(dim=1), torch.full_like(k_of, k), k_of)
+    g = torch.zeros_like(y)
+    for k, (grid, lo, hi) in enumerate(levels):
+        sel = k_of == k
+        if not bool(sel.any()):
+            continue
+        yk = y[sel]
+        h = (torch.tensor(hi, dtype=y.dtype, device=y.device) - torch.tensor(lo, dtype=y.dtype, device=y.device)) \
+            / (grid.shape[0] - 1)
+        gk = torch.empty_like(yk)
+        for a in range(3):
+            e = torch.zeros(3, dtype=y.dtype, device=y.device)
+            e[a] = 0.5 * h[a]
+            gk[:, a] = (F.interpolate(grid, lo, hi, yk + e) - F.interpolate(grid, lo, hi, yk - e)) / (2 * e[a])
+        g[sel] = gk
+    g = g / g.norm(dim=1, keepdim=True).clamp(min=1e-30)
+    return torch.where(((g * d).sum(dim=1) > 0)[:, None], -g, g)
+
+
+def run_gi_images(args):
+    """GI images (the image form of the paper's GI experiment, Section 3 "GI &
+    Shadow Rays"): per pixel the surface point x the camera sees (primary rays,
+    triangles, in every form), direct light from 4 point lights through shadow
+    rays (two splits, any hit), and one bounce through spp cosine GI rays (one
+    split, closest hit, t_max 30 m) whose hit points y are lit through shadow
+    rays too.  Constant albedo 0.7 (the paper's assumption); the normal at a
+    field-resolved y is the gradient of the form's own field.  The GI and shadow
+    queries run as triangles only, combined (m = 2) and field only, on the dense
+    exact grid and on the paper's 5 x 64^3 cascade.  Writes the images and
+    4 x |image - image(triangles only)| error images as PNG to --out, prints the
+    errors (per pixel, on 8 x 8 tile means, and of the direct light alone) and
+    the time of the GI and shadow queries."""
+    import torch
+
+    import paper_2305_07253_gb300 as rq
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    s = S.make_scene("frame")
+    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
+    W, H, spp, albedo, power = 960, 540, 16, 0.7, 25.0
+    bias = 1e-3 * s.diagonal
+    prim_rays = R.primary_rays(s, W, H)
+    hits = rq.hit_fields(rq.rt_trace_bvh(scene, torch.from_numpy(prim_rays).to(dev)))
+    t = hits["t"].cpu().numpy().astype(np.float64)
+    prim = hits["prim"].cpu().numpy()
+    seen = np.isfinite(t)
+    o, d = prim_rays[:, 0:3].astype(np.float64), prim_rays[:, 4:7].astype(np.float64)
+    V, Fi = s.verts.astype(np.float64), s.tris
+    x = o + np.where(seen, t, 0.0)[:, None] * d
+    tri = np.where(seen, prim, 0)
+    nx = np.cross(V[Fi[tri, 1]] - V[Fi[tri, 0]], V[Fi[tri, 2]] - V[Fi[tri, 0]])
+    nx /= np.maximum(np.linalg.norm(nx, axis=1, keepdims=True), 1e-30)
+    nx *= np.where(np.einsum("ij,ij->i", nx, d) > 0, -1.0, 1.0)[:, None]
+    lights = torch.tensor(_free_lights(s), dtype=torch.float64, device=dev)
+    n = W * H
+    xt, nxt = torch.from_numpy(x).to(dev), torch.from_numpy(nx).to(dev)
+    face_n = torch.from_numpy(np.cross(V[Fi[:, 1]] - V[Fi[:, 0]], V[Fi[:, 2]] - V[Fi[:, 0]])).to(dev)
+    face_n = face_n / face_n.norm(dim=1, keepdim=True).clamp(min=1e-30)
+    gi = torch.from_numpy(R.ao_rays(x, nx, np.full(n, spp, dtype=np.int64), 45, 30.0, bias)).to(dev)
+
+    def shadow_rays(p, nn):
+        """p, nn (m, 3) float64 -> rays to every light (m * L, 8) float32, cos terms, 1/d^2."""
+        L = lights.shape[0]
+        org = (p + bias * nn)[:, None, :].expand(-1, L, -1)
+        v = lights[None, :, :] - org
+        dist = v.norm(dim=2)
+        dirn = v / dist[..., None]
+        cos = (dirn * nn[:, None, :]).sum(dim=2).clamp(min=0.0)
+        r = torch.cat([org, torch.zeros_like(dist)[..., None], dirn, (dist - bias).clamp(min=0.0)[..., None]],
+                      dim=2).reshape(-1, 8).float()
+        return r.contiguous(), cos, 1.0 / dist.pow(2)
+
+    def direct(p, nn, prm, sdf):
+        r, cos, inv2 = shadow_rays(p, nn)
+        h = rq.rt_trace_combined(scene, sdf, r, prm)
+        vis = (h[:, 4] == rq.TRACER_MISS).double().reshape(cos.shape)
+        return (power * vis * cos * inv2).sum(dim=1), r
+
+    dense = torch.empty((256, 256, 256), dtype=torch.float32, device=dev)
+    sdf_dense = rq.rt_sdf_create(dense, s.lo, s.hi)
+    rq.rt_sdf_bake(scene, sdf_dense, rq.BAKE_BVH)
+    cg = torch.empty((5, 64, 64, 64), dtype=torch.float32, device=dev)
+    sdf_c = rq.rt_cascade_create(cg, 0.1, np.asarray(s.camera.eye, dtype=np.float32))
+    rq.rt_sdf_bake(scene, sdf_c, rq.BAKE_JFA)
+    lv_dense = [(dense, tuple(s.lo), tuple(s.hi))]
+    lv_c = [(cg[k], *rq.rt_cascade_box(sdf_c, k)) for k in range(5)]
+    gi_p = {"triangles": rq.split_params(mode=rq.MODE_BVH),
+            "combined": rq.split_params(mode=rq.MODE_SPLIT1, m_near=M_MIDDLE),
+            "field": rq.split_params(mode=rq.MODE_SDF)}
+    sh_p = {"triangles": rq.split_params(mode=rq.MODE_BVH, any_hit=True),
+            "combined": rq.split_params(mode=rq.MODE_SPLIT2, m_near=M_MIDDLE, m_far=M_MIDDLE, any_hit=True),
+            "field": rq.split_params(mode=rq.MODE_SDF, any_hit=True)}
+    forms = {"triangles": ("triangles", None, None), "combined_dense": ("combined", sdf_dense, lv_dense),
+             "field_dense": ("field", sdf_dense, lv_dense), "combined_cascade": ("combined", sdf_c, lv_c),
+             "field_cascade": ("field", sdf_c, lv_c)}
+    py, px = np.mgrid[0:H, 0:W]
+    order = R._tile_order(px.ravel(), py.ravel(), W)
+    pix_y, pix_x = py.ravel()[order], px.ravel()[order]
+    os.makedirs(args.out, exist_ok=True)
+    K = max(3, args.steps // 40)
+    out, ref, expo = {}, None, None
+    for name, (kind, sdf, lv) in forms.items():
+        e_x, r_x = direct(xt, nxt, sh_p[kind], sdf)
+        hg = rq.rt_trace_combined(scene, sdf, gi, gi_p[kind])
+        f = rq.hit_fields(hg)
+        tg = f["t"].double()
+        hit = torch.isfinite(tg)
+        y = gi[:, 0:3].double() + torch.where(hit, tg, torch.zeros_like(tg))[:, None] * gi[:, 4:7].double()
+        ny = torch.zeros_like(y)
+        bvh = f["tracer"] == rq.TRACER_BVH
+        if bool(bvh.any()):
+            fn = face_n[f["prim"][bvh].long()]
+            db = gi[bvh, 4:7].double()
+            ny[bvh] = torch.where(((fn * db).sum(dim=1) > 0)[:, None], -fn, fn)
+        fld = f["tracer"] == rq.TRACER_SDF
+        if bool(fld.any()):
+            ny[fld] = _field_normals(lv, y[fld], gi[fld, 4:7].double())
+        e_y, r_y = direct(y, ny, sh_p[kind], sdf)
+        e_y = torch.where(hit, e_y, torch.zeros_like(e_y))
+        e_ind = albedo * e_y.reshape(n, spp).mean(dim=1)
+        rad = (albedo / math.pi) * (e_x + e_ind)
+        rad = rad.cpu().numpy()
+        rad[~seen] = 0.0
+        img = np.zeros((H, W))
+        img[pix_y, pix_x] = rad
+        dimg = np.zeros((H, W))
+        dimg[pix_y, pix_x] = np.where(seen, (albedo / math.pi) * e_x.cpu().numpy(), 0.0)
+        if expo is None:
+            expo = 1.0 / max(float(np.percentile(rad[seen], 90)), 1e-12)
+        tone = 1.0 - np.exp(-expo * img)
+        _write_png(os.path.join(args.out, f"gi_{name}.png"), tone)
+        ms = (_time_ms(lambda: rq.rt_trace_combined(scene, sdf, r_x, sh_p[kind]), K) +
+              _time_ms(lambda: rq.rt_trace_combined(scene, sdf, gi, gi_p[kind]), K) +
+              _time_ms(lambda: rq.rt_trace_combined(scene, sdf, r_y, sh_p[kind]), K))
+        entry = {"query_ms": ms, "rays": int(r_x.shape[0] + gi.shape[0] + r_y.shape[0])}
+        def tiles(a):
+            return a[:H // 8 * 8, :W // 8 * 8].reshape(H // 8, 8, W // 8, 8).mean(axis=(1, 3))
+
+        def rel_err(a, b):
+            m = b > 0
+            r = np.abs(a - b)[m] / b[m]
+            return {"mean_rel": float(r.mean()), "share_off_10pct": float((r > 0.1).mean())}
+        if ref is None:
+            ref, ref_tone, ref_direct = img, tone, dimg
+        else:
+            err = np.abs(tone - ref_tone)
+            _write_png(os.path.join(args.out, f"gi_err_{name}.png"), 4.0 * err)
+            entry.update({"mean_abs_d_tone": float(err.mean()), "pixels": rel_err(img, ref),
+                          "tiles_8x8": rel_err(tiles(img), tiles(ref)), "direct_only": rel_err(dimg, ref_direct)})
+        out[name] = entry
+    print(json.dumps({"metric": "GI images vs triangles only", "config": {"workload": "frame-gi-images", "width": W,
+                                                                         "height": H, "spp": spp, "lights": 4,
+                                                                         "albedo": albedo},
+                      "images": sorted(os.listdir(args.out)), "forms": out}), flush=True)
+
+
 def run_dfbuild(args):
     """The paper's field build (voxelisation, jump flooding, sweeps) of the
     combined-mode cascade, 5 x 64^3 with a 0.1 m finest voxel around the camera
@@ -1033,6 +1220,8 @@ def main():
         run_cascade(args)
     elif args.workload == "ao-images":
         run_ao_images(args)
+    elif args.workload == "gi-images":
+        run_gi_images(args)
     elif args.workload == "gather":
         run_gather(args)
     elif args.workload == "dfbuild":
