@@ -94,6 +94,22 @@ __device__ __forceinline__ BvhRay bvh_ray(float3 o, float3 d)
     return r;
 }
 
+// three-input maximum / minimum (one instruction on sm_100 and later; exact, as a
+// chain of two-input ones is, for the finite slab distances they take)
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Slab tests of both children of one node against [ta, tf]; 64-byte node read
 // as two 32-byte vectors.
 struct NodeHit {
@@ -109,13 +125,13 @@ __device__ __forceinline__ NodeHit visit_node(const BNode* nodes, int node, cons
     float x0 = fmaf(v[0], r.idir.x, -r.ood.x), x1 = fmaf(v[1], r.idir.x, -r.ood.x);
     float y0 = fmaf(v[2], r.idir.y, -r.ood.y), y1 = fmaf(v[3], r.idir.y, -r.ood.y);
     float z0 = fmaf(w[0], r.idir.z, -r.ood.z), z1 = fmaf(w[1], r.idir.z, -r.ood.z);
-    float tn0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), ta));
-    float tf0 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tf));
+    float tn0 = fmaxf(max3f(fminf(x0, x1), fminf(y0, y1), fminf(z0, z1)), ta);
+    float tf0 = fminf(min3f(fmaxf(x0, x1), fmaxf(y0, y1), fmaxf(z0, z1)), tf);
     x0 = fmaf(v[4], r.idir.x, -r.ood.x); x1 = fmaf(v[5], r.idir.x, -r.ood.x);
     y0 = fmaf(v[6], r.idir.y, -r.ood.y); y1 = fmaf(v[7], r.idir.y, -r.ood.y);
     z0 = fmaf(w[2], r.idir.z, -r.ood.z); z1 = fmaf(w[3], r.idir.z, -r.ood.z);
-    float tn1 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), ta));
-    float tf1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tf));
+    float tn1 = fmaxf(max3f(fminf(x0, x1), fminf(y0, y1), fminf(z0, z1)), ta);
+    float tf1 = fminf(min3f(fmaxf(x0, x1), fmaxf(y0, y1), fmaxf(z0, z1)), tf);
     NodeHit h;
     h.h0 = tn0 <= tf0;
     h.h1 = tn1 <= tf1;
@@ -194,10 +210,6 @@ __device__ __forceinline__ bool trav_trip(const TraceArgs& a, const BvhRay& r, T
                                           Hit& best, uint32_t& flags, Counts& cnt, int budget)
 {
     for (int it = 0; it < budget; ++it) {
-        if (++s.guard > (1u << 26)) {  // a tree visit is bounded by 2n-1 nodes; stops only a corrupt structure
-            flags |= RT_FLAG_ITER_LIMIT;
-            return true;
-        }
         if (s.node >= 0) {
             if (COUNT) ++cnt.nodes;
             NodeHit h = visit_node(a.nodes, s.node, r, s.ta, s.tbest);
@@ -220,6 +232,14 @@ __device__ __forceinline__ bool trav_trip(const TraceArgs& a, const BvhRay& r, T
         }
         if (s.sp == 0) return true;
         s.node = stack[--s.sp];
+    }
+    // a tree visit is bounded by 2n-1 nodes: the guard, charged a trip at a time
+    // (checking it every iteration cost 2 % of the triangles-only time), stops
+    // only a corrupt structure
+    s.guard += (uint32_t)budget;
+    if (s.guard >= (1u << 26)) {
+        flags |= RT_FLAG_ITER_LIMIT;
+        return true;
     }
     return false;
 }
@@ -395,7 +415,7 @@ __device__ __forceinline__ bool bvh_segment(const TraceArgs& a, float3 o, float3
     const BvhRay r = bvh_ray(o, d);
     typename TravOf<WIDE>::entry stack[TravOf<WIDE>::depth];
     typename TravOf<WIDE>::state s = tbegin<WIDE>(a, r, ta, tb);
-    while (!ttrip<COUNT, WIDE>(a, r, s, stack, any_hit, best, flags, cnt, 1 << 30)) {
+    while (!ttrip<COUNT, WIDE>(a, r, s, stack, any_hit, best, flags, cnt, 1 << 26)) {
     }
     return s.found;
 }
