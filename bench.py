@@ -457,29 +457,6 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def make_frame_batches(s, frame: int, seed: int = 2305):
-    """One frame of the mixed workload (Section 3's query kinds): primary rays,
-    1-4 AO rays per pixel (t_max 0.5 m, one split), one GI ray per pixel (t_max
-    30 m, one split) and shadow rays to 4 random point lights (two splits, any
-    hit), their count drawn from [0.5 M, 2.07 M]."""
-    from synth import rng as RNG
-    n_px = 1920 * 1080
-    fs = seed * 1000 + frame
-    prim = R.primary_rays(s)
-    p, nn = R.surface_points(s, n_px, fs)
-    bias = 1e-3 * s.diagonal
-    u = RNG.uniform(fs, 901, n_px + 2)
-    per_pt = 1 + (u[:n_px] * 4).astype(np.int64)
-    ao = R.ao_rays(p, nn, per_pt, fs, 0.5, bias)
-    gi = R.ao_rays(p, nn, np.ones(n_px, dtype=np.int64), fs + 7, 30.0, bias)
-    n_sh = int(500_000 + u[n_px] * (n_px - 500_000))
-    lights = 0.5 + RNG.uniform(fs, 902, 12).reshape(4, 3) * (np.array(s.room) - 1.0)
-    sh = R.shadow_rays(p[:n_sh], nn[:n_sh], lights, fs, bias)
-    return [("primary", prim, dict(mode=0)), ("ao", ao, dict(mode=1, m_near=M_MIDDLE)),
-            ("gi", gi, dict(mode=1, m_near=M_MIDDLE)),
-            ("shadow", sh, dict(mode=2, m_near=M_MIDDLE, m_far=M_MIDDLE, any_hit=True))]
-
-
 def run_batching(args):
     import torch
 
@@ -499,7 +476,7 @@ def run_batching(args):
     t0 = time.perf_counter()
     for f in range(args.frames):
         fb = []
-        for name, rays, kw in make_frame_batches(s, f):
+        for name, rays, kw in R.mixed_frame(s, f, M_MIDDLE):
             rd = torch.from_numpy(rays).to(dev)
             fb.append((name, rd, rq.split_params(**kw), torch.empty((rd.shape[0], 6), dtype=torch.int32, device=dev)))
         frames.append(fb)

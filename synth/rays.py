@@ -222,3 +222,26 @@ def free_space_rays(scene: Scene, n: int, seed: int, margin: float, t_max: float
     d = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
     tm = scene.diagonal if t_max is None else t_max
     return _renorm(pack(o, d, 0.0, tm))
+
+
+def mixed_frame(scene: Scene, frame: int, m: float, seed: int = 2305):
+    """One frame of the mixed workload (the query kinds of Section 3): primary rays
+    (triangles only), 1-4 AO rays per pixel (t_max 0.5 m, one split), one GI ray
+    per pixel (t_max 30 m, one split) and shadow rays to 4 random point lights (two
+    splits, any hit), their count drawn from [0.5 M, 2.07 M].  Returns
+    [(name, rays, split parameters as keywords)] with multiplier m."""
+    n_px = 1920 * 1080
+    fs = seed * 1000 + frame
+    prim = primary_rays(scene)
+    p, nn = surface_points(scene, n_px, fs)
+    bias = 1e-3 * scene.diagonal
+    u = rng.uniform(fs, 901, n_px + 2)
+    per_pt = 1 + (u[:n_px] * 4).astype(np.int64)
+    ao = ao_rays(p, nn, per_pt, fs, 0.5, bias)
+    gi = ao_rays(p, nn, np.ones(n_px, dtype=np.int64), fs + 7, 30.0, bias)
+    n_sh = int(500_000 + u[n_px] * (n_px - 500_000))
+    lights = 0.5 + rng.uniform(fs, 902, 12).reshape(4, 3) * (np.array(scene.room) - 1.0)
+    sh = shadow_rays(p[:n_sh], nn[:n_sh], lights, fs, bias)
+    return [("primary", prim, dict(mode=0)), ("ao", ao, dict(mode=1, m_near=m)),
+            ("gi", gi, dict(mode=1, m_near=m)),
+            ("shadow", sh, dict(mode=2, m_near=m, m_far=m, any_hit=True))]

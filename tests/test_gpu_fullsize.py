@@ -63,3 +63,29 @@ def test_fullsize_combined_sampled(frame, m):
     check_sdf_resolved(g, o, sel=same & (o["tracer"] == 2), max_flip_frac=0.005)
     # every ray got a record: no stack overflow anywhere in the full batch
     assert not np.any(g_all["flags"] & rq.FLAG_STACK_OVERFLOW)
+
+
+def test_fullsize_mixed_batches(frame):
+    """One frame of the batching configuration (primary rays, 1-4 AO rays per
+    pixel, one GI ray per pixel, shadow rays to 4 point lights) through
+    rt_trace_batches: the same records as one call per batch, and a seeded
+    sample of every batch agrees with the checker."""
+    rq = frame["rq"]
+    batches = R.mixed_frame(frame["s"], 0, 2.0)
+    dev = [(torch.from_numpy(r).cuda(), rq.split_params(**kw)) for _, r, kw in batches]
+    outs = rq.rt_trace_batches(frame["scene"], frame["sdf"], dev)
+    rng = np.random.default_rng(14)
+    for (name, rays, kw), (rd, p), got in zip(batches, dev, outs):
+        ref = rq.rt_trace_combined(frame["scene"], frame["sdf"], rd, p)
+        if p.any_hit:  # any valid intersection may be reported
+            assert torch.equal(got[:, 4] > 0, ref[:, 4] > 0), name
+        else:
+            assert torch.equal(got, ref), name
+        sel = np.sort(rng.choice(rays.shape[0], 256, replace=False))
+        g = {k: v[sel] for k, v in gpu_hits_to_numpy(got).items()}
+        o = O.trace_combined(frame["bvh"], frame["ogrid"], rays[sel], O.make_params(**kw), precision=32)
+        assert np.mean((g["tracer"] > 0) == (o["tracer"] > 0)) >= 0.99, name
+        same = g["tracer"] == o["tracer"]
+        check_sdf_resolved(g, o, sel=same & (o["tracer"] == 2), max_flip_frac=0.01)
+        if not p.any_hit:
+            check_bvh_resolved(g, o, rays[sel], frame["s"].verts, frame["s"].tris, sel=same & (o["tracer"] == 1))
