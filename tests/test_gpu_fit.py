@@ -43,42 +43,74 @@ def test_fit_lowers_the_disagreement(surface):
         assert after["only_one_hits"] <= before["only_one_hits"]
 
 
+def _analytic_field(s, n):
+    """A signed-distance-like field of the scene on its n^3 vertex lattice, from
+    the object list on the host (spheres |p - c| - r, boxes by the box distance,
+    the room by the distance to the nearest wall): a grid that neither side's
+    bake produced."""
+    lo, hi = np.asarray(s.lo, dtype=np.float64), np.asarray(s.hi, dtype=np.float64)
+    ax = [np.linspace(lo[k], hi[k], n) for k in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    P = np.stack([X, Y, Z], axis=-1).reshape(-1, 3)
+    phi = np.minimum(P - lo, hi - P).min(axis=1)
+    for ob in s.objects:
+        q = P - np.asarray(ob.center)
+        if ob.kind == "sphere":
+            d = np.linalg.norm(q, axis=1) - ob.radius
+        else:
+            a = np.abs(q @ np.asarray(ob.rot)) - 0.5 * np.asarray(ob.extent)
+            d = np.linalg.norm(np.maximum(a, 0.0), axis=1) + np.minimum(a.max(axis=1), 0.0)
+        phi = np.minimum(phi, d)
+    return phi
+
+
 def test_gradient_matches_fp64_central_differences_on_64_voxels():
     """Fit-scene scale (102,532 triangles, 128^3 grid): the autograd gradient of the
-    loss equals the checker's fp64 central differences of its refined roots."""
-    rq, s, scene, sdf, grid, rays, h_min = _noisy_world("fit", 128, 0.5, 20000)
-    rd = torch.from_numpy(rays).cuda()
-    t_ref = rq.hit_fields(rq.rt_trace_bvh(scene, rd))["t"].clone()
-    g = grid.clone().requires_grad_(True)
+    loss equals the checker's fp64 central differences of its refined roots.  The
+    grid (an analytic field plus noise), the target distances (the checker's
+    triangles) and the loss's rays (those both of the checker's tracers hit) all
+    come from the host."""
+    import paper_2305_07253_gb300 as rq
+    s = S.make_scene("fit")
+    n = 128
+    h = np.array(s.room) / (n - 1)
+    h_min = float(h.min())
+    noise = RNG.normal(3, 77, n ** 3) * (0.5 * h_min)
+    vals = (_analytic_field(s, n) + noise).astype(np.float32).astype(np.float64)
+    rays = R.free_space_rays(s, 20000, 3, 2.0 * float(h.max()))
+    t_ref = O.BVH(s.verts, s.tris).trace(rays)["t"].astype(np.float32).astype(np.float64)
+    prm = O.make_params(mode=3)
+    t0, idx, w = O.sdf_root_adjoint(O.Grid(s.lo, s.hi, [n, n, n], values=vals), rays, prm)
+    in_loss = np.isfinite(t0) & np.isfinite(t_ref)
+    N = int(in_loss.sum())
+    assert N > 1000
+
+    # the device: the same loss over the same rays
+    g = torch.from_numpy(vals.astype(np.float32).reshape(n, n, n)).cuda().requires_grad_(True)
     sdf_g = rq.rt_sdf_create(g, s.lo, s.hi)
-    t, _ = rq.SdfHitDistance.apply(g, rd, None, sdf_g, rq.split_params(mode=rq.MODE_SDF))
-    both = torch.isfinite(t) & torch.isfinite(t_ref)
-    N = int(both.sum())
-    loss = torch.where(both, t - t_ref, torch.zeros_like(t)).pow(2).sum() / N
+    t, _ = rq.SdfHitDistance.apply(g, torch.from_numpy(rays).cuda(), None, sdf_g, rq.split_params(mode=rq.MODE_SDF))
+    use = torch.from_numpy(in_loss).cuda() & torch.isfinite(t)
+    tr = torch.from_numpy(np.where(in_loss, t_ref, 0.0).astype(np.float32)).cuda()
+    loss = torch.where(use, t - tr, torch.zeros_like(t)).pow(2).sum() / N
     loss.backward()
     grad = g.grad.detach().cpu().numpy().reshape(-1).astype(np.float64)
+    device_hit = torch.isfinite(t).cpu().numpy()
 
-    vals = grid.detach().cpu().numpy().reshape(-1).astype(np.float64)
-    n = [128, 128, 128]
-    prm = O.make_params(mode=3)
-    t0, idx, w = O.sdf_root_adjoint(O.Grid(s.lo, s.hi, n, values=vals), rays, prm)
-    t_ref_np = t_ref.cpu().numpy().astype(np.float64)
-    both_np = both.cpu().numpy()
     # voxels whose gradient comes from rays well away from tangency
     cand = np.argsort(-np.abs(grad))[:400]
     checked = 0
     for v in cand:
-        sel = np.nonzero(np.any(idx == v, axis=1) & both_np)[0]
-        if sel.size == 0:
-            continue
+        sel = np.nonzero(np.any(idx == v, axis=1) & in_loss)[0]
+        if sel.size == 0 or not device_hit[sel].all():
+            continue  # a ray the device's march missed is not in its loss
         d = 1e-4 * h_min
         vp = vals.copy(); vp[v] += d
         vm = vals.copy(); vm[v] -= d
-        tp, _, _ = O.sdf_root_adjoint(O.Grid(s.lo, s.hi, n, values=vp), rays[sel], prm)
-        tm, _, _ = O.sdf_root_adjoint(O.Grid(s.lo, s.hi, n, values=vm), rays[sel], prm)
+        tp, _, _ = O.sdf_root_adjoint(O.Grid(s.lo, s.hi, [n, n, n], values=vp), rays[sel], prm)
+        tm, _, _ = O.sdf_root_adjoint(O.Grid(s.lo, s.hi, [n, n, n], values=vm), rays[sel], prm)
         if not (np.all(np.isfinite(tp)) and np.all(np.isfinite(tm))):
             continue
-        fd = np.sum((tp - t_ref_np[sel]) ** 2 - (tm - t_ref_np[sel]) ** 2) / (2 * d) / N
+        fd = np.sum((tp - t_ref[sel]) ** 2 - (tm - t_ref[sel]) ** 2) / (2 * d) / N
         assert grad[v] == pytest.approx(fd, rel=1e-2, abs=1e-3 * np.abs(grad).max()), v
         checked += 1
         if checked == 64:

@@ -292,12 +292,12 @@ def noisy(tiny):
     tiny.rq.rt_sdf_prepare(sdf)
     grid = O.Grid(s.lo, s.hi, tiny.n, values=v32.astype(np.float64))
     rays = R.gi_rays(s, 1024, 31, s.diagonal)
-    return gt, sdf, grid, rays
+    return gt, sdf, grid, rays, v32.astype(np.float64)
 
 
 def test_backward_matches_oracle_adjoint(tiny, noisy, tuning):
     rq = tiny.rq
-    gt, sdf, grid, rays = noisy
+    gt, sdf, grid, rays, _ = noisy
     p = rq.split_params(mode=rq.MODE_SDF, refine_root=True)
     rd = _cuda(rays)
     hits = rq.rt_trace_combined(None, sdf, rd, p)
@@ -322,7 +322,7 @@ def test_backward_matches_oracle_adjoint(tiny, noisy, tuning):
 
 def test_autograd_function_matches_central_differences(tiny, noisy):
     rq = tiny.rq
-    gt, sdf, grid, rays = noisy
+    gt, sdf, grid, rays, host_vals = noisy
     p = rq.split_params(mode=rq.MODE_SDF)
     rd = _cuda(rays[:256])
     gparam = gt.clone().requires_grad_(False)
@@ -334,7 +334,7 @@ def test_autograd_function_matches_central_differences(tiny, noisy):
     loss.backward()
     assert x.grad is not None and torch.isfinite(x.grad).all()
     # central differences of the checker's fp64 refined root on the voxels with the largest gradient
-    vals = gparam.detach().cpu().numpy().reshape(-1).astype(np.float64)
+    vals = host_vals.copy()  # the grid's values as made on the host
     grad = x.grad.cpu().numpy().reshape(-1)
     top = np.argsort(-np.abs(grad))[:16]
     t0, _, _ = O.sdf_root_adjoint(O.Grid(sdf.lo, sdf.hi, tiny.n, values=vals), rays[:256], O.make_params(mode=3))
