@@ -21,7 +21,6 @@ using namespace rtdev;
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBatchTrip = 8;   // traversal iterations between refill checks
 constexpr int kBatchSteps = 4;  // march steps between refill checks
 
 enum Seg { SEG_NONE = 0, SEG_B_FULL, SEG_F_FULL, SEG_B_NEAR, SEG_F_SPLIT, SEG_B_FAR };
@@ -48,6 +47,7 @@ struct Pipe {
     unsigned* out_count;
     unsigned* fetch;
     int32_t refill_min;
+    int32_t trip;             // traversal iterations between refill checks (trip_budget)
 };
 
 __device__ __forceinline__ unsigned lane() { return threadIdx.x & 31u; }
@@ -179,7 +179,7 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
                 }
             }
         } else if (live) {
-            if (ttrip<COUNT, WIDE>(a, r, s, stack, any_hit, best, flags, cnt, kBatchTrip)) {
+            if (ttrip<COUNT, WIDE>(a, r, s, stack, any_hit, best, flags, cnt, pp.trip)) {
                 live = false;
                 done = true;
                 found = s.found;
@@ -417,6 +417,7 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
         pp.out_count = k + 1 < kLaunches ? &ctr[8 + k] : nullptr;
         pp.fetch = &ctr[k];
         pp.refill_min = k == 1 ? tu.refill_min_field : tu.refill_min;
+        pp.trip = trip_budget(pp.refill_min);
         if (k == 1 && need_grid) {
             switch (grid_layout_of(a)) {
 #define RT_BATCH_FIELD(LL)                                                                            \

@@ -21,10 +21,6 @@ using namespace rtdev;
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-#ifndef RT_TRIP_BUDGET
-#define RT_TRIP_BUDGET 8
-#endif
-constexpr int kTripBudget = RT_TRIP_BUDGET;  // traversal iterations between two refill checks
 #ifndef RT_FIELD_BUDGET
 #define RT_FIELD_BUDGET 4
 #endif
@@ -117,6 +113,7 @@ struct StageArgs {
     unsigned* out_count;
     unsigned* fetch;           // work counter of this stage
     int32_t refill_min;
+    int32_t trip;              // traversal iterations between refill checks (trip_budget)
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -224,7 +221,7 @@ __global__ void k_stage_bvh(const TraceArgs a, const StageArgs st)
                 final_miss = invalid;
             }
         } else if (live) {
-            if (ttrip<COUNT, WIDE>(a, r, s, stack, any_hit, best, flags, cnt, kTripBudget)) {
+            if (ttrip<COUNT, WIDE>(a, r, s, stack, any_hit, best, flags, cnt, st.trip)) {
                 done = true;
                 found = s.found;
                 live = false;
@@ -459,6 +456,7 @@ rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s,
         sa.out_count = k + 1 < n_st ? &ctr[3 + (k & 1)] : nullptr;
         sa.fetch = &ctr[k];
         sa.refill_min = (kinds[k] == ST_FIELD_FULL || kinds[k] == ST_FIELD_SPLIT) ? tu.refill_min_field : tu.refill_min;
+        sa.trip = trip_budget(sa.refill_min);
         if (timing) {
             e = cudaEventRecord(timing->events[k], s);
             if (e != cudaSuccess) { rs = rt_cuda_fail(e, "cudaEventRecord"); break; }
@@ -638,6 +636,7 @@ extern "C" rt_status rt_trace_combined_noalloc(const rt_scene* sc, const rt_sdf*
         sa.out_count = k + 1 < n_st ? &ctr[3 + (k & 1)] : nullptr;
         sa.fetch = &ctr[k];
         sa.refill_min = (kinds[k] == ST_FIELD_FULL || kinds[k] == ST_FIELD_SPLIT) ? tu.refill_min_field : tu.refill_min;
+        sa.trip = trip_budget(sa.refill_min);
         st = launch_stage<false>(a, sa, tu, dev->sms, s);
         if (st != RT_OK) return st;
     }

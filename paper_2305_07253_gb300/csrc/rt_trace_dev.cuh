@@ -178,6 +178,14 @@ __device__ __forceinline__ bool test_triangle(const float4* tris, int tri, const
     return false;
 }
 
+// Traversal iterations a lane runs between two refill checks of its warp.  With
+// warp-wide refills (refill_min 32) a warp takes new queries only once every
+// lane is idle, so checks in between are pure overhead: the trip runs until the
+// lane's segment ends (up to 256 iterations).  Measured on the 1080p GI
+// workload, near-triangle stage: 0.256 ms with 8, 0.232 ms with 32 to 4096.
+// With partial refills the check comes every 8 iterations.
+__host__ __device__ __forceinline__ int trip_budget(int refill_min) { return refill_min >= 32 ? 256 : 8; }
+
 // Resumable traversal state of one segment.
 struct Trav {
     int node;
