@@ -413,7 +413,9 @@ rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, c
  *   blocks_per_sm persistent grid = SMs x this (0: as many as fit)
  *   refill_min    triangle stages: a warp fetches new queries when at least
  *                 this many lanes are idle (1..32), or when all are (32 keeps
- *                 the rays of a warp together, which suits coherent rays)
+ *                 the rays of a warp together, which suits coherent rays; a
+ *                 lane then runs its segment to the end between two checks,
+ *                 otherwise it checks every 8 traversal iterations)
  *   refill_min_field  the same for the distance-field stages, whose queries
  *                 end after very different step counts
  *   bvh_width     2 (default): the binary tree (64-byte nodes); 8: the 8-wide
