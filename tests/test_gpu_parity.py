@@ -570,3 +570,30 @@ def test_exported_tree_is_a_valid_bvh(which, tiny, medium):
     nodes, tris = rq.rt_scene_export(w.scene)
     inf = w.scene.info()
     _check_tree(nodes.cpu().numpy(), tris.cpu().numpy(), inf.n_tris, inf.max_depth, w.s.verts, w.s.tris)
+
+
+@pytest.mark.parametrize("bvh_width", [2, 8])
+def test_no_ray_leaks_through_shared_edges_or_vertices(bvh_width):
+    """Watertightness on the device: 100,000-odd rays from inside a closed
+    icosphere, each aimed exactly at one of its vertices or edge midpoints, all
+    hit (closest and any hit), as the checker's fp64 test does."""
+    import paper_2305_07253_gb300 as rq
+    V, F = S.icosphere(3)
+    V = (V * 2.0).astype(np.float32)
+    E = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]])
+    targets = np.concatenate([V, 0.5 * (V[E[:, 0]] + V[E[:, 1]])]).astype(np.float64)
+    reps = 100_000 // targets.shape[0] + 1
+    tg = np.repeat(targets, reps, axis=0)
+    origins = np.random.default_rng(21).uniform(-0.5, 0.5, size=tg.shape)
+    d = tg - origins
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = np.concatenate([origins, np.zeros((len(d), 1)), d, np.full((len(d), 1), 1e30)], axis=1).astype(np.float32)
+    assert rays.shape[0] >= 100_000
+    scene = rq.rt_scene_build(_cuda(V), _cuda(F.astype(np.int32)))
+    prev = rq.rt_set_tuning(bvh_width=bvh_width)
+    try:
+        for any_hit in (False, True):
+            g = gpu_hits_to_numpy(rq.rt_trace_bvh(scene, _cuda(rays), any_hit=any_hit))
+            assert np.all(g["tracer"] == rq.TRACER_BVH), int(np.sum(g["tracer"] != rq.TRACER_BVH))
+    finally:
+        rq.rt_set_tuning(prev)
