@@ -4,14 +4,18 @@
 // runs the distance-field sub-interval first.
 //
 // Two implementations with identical results:
-//   * wavefront (default): one persistent kernel per sub-interval kind
-//     (triangles near, field, triangles far).  Each lane holds one query and
-//     takes a new one from a global counter as soon as its own is finished
-//     (per-lane refill), so no lane idles while the slowest query of its warp
-//     finishes.  Queries that miss a sub-interval are appended to the queue of
-//     the next kind: rays that switch tracer mid-query are regrouped across
-//     the whole batch instead of diverging inside a warp.
+//   * wavefront (stage kernels): one persistent kernel per sub-interval kind
+//     (triangles near, field, triangles far); a kind no query of the call has
+//     is not launched.  Each lane holds one query and takes a new one from a
+//     global counter once enough lanes of its warp are idle (per-lane refill:
+//     all 32 for triangles, which keeps coherent rays together, 16 for the
+//     field, whose marches end after very different step counts).  Queries
+//     that miss a sub-interval are appended to the queue of the next kind:
+//     rays that switch tracer mid-query are regrouped across the whole batch
+//     instead of diverging inside a warp.
 //   * simple: one thread per query runs all of its sub-intervals.
+// The default (RT_KERNEL_AUTO) takes the simple kernel for triangles-only
+// calls, where there is nothing to regroup, and the stage kernels otherwise.
 #include <mutex>
 
 #include "rt_trace_dev.cuh"
