@@ -305,7 +305,9 @@ def rt_sdf_sites(scene: Scene, sdf: Sdf, stage: int = 3, out: torch.Tensor | Non
 
 
 def rt_sdf_bake(scene: Scene, sdf: Sdf, method: int = BAKE_AUTO, stream=None) -> None:
-    """Exact signed-distance bake into the grid of `sdf` (also refreshes its cell copy)."""
+    """Fill the grid of `sdf` (a dense grid or a cascade): the exact signed distance
+    (BAKE_AUTO, BAKE_BVH, BAKE_BRUTE) or the paper's build, voxelisation + jump
+    flooding + sweeps (BAKE_JFA).  Also refreshes its cell copy."""
     _check(lib().rt_sdf_bake(scene.handle, sdf.handle, int(method), _stream(stream)))
 
 
