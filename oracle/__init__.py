@@ -22,7 +22,7 @@ _lock = threading.Lock()
 _lib = None
 
 HIT_DTYPE = np.dtype([("t", "f8"), ("u", "f8"), ("v", "f8"), ("prim", "i4"), ("tracer", "i4"),
-                      ("flags", "u4"), ("steps", "i4")])
+                      ("flags", "u4"), ("steps", "i4"), ("margin", "f8")])
 FLAG_STEP_LIMIT = 2
 
 
@@ -68,6 +68,8 @@ def lib():
             L.or_grid_new.restype = P
             L.or_grid_free.argtypes = [P]
             L.or_grid_values.argtypes = [P, P, i64, i32, P]
+            L.or_grid_export.argtypes = [P, P, P]
+            L.or_tri_check.argtypes = [P, P, i64, P, P, i64, i32, P]
             L.or_trace_sdf.argtypes = [P, P, i64, P, i32, i32, P]
             L.or_trace_combined.argtypes = [P, P, P, i64, P, i32, i32, P]
             L.or_grid_sample.argtypes = [P, P, i64, P, P]
@@ -115,6 +117,24 @@ def watertight(o, d, a, b, c):
     args = [_f64(x) for x in (o, d, a, b, c)]
     hit = lib().or_watertight(*[_ptr(x) for x in args], _ptr(out))
     return bool(hit), out
+
+
+def tri_check(verts, tris, rays, prims, nthreads: int | None = None) -> np.ndarray:
+    """fp64 watertight test of each ray against the one triangle prims[i]:
+    a record array with hit (bool), t, u, v and ndotd = |n . d| (n the unit
+    normal).  A prim outside the mesh gives hit = False."""
+    V = _f64(verts)
+    F = np.ascontiguousarray(tris, dtype=np.int32)
+    R = _rays(rays)
+    pr = np.ascontiguousarray(prims, dtype=np.int32).reshape(-1)
+    assert pr.size == R.shape[0]
+    out = np.zeros((R.shape[0], 5))
+    lib().or_tri_check(_ptr(V), _ptr(F), F.shape[0], _ptr(R), _ptr(pr), R.shape[0], nthreads or default_threads(),
+                       _ptr(out))
+    rec = np.zeros(R.shape[0], dtype=[("hit", "?"), ("t", "f8"), ("u", "f8"), ("v", "f8"), ("ndotd", "f8")])
+    rec["hit"] = out[:, 0] != 0
+    rec["t"], rec["u"], rec["v"], rec["ndotd"] = out[:, 1], out[:, 2], out[:, 3], out[:, 4]
+    return rec
 
 
 def trace_brute(verts, tris, rays, nthreads: int | None = None) -> np.ndarray:
@@ -212,6 +232,15 @@ class Grid:
         out = np.zeros(idx.size)
         lib().or_grid_values(self.h, _ptr(idx), idx.size, nthreads or default_threads(), _ptr(out))
         return out
+
+    def export(self):
+        """(values fp64, known bool) of every sample, x fastest; a grid computed
+        on first use knows the samples evaluated so far (others read 0)."""
+        count = int(np.prod(self.n.astype(np.int64)))
+        vals = np.zeros(count)
+        known = np.zeros(count, dtype=np.uint8)
+        lib().or_grid_export(self.h, _ptr(vals), _ptr(known))
+        return vals, known.astype(bool)
 
     def sample(self, P):
         P = _f64(P).reshape(-1, 3)

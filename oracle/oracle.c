@@ -110,6 +110,7 @@ static void hit_miss(or_hit* h)
     h->tracer = 0;
     h->flags = 0;
     h->steps = 0;
+    h->margin = INFINITY;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -165,6 +166,61 @@ int or_watertight(const double o[3], const double d[3], const double a[3], const
     wt_ray w;
     wt_setup(d, &w);
     return wt_test(o, &w, a, b, c, &out[0], &out[1], &out[2]);
+}
+
+typedef struct {
+    const double* V;
+    const int32_t* F;
+    int64_t nt;
+    const float* rays;
+    const int32_t* prim;
+    double* out;
+} tc_ctx;
+
+static void tc_range(void* vctx, int64_t s, int64_t e)
+{
+    tc_ctx* c = (tc_ctx*)vctx;
+    for (int64_t i = s; i < e; ++i) {
+        double* r = c->out + 5 * i;
+        r[0] = 0; r[1] = INFINITY; r[2] = r[3] = r[4] = 0;
+        int32_t k = c->prim[i];
+        if (k < 0 || k >= c->nt) continue;
+        double o[3], d[3], ta, tb;
+        ray_load(c->rays + 8 * i, o, d, &ta, &tb);
+        const int32_t* f = c->F + 3 * (int64_t)k;
+        const double *a = c->V + 3 * (int64_t)f[0], *b = c->V + 3 * (int64_t)f[1], *cc = c->V + 3 * (int64_t)f[2];
+        wt_ray w;
+        wt_setup(d, &w);
+        double t, u, v;
+        double e1[3], e2[3], n[3];
+        sub3(b, a, e1); sub3(cc, a, e2); cross3(e1, e2, n);
+        if (wt_test(o, &w, a, b, cc, &t, &u, &v)) {
+            r[0] = 1; r[1] = t; r[2] = u; r[3] = v;
+        } else {
+            /* a miss: where the ray's line meets the triangle's plane, in the
+             * same barycentric weights (Cramer's rule on o + t d = a + u e1 + v e2),
+             * so that the caller sees how far outside an edge it passes */
+            double pv[3], tv[3], qv[3];
+            cross3(d, e2, pv);
+            double det = dot3(e1, pv);
+            if (det != 0) {
+                sub3(o, a, tv);
+                cross3(tv, e1, qv);
+                r[2] = dot3(tv, pv) / det;
+                r[3] = dot3(d, qv) / det;
+                r[1] = dot3(e2, qv) / det;
+            }
+        }
+        double len = sqrt(dot3(n, n));
+        r[4] = len > 0 ? fabs(dot3(n, d)) / len : 0;
+    }
+}
+
+void or_tri_check(const double* V, const int32_t* F, int64_t nt, const float* rays, const int32_t* prim,
+                  int64_t nr, int32_t nthreads, double* out)
+{
+    tc_ctx c = {V, F, nt, rays, prim, out};
+    parallel_for(nr, nthreads, 256, tc_range, &c);
 }
 
 /* Accept a candidate into the running closest hit: t in [ta, tb], then the
@@ -769,6 +825,19 @@ void or_grid_free(or_grid* g)
     free(g);
 }
 
+void or_grid_export(const or_grid* g, double* values, uint8_t* known)
+{
+    for (int64_t i = 0; i < g->count; ++i) {
+        int k = g->known ? __atomic_load_n(&g->known[i], __ATOMIC_ACQUIRE) != 0 : 1;
+        if (values) values[i] = k ? g->val[i] : 0.0;
+        if (known) known[i] = (uint8_t)k;
+    }
+}
+
+/* a sample as the single-precision march reads it: the fp64 value rounded
+ * once to float (IEEE round to nearest even) */
+static float fetch_f(const or_grid* g, int64_t i) { return (float)grid_get(g, i); }
+
 typedef struct {
     or_grid* g;
     const int64_t* idx;
@@ -842,7 +911,7 @@ int32_t or_cascade_level_grid(const or_cascade* c, int32_t k, int64_t ilo[3], do
 }
 
 /* the two precisions of the distance-field segment */
-#define GRID_FETCH(g, i) ((REAL)grid_get((g), (i)))
+#define GRID_FETCH(g, i) grid_get((g), (i))
 #define REAL double
 #define SFX(x) x##_d
 #define FMA fma
@@ -866,6 +935,8 @@ int32_t or_cascade_level_grid(const or_cascade* c, int32_t k, int64_t ilo[3], do
 #undef GHI
 #undef GIH
 #undef GH
+#undef GRID_FETCH
+#define GRID_FETCH(g, i) fetch_f((g), (i))
 #define REAL float
 #define SFX(x) x##_f
 #define FMA fmaf

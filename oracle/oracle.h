@@ -33,6 +33,9 @@ typedef struct {
     int32_t tracer;    /* 0 miss, 1 triangle (BVH) segment, 2 distance-field segment */
     uint32_t flags;    /* OR_FLAG_* */
     int32_t steps;     /* distance-field march steps taken by this query */
+    double margin;     /* smallest |phi - eps_hit| over the query's march steps
+                          (+inf without a step): how near the hit test of any
+                          step came to the other outcome */
 } or_hit;
 
 #define OR_FLAG_STEP_LIMIT 2u
@@ -56,6 +59,14 @@ typedef struct or_cascade or_cascade;
  * Returns 1 when the ray's line meets the triangle; out = {t, u, v}. */
 int or_watertight(const double o[3], const double d[3], const double a[3], const double b[3],
                   const double c[3], double out[3]);
+
+/* fp64 watertight test of ray i against triangle prim[i] alone (prim < 0 or
+ * >= nt: no test).  out: 5 doubles per ray: hit (1 or 0), t, u, v, and
+ * |n . d| with n the unit normal of the triangle.  On a miss t, u, v locate
+ * where the ray's line meets the triangle's plane (u or v or 1-u-v < 0 there;
+ * all 0 and t = +inf when the line is parallel to the plane). */
+void or_tri_check(const double* V, const int32_t* F, int64_t nt, const float* rays, const int32_t* prim,
+                  int64_t nr, int32_t nthreads, double* out);
 
 /* Closest hit by definition: every triangle tested, t in [t_min, t_max]. */
 void or_trace_brute(const double* V, const int32_t* F, int64_t nt, const float* rays, int64_t nr,
@@ -85,6 +96,10 @@ or_grid* or_grid_new_lattice(const int64_t ilo[3], double h, const int32_t n[3],
                              const or_bvh* src);
 void or_grid_free(or_grid* g);
 void or_grid_values(or_grid* g, const int64_t* idx, int64_t count, int32_t nthreads, double* out);
+/* Every sample value (fp64) and whether it is known: all samples of a dense
+ * grid, the samples evaluated so far of one computed on first use.  Unknown
+ * samples are written as 0.  Either output may be NULL. */
+void or_grid_export(const or_grid* g, double* values, uint8_t* known);
 
 /* Queries.  precision 64: everything in double; precision 32: the distance-field
  * segment, the split and the trilinear sample in IEEE single precision (the

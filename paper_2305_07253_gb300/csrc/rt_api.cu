@@ -473,15 +473,19 @@ static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ra
     if (st != RT_OK) return st;
     if (p->mode != RT_MODE_SDF && !sc) return rt_fail(RT_ERR_INVALID_ARG, "mode %d needs a scene", p->mode);
     if (p->mode != RT_MODE_BVH && !sdf) return rt_fail(RT_ERR_INVALID_ARG, "mode %d needs a grid", p->mode);
-    if (sc) {
-        st = device_matches(sc->device);
-        if (st != RT_OK) return st;
-    }
     if (counters && ((uintptr_t)counters & 7u)) return rt_fail(RT_ERR_INVALID_ARG, "counters misaligned");
     if (n == 0) return RT_OK;
     TraceArgs a;
     st = rt_fill_trace_args(a, p->mode == RT_MODE_SDF ? nullptr : sc, p->mode == RT_MODE_BVH ? nullptr : sdf, p);
     if (st != RT_OK) return st;
+    if (sc && p->mode != RT_MODE_SDF) {
+        st = device_matches(sc->device);
+        if (st != RT_OK) return st;
+    }
+    if (sdf && p->mode != RT_MODE_BVH) {
+        st = device_matches(sdf->device);
+        if (st != RT_OK) return st;
+    }
     a.rays = reinterpret_cast<const float4*>(rays);
     a.hits = hits;
     a.n = n;

@@ -383,7 +383,8 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
     if (total == 0) return RT_OK;
     int cur = -1;
     RT_CUDA_TRY(cudaGetDevice(&cur));
-    if (sc && sc->device != cur) return rt_fail(RT_ERR_INVALID_ARG, "scene belongs to another device");
+    if (need_scene && sc->device != cur) return rt_fail(RT_ERR_INVALID_ARG, "scene belongs to another device");
+    if (need_grid && sdf->device != cur) return rt_fail(RT_ERR_INVALID_ARG, "grid belongs to another device");
     BatchDevice* dev = nullptr;
     rt_status st = batch_device(dev);
     if (st != RT_OK) return st;

@@ -610,8 +610,10 @@ extern "C" rt_status rt_trace_combined_noalloc(const rt_scene* sc, const rt_sdf*
     if (((uintptr_t)hits & 7u) != 0) return rt_fail(RT_ERR_INVALID_ARG, "hit buffer not 8-byte aligned");
     int cur = -1;
     RT_CUDA_TRY(cudaGetDevice(&cur));
-    if (sc && sc->device != cur) return rt_fail(RT_ERR_INVALID_ARG, "scene belongs to device %d, current is %d",
-                                                sc->device, cur);
+    if (sc && p->mode != RT_MODE_SDF && sc->device != cur)
+        return rt_fail(RT_ERR_INVALID_ARG, "scene belongs to device %d, current is %d", sc->device, cur);
+    if (sdf && p->mode != RT_MODE_BVH && sdf->device != cur)
+        return rt_fail(RT_ERR_INVALID_ARG, "grid belongs to device %d, current is %d", sdf->device, cur);
     NoAllocDevice* dev = nullptr;
     rt_status st = noalloc_setup(dev);
     if (st != RT_OK) return st;

@@ -18,12 +18,22 @@ import pytest
 import oracle as O
 from synth import rays as R
 from synth import scene as S
-from tests.parity import check_bvh_resolved, check_sdf_resolved, gpu_hits_to_numpy
+from tests.parity import compare, ends_from_split_points, gpu_hits_to_numpy, tri_spans
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 N, L, H0 = 16, 4, 0.0625
+
+
+def _eps_top(h0, levels):
+    """The largest float hit threshold of a cascade (its coarsest level's)."""
+    return np.float32(0.01) * np.float32(np.float32(h0) * 2.0 ** (levels - 1))
+
+
+def _cmp(g, o, t12, rays, s, mode, any_hit=False, eps=None):
+    return compare(g, o, rays, s.verts, s.tris, any_hit=any_hit, ends=ends_from_split_points(rays, t12),
+                   spans=tri_spans(mode), eps_hit=eps if eps is not None else _eps_top(H0, L))
 
 
 def _cuda(x):
@@ -101,9 +111,8 @@ def test_cascade_field_trace_matches_float_march(cw, tuning):
     g = gpu_hits_to_numpy(rq.rt_trace_sdf(cw.sdf, cw.rays_d, rq.split_params(mode=rq.MODE_SDF)))
     o = O.trace_combined(None, cw.cas32, cw.rays, O.make_params(mode=3), precision=32)
     assert np.array_equal(g["tracer"], o["tracer"])
-    summ = check_sdf_resolved(g, o)
-    assert summ["exact"] >= 0.999, summ
-    assert np.array_equal(g["flags"] & 2, o["flags"] & 2)
+    rep = compare(g, o, cw.rays, cw.s.verts, cw.s.tris, eps_hit=_eps_top(H0, L), min_equal=1.0)
+    assert rep["sdf_bit_equal"] == 1.0, rep
 
 
 @pytest.mark.parametrize("m", [1.0, 2.0, 4.0])
@@ -111,13 +120,11 @@ def test_cascade_combined_one_split(cw, m, tuning):
     rq = cw.rq
     p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
     g = gpu_hits_to_numpy(rq.rt_trace_combined(cw.scene, cw.sdf, cw.rays_d, p))
-    o = O.trace_combined(cw.bvh, cw.cas32, cw.rays, O.make_params(mode=1, m_near=m), precision=32)
-    same = g["tracer"] == o["tracer"]
-    assert same.mean() >= 0.9999
+    o, t12 = O.trace_combined(cw.bvh, cw.cas32, cw.rays, O.make_params(mode=1, m_near=m), precision=32,
+                              split_points=True)
     assert np.any(o["tracer"] == 1) and np.any(o["tracer"] == 2)
-    check_bvh_resolved(g, o, cw.rays, cw.s.verts, cw.s.tris, sel=(o["tracer"] == 1) | (g["tracer"] == 1))
-    summ = check_sdf_resolved(g, o, sel=same & (o["tracer"] == 2))
-    assert summ["exact"] >= 0.999, summ
+    rep = _cmp(g, o, t12, cw.rays, cw.s, 1)
+    assert rep["sdf_bit_equal"] == 1.0, rep
 
 
 @pytest.mark.parametrize("any_hit", [True, False])
@@ -126,13 +133,10 @@ def test_cascade_two_split_shadow(cw, any_hit, tuning):
     rays = _shadow_rays(cw.s, 3000, 8)
     p = rq.split_params(mode=rq.MODE_SPLIT2, any_hit=any_hit, m_near=2.0, m_far=2.0)
     g = gpu_hits_to_numpy(rq.rt_trace_combined(cw.scene, cw.sdf, _cuda(rays), p))
-    o = O.trace_combined(cw.bvh, cw.cas32, rays, O.make_params(mode=2, any_hit=any_hit, m_near=2.0, m_far=2.0),
-                         precision=32)
-    assert np.mean((g["tracer"] > 0) == (o["tracer"] > 0)) >= 0.999
-    same = g["tracer"] == o["tracer"]
-    check_sdf_resolved(g, o, sel=same & (o["tracer"] == 2))
-    if not any_hit:
-        check_bvh_resolved(g, o, rays, cw.s.verts, cw.s.tris, sel=(o["tracer"] == 1) & same)
+    o, t12 = O.trace_combined(cw.bvh, cw.cas32, rays, O.make_params(mode=2, any_hit=any_hit, m_near=2.0, m_far=2.0),
+                              precision=32, split_points=True)
+    rep = _cmp(g, o, t12, rays, cw.s, 2, any_hit=any_hit)
+    assert rep["sdf_bit_equal"] == 1.0, rep
 
 
 def test_cascade_endpoint_identities(cw, tuning):
@@ -163,11 +167,10 @@ def test_cascade_f16_matches_float_march_on_rounded_values(cw, tuning):
     for mode, m in ((rq.MODE_SDF, 0.0), (rq.MODE_SPLIT1, 2.0)):
         p = rq.split_params(mode=mode, m_near=m)
         g = gpu_hits_to_numpy(rq.rt_trace_combined(cw.scene, sdf16, cw.rays_d, p))
-        o = O.trace_combined(cw.bvh, cas, cw.rays, O.make_params(mode=mode, m_near=m), precision=32)
-        same = g["tracer"] == o["tracer"]
-        assert same.mean() >= 0.9999
-        summ = check_sdf_resolved(g, o, sel=same & (o["tracer"] == 2))
-        assert summ["exact"] >= 0.999
+        o, t12 = O.trace_combined(cw.bvh, cas, cw.rays, O.make_params(mode=mode, m_near=m), precision=32,
+                                  split_points=True)
+        rep = _cmp(g, o, t12, cw.rays, cw.s, mode)
+        assert rep["sdf_bit_equal"] == 1.0, rep
 
 
 @pytest.mark.parametrize("method", ["brute", "bvh"])
@@ -178,11 +181,13 @@ def test_cascade_bake_matches_exact_distance(cw, method):
     rq.rt_sdf_bake(cw.scene, sdf, rq.BAKE_BRUTE if method == "brute" else rq.BAKE_BVH)
     got = g.cpu().numpy().astype(np.float64)
     assert np.max(np.abs(got - cw.vals64)) < 2e-6
-    # the bake also built the cell copy: tracing it equals tracing the checker's values
+    # the bake also built the cell copy: tracing it equals tracing a fresh
+    # cascade of the same values prepared explicitly
     p = rq.split_params(mode=rq.MODE_SDF)
-    gh = gpu_hits_to_numpy(rq.rt_trace_sdf(sdf, cw.rays_d, p))
-    o = O.trace_combined(None, cw.cas32, cw.rays, O.make_params(mode=3), precision=32)
-    assert np.mean(gh["tracer"] == o["tracer"]) >= 0.999
+    g2 = g.clone()
+    sdf2 = rq.rt_cascade_create(g2, H0, cw.center)
+    rq.rt_sdf_prepare(sdf2)
+    assert torch.equal(rq.rt_trace_sdf(sdf, cw.rays_d, p), rq.rt_trace_sdf(sdf2, cw.rays_d, p))
 
 
 def test_cascade_level_geometry_matches_checker(cw):
@@ -258,9 +263,11 @@ def test_cascade_backward_is_refused(cw):
 
 
 # --------------------------------------------------------------------------
-# full size: the paper's cascades on the frame scene, 1080p GI rays in one call
+# full size: the paper's cascades on the frame scene, 1080p GI rays in one call,
+# every query; both sides read the checker's fp64 bake of every level sample
+# rounded to float32
 # --------------------------------------------------------------------------
-N_SAMPLE = 1024
+FRAME_CASCADES = (("combined", 64, 0.1), ("field_only", 128, 0.05))
 
 
 @pytest.fixture(scope="module")
@@ -271,44 +278,41 @@ def frame_cascade():
     center = np.asarray(s.camera.eye, dtype=np.float32)
     bvh = O.BVH(s.verts, s.tris)
     out = dict(rq=rq, s=s, scene=scene, bvh=bvh, center=center)
-    for name, n, h0 in (("combined", 64, 0.1), ("field_only", 128, 0.05)):
-        g = torch.empty((5, n, n, n), dtype=torch.float32, device="cuda")
+    for name, n, h0 in FRAME_CASCADES:
+        h0f = float(np.float32(h0))
+        vals64 = _level_values(bvh, center.astype(np.float64), h0f, n, 5)
+        v32 = vals64.astype(np.float32)
+        g = _cuda(v32)
         sdf = rq.rt_cascade_create(g, h0, center)
-        rq.rt_sdf_bake(scene, sdf, rq.BAKE_BVH)
-        cas = O.Cascade(center.astype(np.float64), float(np.float32(h0)), n, 5, src=bvh)
-        out[name] = (g, sdf, cas)
+        rq.rt_sdf_prepare(sdf)
+        cas = O.Cascade(center.astype(np.float64), h0f, n, 5, values=v32.astype(np.float64))
+        out[name] = (g, sdf, cas, vals64, h0f)
     rays = R.gi_rays(s, 1920 * 1080, 7, 30.0)
     out["rays"] = rays
     out["rays_d"] = torch.from_numpy(rays).cuda()
-    out["sample"] = np.sort(np.random.default_rng(11).choice(rays.shape[0], N_SAMPLE, replace=False))
     return out
 
 
-def test_fullsize_cascade_bake_sampled(frame_cascade):
-    rng = np.random.default_rng(12)
-    for name in ("combined", "field_only"):
-        g, _, cas = frame_cascade[name]
-        n = g.shape[1]
-        for k in range(5):
-            idx = rng.choice(n ** 3, 512, replace=False)
-            got = g[k].reshape(-1)[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
-            ref = cas.values(k, idx)
-            assert np.max(np.abs(got - ref)) < 1e-4, (name, k)
+def test_fullsize_cascade_device_bake_every_sample(frame_cascade):
+    rq = frame_cascade["rq"]
+    for name, n, h0 in FRAME_CASCADES:
+        _, _, _, vals64, _ = frame_cascade[name]
+        g = torch.empty((5, n, n, n), dtype=torch.float32, device="cuda")
+        rq.rt_sdf_bake(frame_cascade["scene"], rq.rt_cascade_create(g, h0, frame_cascade["center"]), rq.BAKE_BVH)
+        got = g.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(got - vals64)) < 1e-4, name
 
 
 @pytest.mark.parametrize("name,m", [("combined", 2.0), ("combined", 0.0), ("field_only", 0.0)])
-def test_fullsize_cascade_sampled(frame_cascade, name, m):
+def test_fullsize_cascade_every_ray(frame_cascade, name, m):
     rq = frame_cascade["rq"]
-    _, sdf, cas = frame_cascade[name]
+    _, sdf, cas, _, h0 = frame_cascade[name]
     p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
-    g_all = gpu_hits_to_numpy(rq.rt_trace_combined(frame_cascade["scene"], sdf, frame_cascade["rays_d"], p))
-    sel = frame_cascade["sample"]
-    g = {k: v[sel] for k, v in g_all.items()}
-    rays = frame_cascade["rays"][sel]
-    o = O.trace_combined(frame_cascade["bvh"], cas, rays, O.make_params(mode=1, m_near=m), precision=32)
-    same = g["tracer"] == o["tracer"]
-    # the two bakes differ by float rounding, so a march may end one step apart on a few rays
-    assert same.mean() >= 0.995
-    check_bvh_resolved(g, o, rays, frame_cascade["s"].verts, frame_cascade["s"].tris, sel=same & (o["tracer"] == 1))
-    check_sdf_resolved(g, o, sel=same & (o["tracer"] == 2), max_flip_frac=0.005)
-    assert not np.any(g_all["flags"] & rq.FLAG_STACK_OVERFLOW)
+    g = gpu_hits_to_numpy(rq.rt_trace_combined(frame_cascade["scene"], sdf, frame_cascade["rays_d"], p))
+    assert not np.any(g["flags"] & (rq.FLAG_STACK_OVERFLOW | rq.FLAG_ITER_LIMIT))
+    rays = frame_cascade["rays"]
+    o, t12 = O.trace_combined(frame_cascade["bvh"], cas, rays, O.make_params(mode=1, m_near=m), precision=32,
+                              split_points=True)
+    rep = _cmp(g, o, t12, rays, frame_cascade["s"], 1, eps=_eps_top(h0, 5))
+    print(f"{name} m={m}: {rep}")
+    assert rep["sdf_bit_equal"] == 1.0, rep

@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 from synth import rays as R
 from synth import scene as S
-from tests.parity import check_bvh_resolved, check_sdf_resolved, gpu_hits_to_numpy
+from tests.parity import compare, gpu_hits_to_numpy, segment_ends, tri_spans
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -21,6 +21,18 @@ pytestmark = pytest.mark.gpu
 
 def _cuda(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _eps_hit(w):
+    s = w.s
+    hmin = np.min((np.float32(s.hi) - np.float32(s.lo)) / np.float32(w.n[0] - 1))
+    return np.float32(0.01) * np.float32(hmin)
+
+
+def _cmp(w, g, o, rays, mode, m_near=2.0, m_far=2.0, any_hit=False, **kw):
+    h = float(np.max((w.s.hi - w.s.lo) / (w.n[0] - 1)))
+    return compare(g, o, rays, w.s.verts, w.s.tris, any_hit=any_hit, ends=segment_ends(rays, mode, m_near, m_far, h),
+                   spans=tri_spans(mode), eps_hit=_eps_hit(w), **kw)
 
 
 class World:
@@ -98,19 +110,9 @@ def test_scene_build_info(tiny, medium):
 def test_bvh_parity(which, any_hit, tiny, medium, tuning):
     w = tiny if which == "tiny" else medium
     g = gpu_hits_to_numpy(w.rq.rt_trace_bvh(w.scene, w.rays_d, any_hit=any_hit))
-    o = w.bvh.trace(w.rays)
-    if not any_hit:
-        check_bvh_resolved(g, o, w.rays, w.s.verts, w.s.tris)
-    else:
-        # any hit: same hit/miss; the reported hit is a real intersection in the interval
-        assert np.mean((g["tracer"] == 1) == (o["tracer"] == 1)) >= 0.9999
-        idx = np.nonzero(g["tracer"] == 1)[0][::7]
-        for i in idx:
-            f = w.s.tris[g["prim"][i]]
-            V = w.s.verts.astype(np.float64)
-            hit, (t, u, v) = O.watertight(w.rays[i, :3], w.rays[i, 4:7], V[f[0]], V[f[1]], V[f[2]])
-            assert hit and w.rays[i, 3] - 1e-5 <= t <= w.rays[i, 7] * (1 + 1e-5)
-            assert abs(t - g["t"][i]) <= 1e-4 * max(1, t)
+    o = w.bvh.trace(w.rays, any_hit=any_hit)
+    # any hit: every reported hit is checked as a real fp64 intersection in [t_min, t_max]
+    compare(g, o, w.rays, w.s.verts, w.s.tris, any_hit=any_hit)
 
 
 def test_bake_parity_tiny(tiny):
@@ -155,10 +157,9 @@ def test_sdf_trace_matches_float_march(tiny, tuning):
     p = rq.split_params(mode=rq.MODE_SDF)
     g = gpu_hits_to_numpy(rq.rt_trace_sdf(tiny.sdf, tiny.rays_d, p))
     o = O.trace_sdf(tiny.grid32, tiny.rays, O.make_params(mode=3), precision=32)
-    summ = check_sdf_resolved(g, o)
     assert np.array_equal(g["tracer"], o["tracer"])
-    assert summ["exact"] >= 0.999, summ
-    assert np.array_equal(g["flags"] & 2, o["flags"] & 2)
+    rep = _cmp(tiny, g, o, tiny.rays, 3, min_equal=1.0)
+    assert rep["sdf_bit_equal"] == 1.0, rep
 
 
 @pytest.mark.parametrize("m", [0.0, 1.0, 2.0, 4.0, math.inf])
@@ -167,10 +168,8 @@ def test_combined_one_split(tiny, m, tuning):
     p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
     g = gpu_hits_to_numpy(rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p))
     o = O.trace_combined(tiny.bvh, tiny.grid32, tiny.rays, O.make_params(mode=1, m_near=m), precision=32)
-    same = g["tracer"] == o["tracer"]
-    assert same.mean() >= 0.9999
-    check_bvh_resolved(g, o, tiny.rays, tiny.s.verts, tiny.s.tris, sel=(o["tracer"] == 1) | (g["tracer"] == 1))
-    check_sdf_resolved(g, o, sel=same)
+    rep = _cmp(tiny, g, o, tiny.rays, 1, m_near=m)
+    assert rep["sdf_bit_equal"] == 1.0, rep
 
 
 def test_endpoint_identities(tiny, tuning):
@@ -211,11 +210,8 @@ def test_combined_two_split_shadow(tiny, any_hit, tuning):
     g = gpu_hits_to_numpy(rq.rt_trace_combined(tiny.scene, tiny.sdf, _cuda(rays), p))
     o = O.trace_combined(tiny.bvh, tiny.grid32, rays, O.make_params(mode=2, any_hit=any_hit, m_near=2.0, m_far=2.0),
                          precision=32)
-    assert np.mean((g["tracer"] > 0) == (o["tracer"] > 0)) >= 0.999
-    same = g["tracer"] == o["tracer"]
-    check_sdf_resolved(g, o, sel=same & (o["tracer"] == 2))
-    if not any_hit:
-        check_bvh_resolved(g, o, rays, tiny.s.verts, tiny.s.tris, sel=(o["tracer"] == 1) & same)
+    rep = _cmp(tiny, g, o, rays, 2, any_hit=any_hit)
+    assert rep["sdf_bit_equal"] == 1.0, rep
 
 
 def test_fp16_grid_matches_float_march_on_rounded_values(tiny, tuning):
@@ -230,10 +226,8 @@ def test_fp16_grid_matches_float_march_on_rounded_values(tiny, tuning):
         p = rq.split_params(mode=mode, m_near=m)
         g = gpu_hits_to_numpy(rq.rt_trace_combined(tiny.scene, sdf16, tiny.rays_d, p))
         o = O.trace_combined(tiny.bvh, grid, tiny.rays, O.make_params(mode=mode, m_near=m), precision=32)
-        same = g["tracer"] == o["tracer"]
-        assert same.mean() >= 0.9999
-        summ = check_sdf_resolved(g, o, sel=same)
-        assert summ["exact"] >= 0.999
+        rep = _cmp(tiny, g, o, tiny.rays, mode, m_near=m)
+        assert rep["sdf_bit_equal"] == 1.0, rep
 
 
 def test_edge_cases(tiny, tuning):
@@ -347,7 +341,7 @@ def test_autograd_function_matches_central_differences(tiny, noisy):
         tm, _, _ = O.sdf_root_adjoint(O.Grid(sdf.lo, sdf.hi, tiny.n, values=vm), rays[:256], O.make_params(mode=3))
         m = fin & np.isfinite(tp) & np.isfinite(tm) & ok.cpu().numpy()
         fd = np.sum((tp[m] ** 2 - tm[m] ** 2)) / (2 * d)
-        assert grad[vi] == pytest.approx(fd, rel=2e-2, abs=1e-3 * np.abs(grad).max())
+        assert grad[vi] == pytest.approx(fd, rel=1e-2, abs=1e-3 * np.abs(grad).max())
 
 
 def test_tunings_give_identical_hits(tiny, medium):

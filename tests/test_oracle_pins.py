@@ -343,6 +343,99 @@ def test_march_on_plane_matches_geometric_series():
     assert checked > 50
 
 
+def test_march_margin_on_plane_is_the_closest_gap_of_the_series():
+    """The decision margin is min_j |phi_j - eps| over the march's steps; on a
+    plane phi_j = phi_0 q^j (closed form), ending at the first phi_k < eps."""
+    lo, hi, n = [0.0, 0.0, 0.0], [8.0, 8.0, 8.0], [17, 17, 17]
+    n_hat = np.array([-0.3, 0.8, 0.2])
+    n_hat /= np.linalg.norm(n_hat)
+    c0 = float(np.dot(n_hat, [4, 1, 4]))
+    g = O.Grid(lo, hi, n, values=_affine_grid(lo, hi, n, n_hat, -c0))
+    rng = np.random.default_rng(21)
+    eps_vox = 0.01
+    eps = eps_vox * 0.5
+    checked = 0
+    for _ in range(600):
+        o = rng.uniform([1, 4, 1], [7, 7.5, 7])
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        if np.dot(n_hat, d) > -0.3:
+            continue
+        ray = np.array([[*o, 0.0, *d, 100.0]], dtype=np.float32)
+        o32, d32 = ray[0, 0:3].astype(np.float64), ray[0, 4:7].astype(np.float64)
+        t_ref, steps = _plane_case(n_hat, c0, o32, d32, eps)
+        if np.any(o32 + t_ref * d32 < 0) or np.any(o32 + t_ref * d32 > 8):
+            continue
+        phi0 = float(np.dot(n_hat, o32) - c0)
+        q = 1.0 + float(np.dot(n_hat, d32))
+        want = min(abs(phi0 * q ** j - eps) for j in range(steps))
+        prm = O.make_params(mode=3, max_steps=1000, hit_eps_vox=eps_vox, min_step_vox=eps_vox)
+        h = O.trace_sdf(g, ray, prm, precision=64)[0]
+        assert h["margin"] == pytest.approx(want, rel=1e-9, abs=1e-12)
+        checked += 1
+    assert checked > 50
+    # a query that never marches has no margin
+    miss = np.array([[-5, -5, -5, 0.0, -1, 0, 0, 1.0]], dtype=np.float32)
+    assert np.isinf(O.trace_sdf(g, miss, O.make_params(mode=3), precision=64)[0]["margin"])
+
+
+def test_tri_check_closed_form():
+    """Ray aimed at the point of barycentric weights (u, v) of a triangle from
+    distance dist, at a chosen angle to its normal: hit exactly when the point
+    is inside, t = dist, the same (u, v) inside or out, |n . d| = cos(angle)."""
+    rng = np.random.default_rng(22)
+    V = rng.normal(size=(60, 3))
+    F = np.arange(60, dtype=np.int32).reshape(20, 3)
+    rays, prims, want = [], [], []
+    for k in range(20):
+        a, b, c = V[F[k]]
+        nrm = np.cross(b - a, c - a)
+        nrm /= np.linalg.norm(nrm)
+        tang = np.cross(nrm, b - a)
+        tang /= np.linalg.norm(tang)
+        for u, v in ((0.2, 0.3), (0.6, 0.35), (-0.25, 0.5), (0.7, 0.6), (0.5, -1e-3)):
+            p = (1 - u - v) * a + u * b + v * c
+            ang = rng.uniform(0.1, 1.2)
+            d = -(np.cos(ang) * nrm + np.sin(ang) * tang) * rng.choice([-1, 1])
+            dist = rng.uniform(0.5, 3.0)
+            o = p - dist * d
+            rays.append([*o, 0.0, *d, 100.0])
+            prims.append(k)
+            want.append((u >= 0 and v >= 0 and u + v <= 1, dist, u, v, np.cos(ang)))
+    rays = np.array(rays, dtype=np.float64)
+    # the float32 ray the checker sees
+    r32 = rays.astype(np.float32)
+    got = O.tri_check(V, F, r32, np.array(prims))
+    for i, (inside, dist, u, v, cs) in enumerate(want):
+        assert got["hit"][i] == inside, i
+        # the float32 rounding of o and d moves the point by ~1e-7 relative
+        assert got["t"][i] == pytest.approx(dist, rel=1e-5, abs=1e-5)
+        assert got["u"][i] == pytest.approx(u, abs=1e-4) and got["v"][i] == pytest.approx(v, abs=1e-4)
+        assert got["ndotd"][i] == pytest.approx(cs, abs=1e-5)
+    # no triangle: no test
+    none = O.tri_check(V, F, r32[:2], np.array([-1, 20]))
+    assert not none["hit"].any() and np.isinf(none["t"]).all()
+
+
+def test_grid_export_knows_exactly_what_was_evaluated():
+    s = S.make_scene("tiny")
+    bvh = O.BVH(s.verts, s.tris)
+    n = [9, 7, 8]
+    g = O.Grid(s.lo, s.hi, n, src=bvh)
+    vals, known = g.export()
+    assert not known.any() and not vals.any()
+    idx = np.array([0, 5, 17, 100, 503])
+    got = g.values(idx)
+    vals, known = g.export()
+    assert np.array_equal(np.nonzero(known)[0], idx)
+    np.testing.assert_array_equal(vals[idx], got)
+    np.testing.assert_allclose(got, O.sdf_points_brute(s.verts, s.tris, O.grid_points(s.lo, s.hi, n)[idx]),
+                               rtol=0, atol=1e-12)
+    dense = O.Grid(s.lo, s.hi, n, values=np.arange(9 * 7 * 8, dtype=np.float64))
+    vals, known = dense.export()
+    assert known.all() and np.array_equal(vals, np.arange(9 * 7 * 8))
+
+
 def test_march_start_inside_hits_at_t_min_and_step_limit_flags():
     lo, hi, n = [0.0, 0.0, 0.0], [4.0, 4.0, 4.0], [9, 9, 9]
     g = O.Grid(lo, hi, n, values=_affine_grid(lo, hi, n, [1, 0, 0], -1.0))  # phi = x - 1
