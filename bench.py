@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations (batching, precision, fit) and the AO / GI tables")
     ap.add_argument("--cpu-sample", type=int, default=1920 * 1080)
     ap.add_argument("--cpu-reps", type=int, default=3)
     ap.add_argument("--profile", action="store_true",
@@ -69,6 +71,33 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+# ---- seeded inputs of the extra measurements, made in spawned worker processes
+def _gen_mixed_frame(f):
+    return [(name, rays, kw) for name, rays, kw in R.mixed_frame(S.make_scene("frame"), f, M_MIDDLE)]
+
+
+def _gen_fit_rays(n_pool, n_eval):
+    s = S.make_scene("fit")
+    margin = 2.0 * float((np.array(s.room) / (s.spec.grid_n - 1)).max())
+    return R.free_space_rays(s, n_pool, 7, margin), R.free_space_rays(s, n_eval, 8, margin)
+
+
+def _gen_precision_rays():
+    return R.gi_rays(S.make_scene("precision"), 1920 * 1080, 7, 30.0)
+
+
+def input_pool(jobs):
+    """Start the input generators `jobs` = {name: (fn, args)} in a spawn pool;
+    returns {name: future}."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    ex = cf.ProcessPoolExecutor(max_workers=min(len(jobs), max(1, (os.cpu_count() or 2) - 1)),
+                                mp_context=mp.get_context("spawn"))
+    futs = {name: ex.submit(fn, *a) for name, (fn, a) in jobs.items()}
+    ex.shutdown(wait=False)
+    return futs
 
 
 def make_workload():
@@ -190,6 +219,13 @@ def run_ours(args):
     from paper_2305_07253_gb300 import replicas
 
     rank, world, local = replicas.env()
+    extras = rank == 0 and world == 1 and not args.no_extras and not args.profile
+    futs = None
+    if extras:  # the extra measurements' inputs are made on the host while the GPU works
+        jobs = {f"frame{f}": (_gen_mixed_frame, (f,)) for f in range(args.frames)}
+        jobs["fit"] = (_gen_fit_rays, (2 * 1024 * 1024, 1024 * 1024))
+        jobs["precision"] = (_gen_precision_rays, ())
+        futs = input_pool(jobs)
     torch.cuda.set_device(local)
     dist = None
     if replicas.init("nccl"):
@@ -342,8 +378,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_mid, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded procedural scene and rays)",
-        "config": config_dict(s, n_rays, {"parallelism": f"rays replicated per GPU x{world}" if world > 1 else "1 GPU",
-                                          "tuning": rq.rt_get_tuning().as_dict()}),
+        "config": config_dict(s, n_rays),
+        "parallelism": f"rays replicated per GPU x{world}" if world > 1 else "1 GPU",
+        "tuning": rq.rt_get_tuning().as_dict(),
         "bvh_only": {"value": world * n_rays / (ms_bvh * 1e-3), "ms_per_step": ms_bvh},
         "sdf_only": {"value": world * n_rays / (ms_sdf * 1e-3), "ms_per_step": ms_sdf},
         "combined": {"value": value, "ms_per_step": ms_mid, "m": M_MIDDLE},
@@ -367,7 +404,29 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"], line["hit_t_err_vs_fp64"] = cpu_baseline(s, rays, hits_mid, args.cpu_sample,
-                                                                       args.cpu_reps)
+                                                                       args.cpu_reps, grid.cpu().numpy())
+    if extras:
+        # the other configurations and the paper's experiments, untimed for the headline
+        del rays_h, hits_h
+        t0 = time.perf_counter()
+        pool, evals = futs["fit"].result()
+        line["fit"] = extra_fit(rq, pool, evals, steps=args.fit_steps)
+        del pool, evals
+        line["ao"] = extra_ao(rq, scene, s, sdf256=sdf)
+        line["gi_images"] = extra_gi_images(rq, scene, s, W=480, H=270, spp=8)
+        frames = [futs[f"frame{f}"].result() for f in range(args.frames)]
+        line["batching"] = extra_batching(rq, scene, sdf, grid, frames)
+        del frames
+        torch.cuda.empty_cache()
+        line["precision"] = extra_precision(rq, futs["precision"].result())
+        line["extras_seconds"] = time.perf_counter() - t0
+        line["success_conditions"] = {
+            "ordering_bvh_gt_combined_ge_sdf": line["ordering_ok"],
+            "combined_step_ge_0.4_of_roofline": bool(line["roofline"]["step"]["GBps"] / peak >= 0.4),
+            "persistent_graph_beats_per_batch": line["batching"]["persistent_graph_beats_per_batch"],
+            "f16_beats_per_batch": line["batching"]["f16_beats_per_batch"],
+            "f16_beats_f32_at_m2_precision_scene": line["precision"]["f16_beats_f32_at_m2"],
+            "fit_lowers_disagreement": line["fit"]["fit_lowers_disagreement"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -387,7 +446,75 @@ def _oracle_world(s, sample_rays):
     return O, bvh, grid, prm
 
 
-def cpu_baseline(s, rays, gpu_hits, sample, reps):
+def fp64_gap(O, s, rays, g, o, grid_dev_h, ogrid):
+    """Classify every difference between the device records (float path, the
+    device's own bake) and the fp64 checker's (fp64 march on its fp64 bake):
+      equal            same tracer; triangle: same primitive, t within 1e-4
+                       relative; field: t within 1e-3 relative
+      triangle_boundary a triangle hit on either side that lies within 1e-5 of
+                       an edge, grazes (|n.d| < 1e-3), ties (fp64 t of the
+                       device's triangle within 1e-4 of the checker's) or sits
+                       within 1e-4 of a sub-interval end, in fp64
+      field_near_tie   no triangle hit involved, and the fp64 march came within
+                       one hit threshold eps_hit of the other outcome at some
+                       step (its decision margin <= eps_hit): a near-tangent pass
+                       by a surface, where the float march's samples (a few ulp
+                       apart along the ray after many steps) may decide that
+                       step the other way, a step-count flip
+      field_other      anything else."""
+    n = rays.shape[0]
+    gt = g[:, 0].view(np.float32).astype(np.float64)
+    gp = g[:, 1].astype(np.int64)
+    gtr = g[:, 4].astype(np.int64)
+    otr, ot, op = o["tracer"].astype(np.int64), o["t"], o["prim"].astype(np.int64)
+    with np.errstate(invalid="ignore"):
+        rel = np.abs(gt - ot) / np.maximum(1.0, np.abs(ot))
+    equal = ((gtr == 0) & (otr == 0)) | ((gtr == 1) & (otr == 1) & (gp == op) & (rel <= 1e-4)) | \
+        ((gtr == 2) & (otr == 2) & (rel <= 1e-3))
+    vals, known = ogrid.export()
+    bake_err = float(np.max(np.abs(grid_dev_h.reshape(-1)[known].astype(np.float64) - vals[known])))
+    hmax = float(np.max((s.hi - s.lo) / (s.spec.grid_n - 1)))
+    delta = 0.01 * float(np.min((s.hi - s.lo) / (s.spec.grid_n - 1)))  # eps_hit of the default step rule
+    r64 = rays.astype(np.float64)
+    t1 = np.minimum(np.maximum(r64[:, 3] + M_MIDDLE * hmax, r64[:, 3]), r64[:, 7])
+    ends = np.stack([r64[:, 3], t1, r64[:, 7]], axis=1)
+
+    def boundary(idx, prims, t_ref=None):
+        if idx.size == 0:
+            return np.zeros(0, dtype=bool)
+        c = O.tri_check(s.verts, s.tris, rays[idx], prims)
+        edge = np.abs(np.minimum(np.minimum(c["u"], c["v"]), 1 - c["u"] - c["v"])) < 1e-5
+        graze = c["ndotd"] < 1e-3
+        with np.errstate(invalid="ignore"):
+            near_end = np.any(np.abs(ends[idx] - c["t"][:, None]) <= 1e-4 * np.maximum(1, np.abs(ends[idx])), axis=1)
+            tie = np.zeros(idx.size, dtype=bool) if t_ref is None else \
+                np.abs(c["t"] - t_ref) <= 1e-4 * np.maximum(1, np.abs(t_ref))
+        return edge | graze | near_end | tie
+
+    bad = ~equal
+    tri_bound = np.zeros(n, dtype=bool)
+    gi = np.nonzero(bad & (gtr == 1))[0]
+    tri_bound[gi] |= boundary(gi, gp[gi], np.where(otr[gi] == 1, ot[gi], np.nan))
+    oi = np.nonzero(bad & (otr == 1))[0]
+    tri_bound[oi] |= boundary(oi, op[oi])
+    fld = bad & ~((gtr == 1) | (otr == 1))
+    near = fld & (o["margin"] <= delta)
+    other = bad & ~tri_bound & ~near
+    both_f = (gtr == 2) & (otr == 2)
+    hist_edges = (1e-7, 1e-6, 1e-5, 1e-4, delta, 1e-3)
+    hist = {f"<= {x:.3g} m": int((fld & (o["margin"] <= x)).sum()) for x in hist_edges}
+    return {"rays": int(n), "equal": int(equal.sum()), "triangle_boundary": int((bad & tri_bound).sum()),
+            "field_near_tie": int(near.sum()), "field_near_tie_tracer_flips": int((near & (gtr != otr)).sum()),
+            "field_near_tie_both_field": int((near & both_f).sum()), "field_other": int(other.sum()),
+            "eps_hit_m": delta, "device_bake_max_err_m": bake_err, "checker_samples_compared": int(known.sum()),
+            "field_differences_by_fp64_margin": hist,
+            "both_field_rel_dt_max": {"equal": float(rel[both_f & equal].max()) if (both_f & equal).any() else 0.0,
+                                      "near_tie": float(rel[both_f & near].max()) if (both_f & near).any() else 0.0},
+            "field_other_examples": [[int(i), int(gtr[i]), int(otr[i]), float(gt[i]), float(ot[i]),
+                                      float(o["margin"][i])] for i in np.nonzero(other)[0][:5]]}
+
+
+def cpu_baseline(s, rays, gpu_hits, sample, reps, grid_dev_h=None):
     idx = np.linspace(0, rays.shape[0] - 1, min(sample, rays.shape[0])).astype(np.int64)
     sr = rays[idx]
     O, bvh, grid, prm = _oracle_world(s, sr)
@@ -401,15 +528,11 @@ def cpu_baseline(s, rays, gpu_hits, sample, reps):
     g = gpu_hits[idx]
     gt = g[:, 0].view(np.float32).astype(np.float64)
     gtr = g[:, 4]
-    err = {}
-    for name, tr in (("bvh_resolved", 1), ("sdf_resolved", 2)):
-        m = (gtr == tr) & (o["tracer"] == tr)
-        e = np.abs(gt[m] - o["t"][m]) / np.maximum(1.0, np.abs(o["t"][m]))
-        err[name] = {"n": int(m.sum()), "mean_rel": float(e.mean()) if e.size else 0.0,
-                     "p99_rel": float(np.quantile(e, 0.99)) if e.size else 0.0,
-                     "max_rel": float(e.max()) if e.size else 0.0}
+    err = {"bvh_resolved": _err_stats(gt, gtr, o, 1), "sdf_resolved": _err_stats(gt, gtr, o, 2)}
     err["tracer_agreement"] = float(np.mean(gtr == o["tracer"]))
     err["sample"] = f"{len(idx)} rays evenly spaced over the batch, fp64 checker, m={M_MIDDLE}"
+    if grid_dev_h is not None:
+        err["classified"] = fp64_gap(O, s, sr, g, o, grid_dev_h, grid)
     cb = {"value": len(idx) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
           "sample": f"{len(idx)} of {rays.shape[0]} GI rays (evenly spaced), fp64 combined query m={M_MIDDLE}, "
                     f"grid values evaluated before timing, median of {max(1, reps)} passes", "seconds": dt}
@@ -451,61 +574,46 @@ def run_gather(args):
 
 
 def run_reference(args):
+    """The CPU checker (fp64, all host cores) on the benchmark's own workload:
+    each step is one combined query (m = 2) over all 2,073,600 GI rays.  The
+    grid values the rays touch are evaluated in a first, untimed pass (the
+    device bakes its grid before its timed region too)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     s, rays = make_workload()
-    per_step = 4096
-    idx0 = np.random.default_rng(5).permutation(rays.shape[0])
-    n_total = per_step * (args.warmup + args.steps)
-    sel = idx0[: min(n_total, rays.shape[0])]
-    O, bvh, grid, prm = _oracle_world(s, rays[sel])
+    O, bvh, grid, prm = _oracle_world(s, rays)
     cores = O.default_threads()
-    for k in range(args.warmup):
-        O.trace_combined(bvh, grid, rays[sel[(k * per_step) % len(sel):][:per_step]], prm, precision=64)
+    for _ in range(args.warmup):
+        O.trace_combined(bvh, grid, rays, prm, precision=64, nthreads=cores)
     t0 = time.perf_counter()
-    done = 0
-    for k in range(args.steps):
-        off = ((args.warmup + k) * per_step) % len(sel)
-        batch = rays[sel[off:off + per_step]]
-        O.trace_combined(bvh, grid, batch, prm, precision=64, nthreads=cores)
-        done += batch.shape[0]
+    for _ in range(args.steps):
+        O.trace_combined(bvh, grid, rays, prm, precision=64, nthreads=cores)
     dt = time.perf_counter() - t0
-    v = done / dt
+    v = args.steps * rays.shape[0] / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded procedural scene and rays)",
-            "config": config_dict(s, rays.shape[0]),
+            "config": config_dict(s, rays.shape[0]), "parallelism": f"{cores} host threads",
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} GI rays per step, fp64 combined query m={M_MIDDLE}"},
+                             "sample": f"all {rays.shape[0]} GI rays per step, fp64 combined query m={M_MIDDLE}, "
+                                       "grid values the rays touch evaluated before timing"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_batching(args):
+def extra_batching(rq, scene, sdf, grid, frames_np, reps=2, tune=True):
+    """Batching configuration: len(frames_np) frames of mixed batches (primary,
+    AO, GI, shadow; R.mixed_frame) on the frame scene, traced one call per
+    batch, through rt_trace_batches, its CUDA graph, and with a float16 grid."""
     import torch
 
-    import paper_2305_07253_gb300 as rq
     from paper_2305_07253_gb300 import autotune
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    s = S.make_scene("frame")
-    n = s.spec.grid_n
-    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
-    grid = torch.empty((n, n, n), dtype=torch.float32, device=dev)
-    sdf = rq.rt_sdf_create(grid, s.lo, s.hi)
-    rq.rt_sdf_bake(scene, sdf, rq.BAKE_BVH)
-    frames = []
-    t0 = time.perf_counter()
-    for f in range(args.frames):
-        fb = []
-        for name, rays, kw in R.mixed_frame(s, f, M_MIDDLE):
-            rd = torch.from_numpy(rays).to(dev)
-            fb.append((name, rd, rq.split_params(**kw), torch.empty((rd.shape[0], 6), dtype=torch.int32, device=dev)))
-        frames.append(fb)
-    gen_s = time.perf_counter() - t0
+    dev = grid.device
+    frames = [[(name, torch.from_numpy(r).to(dev), rq.split_params(**kw),
+                torch.empty((r.shape[0], 6), dtype=torch.int32, device=dev)) for name, r, kw in fb]
+              for fb in frames_np]
     n_total = sum(b[1].shape[0] for fb in frames for b in fb)
     sizes = [{b[0]: int(b[1].shape[0]) for b in fb} for fb in frames]
 
@@ -514,31 +622,22 @@ def run_batching(args):
             for _, rd, p, h in fb:
                 rq.rt_trace_combined(scene, sdf, rd, p, h)
 
-    def batched():
+    def batched(sd=sdf):
         for fb in frames:
-            rq.rt_trace_batches(scene, sdf, [(rd, p, h) for _, rd, p, h in fb])
+            rq.rt_trace_batches(scene, sd, [(rd, p, h) for _, rd, p, h in fb])
 
-    def timed(fn, reps):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
-    reps = max(1, args.steps // 50)
+    rate = lambda ms: n_total / (ms * 1e-3)  # noqa: E731
+    forms = {}
+    forms["one_call_per_batch"] = _time_ms(per_batch, reps, warm=1)
+    forms["batched"] = _time_ms(batched, reps, warm=1)
     default = rq.rt_get_tuning().as_dict()
-    ms_per_batch_default = timed(per_batch, reps)
-    ms_batched_default = timed(batched, reps)
-    # autotune the batched form on the first frame
-    f0 = [(rd, p, h) for _, rd, p, h in frames[0]]
-    best, results = autotune.autotune(lambda: rq.rt_trace_batches(scene, sdf, f0), reps=3, warmup=1)
-    ms_per_batch = timed(per_batch, reps)
-    ms_batched = timed(batched, reps)
-    # one CUDA graph per frame
+    best, top = default, []
+    prev = rq.rt_get_tuning()
+    if tune:
+        f0 = [(rd, p, h) for _, rd, p, h in frames[0]]
+        best, results = autotune.autotune(lambda: rq.rt_trace_batches(scene, sdf, f0), reps=2, warmup=1)
+        top = sorted(([r[1], r[0]] for r in results), key=lambda x: x[0])[:5]
+        forms["batched_autotuned"] = _time_ms(batched, reps, warm=1)
     graphs = []
     st = torch.cuda.Stream()
     st.wait_stream(torch.cuda.current_stream())
@@ -554,51 +653,69 @@ def run_batching(args):
         for g in graphs:
             g.replay()
 
-    ms_graph = timed(replay, reps)
-    # the same frames with a float16 grid
+    forms["batched_cuda_graph"] = _time_ms(replay, reps, warm=1)
+    del graphs
     g16 = grid.half()
-    sdf16 = rq.rt_sdf_create(g16, s.lo, s.hi)
+    sdf16 = rq.rt_sdf_create(g16, *_box(sdf))
     rq.rt_sdf_prepare(sdf16)
-
-    def batched16():
-        for fb in frames:
-            rq.rt_trace_batches(scene, sdf16, [(rd, p, h) for _, rd, p, h in fb])
-
-    ms_batched16 = timed(batched16, reps)
-    rate = lambda ms: n_total / (ms * 1e-3)  # noqa: E731
-    line = {
-        "metric": "mixed-batch rays/s (primary, shadow, AO, GI per frame)", "value": rate(ms_graph),
-        "unit": UNIT, "n_gpus": 1, "frames": args.frames, "rays_total": n_total, "higher_is_better": True,
-        "data": "synthetic (seeded procedural scene and rays)", "dtype": "f32",
-        "config": {"workload": "frame-mixed-batches", "scene": "frame", "n_tris": int(s.n_tris),
-                   "grid": [n, n, n], "batch_sizes_per_frame": sizes, "input_generation_s": gen_s},
-        "forms": {
-            "one_call_per_batch_default_tuning": {"ms_total": ms_per_batch_default, "value": rate(ms_per_batch_default)},
-            "batched_default_tuning": {"ms_total": ms_batched_default, "value": rate(ms_batched_default)},
-            "one_call_per_batch_autotuned": {"ms_total": ms_per_batch, "value": rate(ms_per_batch)},
-            "batched_autotuned": {"ms_total": ms_batched, "value": rate(ms_batched)},
-            "batched_autotuned_cuda_graph": {"ms_total": ms_graph, "value": rate(ms_graph)},
-            "batched_autotuned_f16_grid": {"ms_total": ms_batched16, "value": rate(ms_batched16)},
-        },
-        "tuning_default": default, "tuning_autotuned": best,
-        "autotune_top5": sorted(([r[1], r[0]] for r in results), key=lambda x: x[0])[:5],
-    }
-    print(json.dumps(line), flush=True)
+    forms["batched_f16_grid"] = _time_ms(lambda: batched(sdf16), reps, warm=1)
+    rq.rt_set_tuning(prev)
+    out = {"frames": len(frames), "rays_total": int(n_total), "batch_sizes_per_frame": sizes,
+           "forms": {k: {"ms_total": v, "value": rate(v)} for k, v in forms.items()},
+           "tuning_default": default, "tuning_autotuned": best, "autotune_top5": top}
+    out["persistent_graph_beats_per_batch"] = bool(forms["batched_cuda_graph"] < forms["one_call_per_batch"])
+    out["f16_beats_per_batch"] = bool(forms["batched_f16_grid"] < forms["one_call_per_batch"])
+    del g16, sdf16, frames
+    return out
 
 
-def run_fit(args):
-    """Gradient fit of a noisy grid (differentiation workload): 102,532 triangles,
-    128^3 float32 grid = exact bake + N(0, (0.5 voxel)^2) noise, 1 M free-space rays
-    per step, loss = mean (t_field - t_triangles)^2 + 100 mean phi(p*)^2 at the
-    triangle hit points, Adam (lr 0.02 voxel), adjoint kernel backward."""
+def _box(sdf):
+    return sdf.lo, sdf.hi
+
+
+def _frame_world(rq, dev):
+    import torch
+    s = S.make_scene("frame")
+    n = s.spec.grid_n
+    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
+    grid = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    sdf = rq.rt_sdf_create(grid, s.lo, s.hi)
+    rq.rt_sdf_bake(scene, sdf, rq.BAKE_BVH)
+    return s, scene, grid, sdf
+
+
+def run_batching(args):
     import torch
 
     import paper_2305_07253_gb300 as rq
+
+    futs = input_pool({f"frame{f}": (_gen_mixed_frame, (f,)) for f in range(args.frames)})
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    s, scene, grid, sdf = _frame_world(rq, dev)
+    frames = [futs[f"frame{f}"].result() for f in range(args.frames)]
+    out = extra_batching(rq, scene, sdf, grid, frames, reps=max(1, args.steps // 50))
+    line = {"metric": "mixed-batch rays/s (primary, shadow, AO, GI per frame)",
+            "value": out["forms"]["batched_cuda_graph"]["value"], "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic (seeded procedural scene and rays)", "dtype": "f32",
+            "config": {"workload": "frame-mixed-batches", "scene": "frame", "n_tris": int(s.n_tris),
+                       "grid": [s.spec.grid_n] * 3}, "batching": out}
+    print(json.dumps(line), flush=True)
+
+
+def extra_fit(rq, pool_np, evals_np, steps=200, per=1024 * 1024):
+    """Differentiation configuration: gradient fit of a noisy grid (102,532
+    triangles, 128^3 float32 = exact bake + N(0, (0.5 voxel)^2) noise), `per`
+    free-space rays a step drawn in turn from `pool_np`, loss = mean (t_field -
+    t_triangles)^2 + 100 mean phi(p*)^2 at the triangle hit points, Adam (lr 0.02
+    voxel) through the adjoint kernel.  Steps/s and the field-vs-triangles
+    disagreement on `evals_np` before and after, and for the clean bake."""
+    import torch
+
     from paper_2305_07253_gb300 import fit as F
     from synth import rng as RNG
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    dev = torch.device("cuda", torch.cuda.current_device())
     s = S.make_scene("fit")
     n = s.spec.grid_n
     scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
@@ -611,17 +728,14 @@ def run_fit(args):
     grid = clean + torch.from_numpy(noise).to(dev)
     sdf = rq.rt_sdf_create(grid, s.lo, s.hi)
     rq.rt_sdf_prepare(sdf)
-    t0 = time.perf_counter()
-    margin = 2.0 * float(h.max())
-    pool = torch.from_numpy(R.free_space_rays(s, 4 * 1024 * 1024, 7, margin)).to(dev)
-    evals = torch.from_numpy(R.free_space_rays(s, 1024 * 1024, 8, margin)).to(dev)
-    gen_s = time.perf_counter() - t0
+    pool = torch.from_numpy(pool_np).to(dev)
+    evals = torch.from_numpy(evals_np).to(dev)
     t_pool = rq.hit_fields(rq.rt_trace_bvh(scene, pool))["t"].clone()
     t_eval = rq.hit_fields(rq.rt_trace_bvh(scene, evals))["t"].clone()
-    per = 1024 * 1024
+    nb = max(1, pool.shape[0] // per)
 
     def batches(step):
-        k = step % 4
+        k = step % nb
         return pool[k * per:(k + 1) * per], t_pool[k * per:(k + 1) * per]
 
     before = F.disagreement(scene, sdf, evals, t_eval)
@@ -636,36 +750,53 @@ def run_fit(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    hist = F.fit_grid(scene, sdf, batches, args.fit_steps, lr=lr, log_every=20, surface_weight=surface_weight)
+    hist = F.fit_grid(scene, sdf, batches, steps, lr=lr, log_every=20, surface_weight=surface_weight)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     after = F.disagreement(scene, sdf, evals, t_eval)
     after_c = F.disagreement(scene, sdf, evals, t_eval, m_near=M_MIDDLE)
-    line = {"metric": "gradient-fit steps/s and field-vs-triangle hit-t disagreement", "value":
-            args.fit_steps / (ms * 1e-3), "unit": "steps/s", "n_gpus": 1, "steps": args.fit_steps,
-            "higher_is_better": True, "data": "synthetic (seeded procedural scene and rays)", "dtype": "f32",
-            "config": {"workload": "fit-noisy-grid", "n_tris": int(s.n_tris), "grid": [n, n, n],
-                       "rays_per_step": per, "noise_sigma_m": 0.5 * h_min, "lr": lr,
-                       "surface_weight": surface_weight,
-                       "input_generation_s": gen_s},
-            "ms_per_step": ms / args.fit_steps,
+    return {"n_tris": int(s.n_tris), "grid": [n, n, n], "rays_per_step": per, "steps": steps,
+            "noise_sigma_m": 0.5 * h_min, "lr": lr, "surface_weight": surface_weight,
+            "steps_per_s": steps / (ms * 1e-3), "ms_per_step": ms / steps,
             "disagreement_field_only": {"noisy_init": before, "fitted": after, "clean_bake": clean_d},
             "disagreement_combined_m2": {"noisy_init": before_c, "fitted": after_c, "clean_bake": clean_c},
+            "fit_lowers_disagreement": bool(after["mean_abs"] < before["mean_abs"]),
             "loss_history": [[hh.step, hh.loss] for hh in hist]}
-    print(json.dumps(line), flush=True)
 
 
-def run_precision(args):
-    """Float16 vs float32 storage of a 512^3 grid on the 8,201,612-triangle scene,
-    1080p GI rays: rays/s per split setting, and hit-t error against the fp64
-    checker per tracer segment (the checker runs in this workload's CPU leg)."""
+def run_fit(args):
     import torch
 
     import paper_2305_07253_gb300 as rq
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    fut = input_pool({"fit": (_gen_fit_rays, (4 * 1024 * 1024, 1024 * 1024))})["fit"]
+    torch.cuda.set_device(0)
+    pool, evals = fut.result()
+    out = extra_fit(rq, pool, evals, steps=args.fit_steps)
+    line = {"metric": "gradient-fit steps/s and field-vs-triangle hit-t disagreement", "value": out["steps_per_s"],
+            "unit": "steps/s", "n_gpus": 1, "steps": args.fit_steps, "higher_is_better": True,
+            "data": "synthetic (seeded procedural scene and rays)", "dtype": "f32",
+            "config": {"workload": "fit-noisy-grid"}, "fit": out}
+    print(json.dumps(line), flush=True)
+
+
+def _err_stats(gt, g_tr, o, tr):
+    sel = (g_tr == tr) & (o["tracer"] == tr)
+    r = np.abs(gt[sel] - o["t"][sel]) / np.maximum(1.0, np.abs(o["t"][sel]))
+    return {"n": int(sel.sum()), "mean_rel": float(r.mean()) if r.size else 0.0,
+            "p99_rel": float(np.quantile(r, 0.99)) if r.size else 0.0,
+            "max_rel": float(r.max()) if r.size else 0.0}
+
+
+def extra_precision(rq, rays, K=5, W=3, sample=16384):
+    """Precision configuration: 8,201,612 triangles, a 512^3 grid baked in float32
+    on the device and stored again in float16, 1080p GI rays: ms per step for
+    m in {0, 2, inf} with each storage, and hit-t error against the fp64 checker
+    (its own BVH and exact bake) per tracer segment on an evenly spaced sample."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
     s = S.make_scene("precision")
     n = s.spec.grid_n
     scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
@@ -675,74 +806,100 @@ def run_precision(args):
     g16 = g32.half()
     sdf16 = rq.rt_sdf_create(g16, s.lo, s.hi)
     rq.rt_sdf_prepare(sdf16)
-    rays = R.gi_rays(s, 1920 * 1080, 7, 30.0)
     rd = torch.from_numpy(rays).to(dev)
     hits = torch.empty((rd.shape[0], 6), dtype=torch.int32, device=dev)
-    K, W = max(3, args.steps // 10), max(3, args.warmup)
-
-    def timed(sdf, p):
-        for _ in range(W):
-            rq.rt_trace_combined(scene, sdf, rd, p, hits)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(K):
-            rq.rt_trace_combined(scene, sdf, rd, p, hits)
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / K
-
-    sample = np.linspace(0, rays.shape[0] - 1, 4096).astype(np.int64)
-    res, got = {}, {}
+    idx = np.linspace(0, rays.shape[0] - 1, sample).astype(np.int64)
+    timing, got = {}, {}
     for m in (0.0, M_MIDDLE, math.inf):
         p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
         for name, sdf in (("f32", sdf32), ("f16", sdf16)):
-            ms = timed(sdf, p)
-            h = rq.rt_trace_combined(scene, sdf, rd, p).cpu().numpy()[sample]
-            got[(m, name)] = h
-            res[f"m={m}/{name}"] = {"ms": ms, "rays_per_s": rays.shape[0] / (ms * 1e-3)}
-    # hit-t error against the fp64 checker on the sample (CPU leg)
+            ms = _time_ms(lambda: rq.rt_trace_combined(scene, sdf, rd, p, hits), K, warm=W)
+            got[(m, name)] = rq.rt_trace_combined(scene, sdf, rd, p).cpu().numpy()[idx]
+            timing[f"m={m}/{name}"] = {"ms": ms, "rays_per_s": rays.shape[0] / (ms * 1e-3)}
+    del sdf16, g16, sdf32, g32, scene
+    torch.cuda.empty_cache()
     import oracle as O
     t0 = time.perf_counter()
     bvh = O.BVH(s.verts, s.tris)
     ogrid = O.Grid(s.lo, s.hi, [n, n, n], src=bvh)
     errs = {}
     for m in (0.0, M_MIDDLE, math.inf):
-        o = O.trace_combined(bvh, ogrid, rays[sample], O.make_params(mode=1, m_near=m), precision=64)
+        o = O.trace_combined(bvh, ogrid, rays[idx], O.make_params(mode=1, m_near=m), precision=64)
         for name in ("f32", "f16"):
             g = got[(m, name)]
-            gt = g[:, 0].view(np.float32).astype(np.float64)
-            gtr = g[:, 4]
-            e = {}
-            for seg, tr in (("bvh_resolved", 1), ("sdf_resolved", 2)):
-                sel = (gtr == tr) & (o["tracer"] == tr)
-                r = np.abs(gt[sel] - o["t"][sel]) / np.maximum(1.0, np.abs(o["t"][sel]))
-                e[seg] = {"n": int(sel.sum()), "mean_rel": float(r.mean()) if r.size else 0.0,
-                          "p99_rel": float(np.quantile(r, 0.99)) if r.size else 0.0,
-                          "max_rel": float(r.max()) if r.size else 0.0}
-            e["tracer_agreement"] = float(np.mean(gtr == o["tracer"]))
-            errs[f"m={m}/{name}"] = e
-    cpu_s = time.perf_counter() - t0
+            gt, gtr = g[:, 0].view(np.float32).astype(np.float64), g[:, 4]
+            errs[f"m={m}/{name}"] = {"bvh_resolved": _err_stats(gt, gtr, o, 1),
+                                     "sdf_resolved": _err_stats(gt, gtr, o, 2),
+                                     "tracer_agreement": float(np.mean(gtr == o["tracer"]))}
+    return {"n_tris": int(s.n_tris), "grid": [n, n, n], "grid_bytes": {"f32": n ** 3 * 4, "f16": n ** 3 * 2},
+            "rays": int(rays.shape[0]), "timing_ms": timing, "hit_t_err_vs_fp64": errs,
+            "f16_beats_f32_at_m2": bool(timing[f"m={M_MIDDLE}/f16"]["ms"] < timing[f"m={M_MIDDLE}/f32"]["ms"]),
+            "cpu_leg": {"sample": f"{sample} evenly spaced GI rays, fp64 checker with its own BVH and exact bake",
+                        "seconds": time.perf_counter() - t0}}
+
+
+def run_precision(args):
+    import torch
+
+    import paper_2305_07253_gb300 as rq
+
+    fut = input_pool({"precision": (_gen_precision_rays, ())})["precision"]
+    torch.cuda.set_device(0)
+    out = extra_precision(rq, fut.result(), K=max(3, args.steps // 10), W=max(3, args.warmup))
     line = {"metric": "float16 vs float32 grid: rays/s and hit-t error vs fp64, per split setting",
-            "value": res[f"m={M_MIDDLE}/f16"]["rays_per_s"], "unit": UNIT, "n_gpus": 1, "steps": K,
-            "higher_is_better": True, "data": "synthetic (seeded procedural scene and rays)", "dtype": "f16 grid, f32 math",
-            "config": {"workload": "precision-512", "n_tris": int(s.n_tris), "grid": [n, n, n],
-                       "grid_bytes": {"f32": int(g32.numel() * 4), "f16": int(g16.numel() * 2)},
-                       "rays": int(rays.shape[0]), "t_max_m": 30.0},
-            "timing": res, "hit_t_err_vs_fp64": errs,
-            "cpu_leg": {"sample": "4096 evenly spaced GI rays, fp64 checker with its own BVH and exact bake",
-                        "seconds": cpu_s}}
+            "value": out["timing_ms"][f"m={M_MIDDLE}/f16"]["rays_per_s"], "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic (seeded procedural scene and rays)",
+            "dtype": "f16 grid, f32 math", "config": {"workload": "precision-512"}, "precision": out}
     print(json.dumps(line), flush=True)
 
 
-def run_ao(args):
+def extra_ao(rq, scene, s, sdf256=None, K=3, n_pts=1 << 18, spp=16):
     """Ambient occlusion with the three tracers (the numeric form of the paper's
-    AO comparison, Section 3 "Occlusion Queries" and Fig. 2): 262,144 camera-facing
-    surface points, 16 cosine rays each, t in [0, t_ao]; AO = share of a point's
-    rays that reach t_ao unoccluded.  For each t_ao and split multiplier: tracing time, and the AO error
-    against triangles only (mean |dAO|, mean signed dAO = darkening, share of
-    points off by more than 0.1).  Each form is timed with the default tuning and
-    with one thread per query."""
+    AO comparison, Section 3 "Occlusion Queries" and Fig. 2): n_pts camera-facing
+    surface points, spp cosine rays each, t in [0, t_ao]; AO = share of a point's
+    rays that reach t_ao unoccluded (harness.ambient_occlusion).  For each grid
+    (the 256^3 frame grid and a coarse 64^3 one), t_ao and multiplier m: ms per
+    call (default tuning, and one thread per query), and the AO error against
+    triangles only (mean |dAO|, mean signed dAO, share of points off by > 0.1)."""
+    import torch
+
+    from paper_2305_07253_gb300 import harness as HN
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p, nn = R.surface_points(s, n_pts, 31)
+    bias = 1e-3 * s.diagonal
+    out = {}
+    for n in (s.spec.grid_n, 64):
+        if n == s.spec.grid_n and sdf256 is not None:
+            sdf, grid = sdf256, None
+        else:
+            grid = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+            sdf = rq.rt_sdf_create(grid, s.lo, s.hi)
+            rq.rt_sdf_bake(scene, sdf, rq.BAKE_BVH)
+        for t_ao in (0.5, 2.0, 10.0):
+            rays = torch.from_numpy(R.ao_rays(p, nn, np.full(n_pts, spp, dtype=np.int64), 32, t_ao, bias)).to(dev)
+            hits = torch.empty((rays.shape[0], 6), dtype=torch.int32, device=dev)
+            ao_ref = None
+            for m in (math.inf, 4.0, 2.0, 1.0, 0.0):
+                prm = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
+                ms = _time_ms(lambda: rq.rt_trace_combined(scene, sdf, rays, prm, hits), K)
+                prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
+                ms_simple = _time_ms(lambda: rq.rt_trace_combined(scene, sdf, rays, prm, hits), K)
+                rq.rt_set_tuning(prev)
+                ao = HN.ao_from_records(hits[:, 4], spp)
+                if ao_ref is None:
+                    ao_ref = ao.clone()
+                d = ao - ao_ref
+                out[f"grid={n}/t_ao={t_ao}/m={m}"] = {
+                    "ms": ms, "ms_one_thread_per_query": ms_simple, "rays_per_s": rays.shape[0] / (ms * 1e-3),
+                    "ao_mean": float(ao.mean()), "mean_abs_dAO": float(d.abs().mean()), "mean_dAO": float(d.mean()),
+                    "share_off_0.1": float((d.abs() > 0.1).float().mean())}
+            del rays, hits
+        del sdf, grid
+    return {"points": n_pts, "rays_per_point": spp, "grids": [s.spec.grid_n, 64], "table": out}
+
+
+def run_ao(args):
     import torch
 
     import paper_2305_07253_gb300 as rq
@@ -751,54 +908,11 @@ def run_ao(args):
     torch.cuda.set_device(dev)
     s = S.make_scene("frame")
     scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
-    n_pts, spp = 1 << 18, 16
-    p, nn = R.surface_points(s, n_pts, 31)
-    bias = 1e-3 * s.diagonal
-    out = {}
-    K = max(3, args.steps // 20)
-    # the 256^3 grid of the frame workload, and a coarse 64^3 grid (0.31 m voxels,
-    # near the 0.1-0.4 m voxels of the paper's combined-mode cascades)
-    for n in (s.spec.grid_n, 64):
-        grid = torch.empty((n, n, n), dtype=torch.float32, device=dev)
-        sdf = rq.rt_sdf_create(grid, s.lo, s.hi)
-        rq.rt_sdf_bake(scene, sdf, rq.BAKE_BVH)
-        for t_ao in (0.5, 2.0, 10.0):
-            rays = torch.from_numpy(R.ao_rays(p, nn, np.full(n_pts, spp, dtype=np.int64), 32, t_ao, bias)).to(dev)
-            hits = torch.empty((rays.shape[0], 6), dtype=torch.int32, device=dev)
-            ao_ref = None
-            for m in (math.inf, 4.0, 2.0, 1.0, 0.0):
-                prm = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
-                for _ in range(2):
-                    rq.rt_trace_combined(scene, sdf, rays, prm, hits)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(K):
-                    rq.rt_trace_combined(scene, sdf, rays, prm, hits)
-                e1.record()
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / K
-                # the same query with one thread per query (same records)
-                prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
-                ms_simple = _time_ms(lambda: rq.rt_trace_combined(scene, sdf, rays, prm, hits), K)
-                rq.rt_set_tuning(prev)
-                occl = (hits[:, 4] > 0).float().reshape(n_pts, spp).mean(dim=1)
-                ao = 1.0 - occl
-                if ao_ref is None:
-                    ao_ref = ao.clone()
-                d = ao - ao_ref
-                out[f"grid={n}/t_ao={t_ao}/m={m}"] = {
-                    "ms": ms, "rays_per_s": rays.shape[0] / (ms * 1e-3), "ms_one_thread_per_query": ms_simple,
-                    "ao_mean": float(ao.mean()),
-                    "mean_abs_dAO": float(d.abs().mean()), "mean_dAO": float(d.mean()),
-                    "share_off_0.1": float((d.abs() > 0.1).float().mean())}
-        del sdf, grid
+    out = extra_ao(rq, scene, s, K=max(3, args.steps // 20))
     line = {"metric": "AO tracing time and AO error vs triangles-only, per AO distance and split multiplier",
-            "value": out[f"grid={s.spec.grid_n}/t_ao=2.0/m=2.0"]["rays_per_s"], "unit": UNIT, "n_gpus": 1,
+            "value": out["table"][f"grid={s.spec.grid_n}/t_ao=2.0/m=2.0"]["rays_per_s"], "unit": UNIT, "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic (seeded procedural scene and rays)", "dtype": "f32",
-            "config": {"workload": "frame-ao", "n_tris": int(s.n_tris), "grids": [s.spec.grid_n, 64],
-                       "points": n_pts, "rays_per_point": spp},
-            "ao": out}
+            "config": {"workload": "frame-ao", "n_tris": int(s.n_tris)}, "ao": out}
     print(json.dumps(line), flush=True)
 
 
@@ -932,188 +1046,105 @@ def _write_png(path, img):
                 chunk(b"IDAT", zlib.compress(raw, 6)) + chunk(b"IEND", b""))
 
 
-def run_ao_images(args):
-    """AO images (the image form of the paper's Fig. 2): per pixel the surface
-    point the camera sees (primary rays, triangles), spp cosine rays to t_ao,
-    AO = share that escapes; with triangles only, the combined query (m = 2) and
-    the field only, on the dense exact grid and on the paper's 5 x 64^3 cascade.
-    Writes the images and |AO - AO(triangles only)| x 4 error images as PNG to
-    --out, prints the mean errors."""
-    import torch
-
-    import paper_2305_07253_gb300 as rq
-
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    s = S.make_scene("frame")
-    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
-    W, H, spp, t_ao = 960, 540, 16, 2.0
-    prim_rays = R.primary_rays(s, W, H)
-    hits = rq.hit_fields(rq.rt_trace_bvh(scene, torch.from_numpy(prim_rays).to(dev)))
-    t = hits["t"].cpu().numpy().astype(np.float64)
-    prim = hits["prim"].cpu().numpy()
-    seen = np.isfinite(t)
-    o = prim_rays[:, 0:3].astype(np.float64)
-    d = prim_rays[:, 4:7].astype(np.float64)
-    V = s.verts.astype(np.float64)
-    F = s.tris
-    p = o + np.where(seen, t, 0.0)[:, None] * d
-    tri = np.where(seen, prim, 0)
-    nrm = np.cross(V[F[tri, 1]] - V[F[tri, 0]], V[F[tri, 2]] - V[F[tri, 0]])
-    nrm /= np.maximum(np.linalg.norm(nrm, axis=1, keepdims=True), 1e-30)
-    nrm *= np.where(np.einsum("ij,ij->i", nrm, d) > 0, -1.0, 1.0)[:, None]  # facing the camera
-    ao_rays = torch.from_numpy(R.ao_rays(p, nrm, np.full(p.shape[0], spp, dtype=np.int64), 44, t_ao,
-                                         1e-3 * s.diagonal)).to(dev)
-    # pixel of every primary ray (the rays come in 8x8 screen tiles)
+def _pixels(W, H):
+    """(row, column) of every primary ray (the rays come in 8x8 screen tiles)."""
     py, px = np.mgrid[0:H, 0:W]
     order = R._tile_order(px.ravel(), py.ravel(), W)
-    pix_y, pix_x = py.ravel()[order], px.ravel()[order]
-    n = W * H
-    dense = torch.empty((256, 256, 256), dtype=torch.float32, device=dev)
+    return py.ravel()[order], px.ravel()[order]
+
+
+def _visible(rq, scene, s, W, H):
+    import torch
+    prim_rays = R.primary_rays(s, W, H)
+    f = rq.hit_fields(rq.rt_trace_bvh(scene, torch.from_numpy(prim_rays).cuda()))
+    from paper_2305_07253_gb300 import harness as HN
+    return HN.visible_points(prim_rays, f["t"].cpu().numpy().astype(np.float64), f["prim"].cpu().numpy(),
+                             s.verts, s.tris)
+
+
+def _image_fields(rq, scene, s):
+    import torch
+    dense = torch.empty((256, 256, 256), dtype=torch.float32, device="cuda")
     sdf_dense = rq.rt_sdf_create(dense, s.lo, s.hi)
     rq.rt_sdf_bake(scene, sdf_dense, rq.BAKE_BVH)
-    cg = torch.empty((5, 64, 64, 64), dtype=torch.float32, device=dev)
+    cg = torch.empty((5, 64, 64, 64), dtype=torch.float32, device="cuda")
     sdf_c = rq.rt_cascade_create(cg, 0.1, np.asarray(s.camera.eye, dtype=np.float32))
     rq.rt_sdf_bake(scene, sdf_c, rq.BAKE_JFA)
+    return (dense, sdf_dense), (cg, sdf_c)
+
+
+def extra_ao_images(rq, scene, s, W=960, H=540, spp=16, t_ao=2.0, out_dir=None):
+    """AO images (the image form of the paper's Fig. 2): per pixel the surface
+    point the camera sees (primary rays, triangles), spp cosine rays to t_ao
+    (harness.ambient_occlusion), with triangles only, the combined query (m = 2)
+    and the field only, on the dense exact grid and on the paper's 5 x 64^3
+    cascade built by its own method; per-pixel error against triangles only.
+    With out_dir, writes the images and 4 x |dAO| error images as PNG."""
+    from paper_2305_07253_gb300 import harness as HN
+    x, nx, seen = _visible(rq, scene, s, W, H)
+    pix_y, pix_x = _pixels(W, H)
+    (_, sdf_dense), (_, sdf_c) = _image_fields(rq, scene, s)
     forms = {"triangles": (None, rq.split_params(mode=rq.MODE_BVH)),
              "combined_dense": (sdf_dense, rq.split_params(mode=rq.MODE_SPLIT1, m_near=M_MIDDLE)),
              "field_dense": (sdf_dense, rq.split_params(mode=rq.MODE_SDF)),
              "combined_cascade": (sdf_c, rq.split_params(mode=rq.MODE_SPLIT1, m_near=M_MIDDLE)),
              "field_cascade": (sdf_c, rq.split_params(mode=rq.MODE_SDF))}
-    os.makedirs(args.out, exist_ok=True)
+    if out_dir:
+        os.makedirs(out_dir, exist_ok=True)
     out, ref = {}, None
     for name, (sdf, prm) in forms.items():
-        h = rq.rt_trace_combined(scene, sdf, ao_rays, prm)
-        ao = 1.0 - (h[:, 4] > 0).float().reshape(n, spp).mean(dim=1).cpu().numpy()
+        ao, _, _ = HN.ambient_occlusion(scene, sdf, prm, x, nx, spp, t_ao, 44, 1e-3 * s.diagonal)
+        ao = ao.cpu().numpy()
         ao[~seen] = 1.0
         img = np.ones((H, W))
         img[pix_y, pix_x] = ao
-        _write_png(os.path.join(args.out, f"ao_{name}.png"), img)
+        if out_dir:
+            _write_png(os.path.join(out_dir, f"ao_{name}.png"), img)
         if ref is None:
             ref = img
         else:
             err = np.abs(img - ref)
-            _write_png(os.path.join(args.out, f"ao_err_{name}.png"), 4.0 * err)
+            if out_dir:
+                _write_png(os.path.join(out_dir, f"ao_err_{name}.png"), 4.0 * err)
             out[name] = {"mean_abs_dAO": float(err.mean()), "share_off_0.1": float((err > 0.1).mean())}
-    print(json.dumps({"metric": "AO images vs triangles only", "config": {"workload": "frame-ao-images", "width": W,
-                                                                         "height": H, "spp": spp, "t_ao": t_ao},
-                      "images": sorted(os.listdir(args.out)), "errors": out}), flush=True)
+    return {"width": W, "height": H, "spp": spp, "t_ao": t_ao, "errors_vs_triangles": out}
 
 
-def _free_lights(s, count=4, below_ceiling=0.4, clearance=0.3):
-    """Point lights in free space under the ceiling: candidates on a grid, kept
-    when clear of every object's bounding sphere, the `count` nearest to the
-    quarter points of the room taken."""
-    room = np.asarray(s.room, dtype=np.float64)
-    xs = np.linspace(0.1, 0.9, 9)
-    cand = np.array([[x * room[0], room[1] - below_ceiling, z * room[2]] for x in xs for z in xs])
-    ok = np.ones(len(cand), dtype=bool)
-    for ob in s.objects:
-        ok &= np.linalg.norm(cand - np.asarray(ob.center), axis=1) > ob.radius + clearance
-    cand = cand[ok]
-    out = []
-    for qx, qz in ((0.25, 0.25), (0.75, 0.25), (0.25, 0.75), (0.75, 0.75))[:count]:
-        q = np.array([qx * room[0], room[1] - below_ceiling, qz * room[2]])
-        out.append(cand[np.argmin(np.linalg.norm(cand - q, axis=1))])
-    return np.array(out)
-
-
-def _field_normals(levels, y, d):
-    """Unit gradient of a field at points y (m, 3), flipped against the ray
-    directions d: central differences of the trilinear interpolant with half a
-    voxel.  levels: [(grid (n, n, n) x fastest, lo (3), hi (3))], finest first;
-    a point takes the finest level whose box holds it (the coarsest otherwise)."""
-    import torch
-    from paper_2305_07253_gb300 import fit as F
-    k_of = torch.full((y.shape[0],), len(levels) - 1, dtype=torch.long, device=y.device)
-    for k in range(len(levels) - 2, -1, -1):
-        lo = torch.tensor(levels[k][1], dtype=y.dtype, device=y.device)
-        hi = torch.tensor(levels[k][2], dtype=y.dtype, device=y.device)
-        k_of = torch.where(((y >= lo) & (y <= hi)).all(dim=1), torch.full_like(k_of, k), k_of)
-    g = torch.zeros_like(y)
-    for k, (grid, lo, hi) in enumerate(levels):
-        sel = k_of == k
-        if not bool(sel.any()):
-            continue
-        yk = y[sel]
-        h = (torch.tensor(hi, dtype=y.dtype, device=y.device) - torch.tensor(lo, dtype=y.dtype, device=y.device)) \
-            / (grid.shape[0] - 1)
-        gk = torch.empty_like(yk)
-        for a in range(3):
-            e = torch.zeros(3, dtype=y.dtype, device=y.device)
-            e[a] = 0.5 * h[a]
-            gk[:, a] = (F.interpolate(grid, lo, hi, yk + e) - F.interpolate(grid, lo, hi, yk - e)) / (2 * e[a])
-        g[sel] = gk
-    g = g / g.norm(dim=1, keepdim=True).clamp(min=1e-30)
-    return torch.where(((g * d).sum(dim=1) > 0)[:, None], -g, g)
-
-
-def run_gi_images(args):
-    """GI images (the image form of the paper's GI experiment, Section 3 "GI &
-    Shadow Rays"): per pixel the surface point x the camera sees (primary rays,
-    triangles, in every form), direct light from 4 point lights through shadow
-    rays (two splits, any hit), and one bounce through spp cosine GI rays (one
-    split, closest hit, t_max 30 m) whose hit points y are lit through shadow
-    rays too.  Constant albedo 0.7 (the paper's assumption); the normal at a
-    field-resolved y is the gradient of the form's own field.  The GI and shadow
-    queries run as triangles only, combined (m = 2) and field only, on the dense
-    exact grid and on the paper's 5 x 64^3 cascade.  Writes the images and
-    4 x |image - image(triangles only)| error images as PNG to --out, prints the
-    errors (per pixel, on 8 x 8 tile means, and of the direct light alone) and
-    the time of the GI and shadow queries."""
+def run_ao_images(args):
     import torch
 
     import paper_2305_07253_gb300 as rq
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    torch.cuda.set_device(0)
     s = S.make_scene("frame")
-    scene = rq.rt_scene_build(torch.from_numpy(s.verts).to(dev), torch.from_numpy(s.tris).to(dev))
-    W, H, spp, albedo, power = 960, 540, 16, 0.7, 25.0
+    scene = rq.rt_scene_build(torch.from_numpy(s.verts).cuda(), torch.from_numpy(s.tris).cuda())
+    out = extra_ao_images(rq, scene, s, out_dir=args.out)
+    print(json.dumps({"metric": "AO images vs triangles only", "config": {"workload": "frame-ao-images"},
+                      "images": sorted(os.listdir(args.out)), "ao_images": out}), flush=True)
+
+
+def extra_gi_images(rq, scene, s, W=960, H=540, spp=16, albedo=0.7, power=25.0, K=3, out_dir=None):
+    """GI images (the image form of the paper's GI experiment, Section 3 "GI &
+    Shadow Rays"): per pixel the surface point x the camera sees (primary rays,
+    triangles, in every form) and its one-bounce radiance (harness.one_bounce):
+    direct light from 4 point lights through shadow rays (two splits, any hit)
+    and spp cosine GI rays (one split, closest hit, t_max 30 m) whose hit points
+    are lit the same way; constant albedo.  Forms: triangles only, combined
+    (m = 2) and field only, on the dense exact grid and on the paper's 5 x 64^3
+    cascade.  Errors against triangles only per pixel, on 8 x 8 tile means and
+    for the direct light alone, and the time of each form's queries.  With
+    out_dir, writes tone-mapped images and 4 x error images as PNG."""
+    import torch
+
+    from paper_2305_07253_gb300 import harness as HN
     bias = 1e-3 * s.diagonal
-    prim_rays = R.primary_rays(s, W, H)
-    hits = rq.hit_fields(rq.rt_trace_bvh(scene, torch.from_numpy(prim_rays).to(dev)))
-    t = hits["t"].cpu().numpy().astype(np.float64)
-    prim = hits["prim"].cpu().numpy()
-    seen = np.isfinite(t)
-    o, d = prim_rays[:, 0:3].astype(np.float64), prim_rays[:, 4:7].astype(np.float64)
+    x, nx, seen = _visible(rq, scene, s, W, H)
+    pix_y, pix_x = _pixels(W, H)
+    lights = S.free_lights(s)
     V, Fi = s.verts.astype(np.float64), s.tris
-    x = o + np.where(seen, t, 0.0)[:, None] * d
-    tri = np.where(seen, prim, 0)
-    nx = np.cross(V[Fi[tri, 1]] - V[Fi[tri, 0]], V[Fi[tri, 2]] - V[Fi[tri, 0]])
-    nx /= np.maximum(np.linalg.norm(nx, axis=1, keepdims=True), 1e-30)
-    nx *= np.where(np.einsum("ij,ij->i", nx, d) > 0, -1.0, 1.0)[:, None]
-    lights = torch.tensor(_free_lights(s), dtype=torch.float64, device=dev)
-    n = W * H
-    xt, nxt = torch.from_numpy(x).to(dev), torch.from_numpy(nx).to(dev)
-    face_n = torch.from_numpy(np.cross(V[Fi[:, 1]] - V[Fi[:, 0]], V[Fi[:, 2]] - V[Fi[:, 0]])).to(dev)
+    face_n = torch.from_numpy(np.cross(V[Fi[:, 1]] - V[Fi[:, 0]], V[Fi[:, 2]] - V[Fi[:, 0]])).cuda()
     face_n = face_n / face_n.norm(dim=1, keepdim=True).clamp(min=1e-30)
-    gi = torch.from_numpy(R.ao_rays(x, nx, np.full(n, spp, dtype=np.int64), 45, 30.0, bias)).to(dev)
-
-    def shadow_rays(p, nn):
-        """p, nn (m, 3) float64 -> rays to every light (m * L, 8) float32, cos terms, 1/d^2."""
-        L = lights.shape[0]
-        org = (p + bias * nn)[:, None, :].expand(-1, L, -1)
-        v = lights[None, :, :] - org
-        dist = v.norm(dim=2)
-        dirn = v / dist[..., None]
-        cos = (dirn * nn[:, None, :]).sum(dim=2).clamp(min=0.0)
-        r = torch.cat([org, torch.zeros_like(dist)[..., None], dirn, (dist - bias).clamp(min=0.0)[..., None]],
-                      dim=2).reshape(-1, 8).float()
-        return r.contiguous(), cos, 1.0 / dist.pow(2)
-
-    def direct(p, nn, prm, sdf):
-        r, cos, inv2 = shadow_rays(p, nn)
-        h = rq.rt_trace_combined(scene, sdf, r, prm)
-        vis = (h[:, 4] == rq.TRACER_MISS).double().reshape(cos.shape)
-        return (power * vis * cos * inv2).sum(dim=1), r
-
-    dense = torch.empty((256, 256, 256), dtype=torch.float32, device=dev)
-    sdf_dense = rq.rt_sdf_create(dense, s.lo, s.hi)
-    rq.rt_sdf_bake(scene, sdf_dense, rq.BAKE_BVH)
-    cg = torch.empty((5, 64, 64, 64), dtype=torch.float32, device=dev)
-    sdf_c = rq.rt_cascade_create(cg, 0.1, np.asarray(s.camera.eye, dtype=np.float32))
-    rq.rt_sdf_bake(scene, sdf_c, rq.BAKE_JFA)
+    (dense, sdf_dense), (cg, sdf_c) = _image_fields(rq, scene, s)
     lv_dense = [(dense, tuple(s.lo), tuple(s.hi))]
     lv_c = [(cg[k], *rq.rt_cascade_box(sdf_c, k)) for k in range(5)]
     gi_p = {"triangles": rq.split_params(mode=rq.MODE_BVH),
@@ -1125,65 +1156,61 @@ def run_gi_images(args):
     forms = {"triangles": ("triangles", None, None), "combined_dense": ("combined", sdf_dense, lv_dense),
              "field_dense": ("field", sdf_dense, lv_dense), "combined_cascade": ("combined", sdf_c, lv_c),
              "field_cascade": ("field", sdf_c, lv_c)}
-    py, px = np.mgrid[0:H, 0:W]
-    order = R._tile_order(px.ravel(), py.ravel(), W)
-    pix_y, pix_x = py.ravel()[order], px.ravel()[order]
-    os.makedirs(args.out, exist_ok=True)
-    K = max(3, args.steps // 40)
+    if out_dir:
+        os.makedirs(out_dir, exist_ok=True)
+
+    def tiles(a):
+        return a[:H // 8 * 8, :W // 8 * 8].reshape(H // 8, 8, W // 8, 8).mean(axis=(1, 3))
+
+    def rel_err(a, b):
+        m = b > 0
+        r = np.abs(a - b)[m] / b[m]
+        return {"mean_rel": float(r.mean()), "share_off_10pct": float((r > 0.1).mean())}
+
     out, ref, expo = {}, None, None
     for name, (kind, sdf, lv) in forms.items():
-        e_x, r_x = direct(xt, nxt, sh_p[kind], sdf)
-        hg = rq.rt_trace_combined(scene, sdf, gi, gi_p[kind])
-        f = rq.hit_fields(hg)
-        tg = f["t"].double()
-        hit = torch.isfinite(tg)
-        y = gi[:, 0:3].double() + torch.where(hit, tg, torch.zeros_like(tg))[:, None] * gi[:, 4:7].double()
-        ny = torch.zeros_like(y)
-        bvh = f["tracer"] == rq.TRACER_BVH
-        if bool(bvh.any()):
-            fn = face_n[f["prim"][bvh].long()]
-            db = gi[bvh, 4:7].double()
-            ny[bvh] = torch.where(((fn * db).sum(dim=1) > 0)[:, None], -fn, fn)
-        fld = f["tracer"] == rq.TRACER_SDF
-        if bool(fld.any()):
-            ny[fld] = _field_normals(lv, y[fld], gi[fld, 4:7].double())
-        e_y, r_y = direct(y, ny, sh_p[kind], sdf)
-        e_y = torch.where(hit, e_y, torch.zeros_like(e_y))
-        e_ind = albedo * e_y.reshape(n, spp).mean(dim=1)
-        rad = (albedo / math.pi) * (e_x + e_ind)
-        rad = rad.cpu().numpy()
+        res = HN.one_bounce(scene, sdf, gi_p[kind], sh_p[kind], x, nx, face_n, lv, lights, power, albedo, spp, 45,
+                            bias)
+        rad = res["radiance"].cpu().numpy()
         rad[~seen] = 0.0
         img = np.zeros((H, W))
         img[pix_y, pix_x] = rad
         dimg = np.zeros((H, W))
-        dimg[pix_y, pix_x] = np.where(seen, (albedo / math.pi) * e_x.cpu().numpy(), 0.0)
+        dimg[pix_y, pix_x] = np.where(seen, res["direct"].cpu().numpy(), 0.0)
         if expo is None:
             expo = 1.0 / max(float(np.percentile(rad[seen], 90)), 1e-12)
         tone = 1.0 - np.exp(-expo * img)
-        _write_png(os.path.join(args.out, f"gi_{name}.png"), tone)
+        if out_dir:
+            _write_png(os.path.join(out_dir, f"gi_{name}.png"), tone)
+        r_x, gi, r_y = res["batches"]
         ms = (_time_ms(lambda: rq.rt_trace_combined(scene, sdf, r_x, sh_p[kind]), K) +
               _time_ms(lambda: rq.rt_trace_combined(scene, sdf, gi, gi_p[kind]), K) +
               _time_ms(lambda: rq.rt_trace_combined(scene, sdf, r_y, sh_p[kind]), K))
         entry = {"query_ms": ms, "rays": int(r_x.shape[0] + gi.shape[0] + r_y.shape[0])}
-        def tiles(a):
-            return a[:H // 8 * 8, :W // 8 * 8].reshape(H // 8, 8, W // 8, 8).mean(axis=(1, 3))
-
-        def rel_err(a, b):
-            m = b > 0
-            r = np.abs(a - b)[m] / b[m]
-            return {"mean_rel": float(r.mean()), "share_off_10pct": float((r > 0.1).mean())}
         if ref is None:
             ref, ref_tone, ref_direct = img, tone, dimg
         else:
             err = np.abs(tone - ref_tone)
-            _write_png(os.path.join(args.out, f"gi_err_{name}.png"), 4.0 * err)
+            if out_dir:
+                _write_png(os.path.join(out_dir, f"gi_err_{name}.png"), 4.0 * err)
             entry.update({"mean_abs_d_tone": float(err.mean()), "pixels": rel_err(img, ref),
                           "tiles_8x8": rel_err(tiles(img), tiles(ref)), "direct_only": rel_err(dimg, ref_direct)})
         out[name] = entry
-    print(json.dumps({"metric": "GI images vs triangles only", "config": {"workload": "frame-gi-images", "width": W,
-                                                                         "height": H, "spp": spp, "lights": 4,
-                                                                         "albedo": albedo},
-                      "images": sorted(os.listdir(args.out)), "forms": out}), flush=True)
+        del res
+    return {"width": W, "height": H, "spp": spp, "lights": int(lights.shape[0]), "albedo": albedo, "forms": out}
+
+
+def run_gi_images(args):
+    import torch
+
+    import paper_2305_07253_gb300 as rq
+
+    torch.cuda.set_device(0)
+    s = S.make_scene("frame")
+    scene = rq.rt_scene_build(torch.from_numpy(s.verts).cuda(), torch.from_numpy(s.tris).cuda())
+    out = extra_gi_images(rq, scene, s, K=max(3, args.steps // 40), out_dir=args.out)
+    print(json.dumps({"metric": "GI images vs triangles only", "config": {"workload": "frame-gi-images"},
+                      "images": sorted(os.listdir(args.out)), "gi_images": out}), flush=True)
 
 
 def run_dfbuild(args):

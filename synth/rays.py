@@ -193,6 +193,22 @@ def shadow_rays(p: np.ndarray, nn: np.ndarray, lights: np.ndarray, seed: int, bi
     return _renorm(pack(o, d, 0.0, np.maximum(dist - bias, 0.0)))
 
 
+def light_rays(p: np.ndarray, nn: np.ndarray, lights: np.ndarray, bias: float):
+    """Shadow rays from every surface point to every point light (Section 3,
+    GI & shadow rays): origin p + bias n, t in [0, distance - bias], point-major
+    (ray i * L + l goes from point i to light l).  Also returns the geometry of
+    each pair at the point: cos of the angle between n and the light direction
+    (clamped at 0) and 1 / distance^2, both (m, L) float64."""
+    m, L = p.shape[0], lights.shape[0]
+    o = p + bias * nn
+    v = lights[None, :, :] - o[:, None, :]
+    dist = np.linalg.norm(v, axis=2)
+    d = v / np.maximum(dist, 1e-12)[..., None]
+    cos = np.maximum(np.einsum("mlk,mk->ml", d, nn), 0.0)
+    rays = pack(np.repeat(o, L, axis=0), d.reshape(-1, 3), 0.0, np.maximum(dist - bias, 0.0).reshape(-1))
+    return _renorm(rays), cos, 1.0 / np.maximum(dist, 1e-12) ** 2
+
+
 def free_space_rays(scene: Scene, n: int, seed: int, margin: float, t_max: float | None = None) -> np.ndarray:
     """Origins uniform in the room, at least `margin` outside every object's bounding
     sphere and away from the walls; directions uniform on the sphere."""

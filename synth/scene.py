@@ -294,3 +294,22 @@ def make_scene(name: str, seed: int = 2305) -> Scene:
     verts = np.ascontiguousarray(np.concatenate(Vs).astype(np.float32))
     tris = np.ascontiguousarray(np.concatenate(Fs).astype(np.int32))
     return Scene(spec, seed, verts, tris, scene_objs, spec.room, cam, dropped)
+
+
+def free_lights(scene: Scene, count: int = 4, below_ceiling: float = 0.4, clearance: float = 0.3) -> np.ndarray:
+    """Point lights in free space under the ceiling: candidates on a 9 x 9 grid
+    at below_ceiling under it, kept when `clearance` outside every object's
+    bounding sphere; the one nearest to each quarter point of the room is taken.
+    (count, 3) float64."""
+    room = np.asarray(scene.room, dtype=np.float64)
+    xs = np.linspace(0.1, 0.9, 9)
+    cand = np.array([[x * room[0], room[1] - below_ceiling, z * room[2]] for x in xs for z in xs])
+    ok = np.ones(len(cand), dtype=bool)
+    for ob in scene.objects:
+        ok &= np.linalg.norm(cand - np.asarray(ob.center), axis=1) > ob.radius + clearance
+    cand = cand[ok]
+    out = []
+    for qx, qz in ((0.25, 0.25), (0.75, 0.25), (0.25, 0.75), (0.75, 0.75))[:count]:
+        q = np.array([qx * room[0], room[1] - below_ceiling, qz * room[2]])
+        out.append(cand[np.argmin(np.linalg.norm(cand - q, axis=1))])
+    return np.array(out)

@@ -193,6 +193,7 @@ def compare(g: dict, o: np.ndarray, rays, verts, tris, *, any_hit: bool = False,
     rep["t_err_max_sdf"] = float(rel[both_sdf].max()) if both_sdf.any() else 0.0
     rep["examples"] = [(int(i), int(gt[i]), int(ot[i]), float(g["t"][i]), float(o["t"][i]), int(g["prim"][i]),
                         int(otp[i])) for i in unexplained[:8]]
+    rep["mask_equal"] = equal
     if check:
         assert unexplained.size == 0, f"unexplained mismatches: {rep}; (i, tracer dev/chk, t dev/chk, prim dev/chk): " \
                                       f"{rep['examples']}"
