@@ -368,11 +368,14 @@ def run_ours(args):
         d = json.load(open(tf))
         if d.get("trace_hash") == trace_hash() and d.get("workload") == WORKLOAD:
             traffic = d.get("bytes_per_launch", {}).get(dom_stage)
+    caches = cache_ceilings()
     kernel_names = {"bvh_near": "k_stage_bvh (near triangle sub-interval)",
                     "field_split": "k_stage_field (distance-field sub-interval)",
                     "bvh_full": "k_stage_bvh", "field_full": "k_stage_field", "all": "k_trace"}
     stages = {name: {st: {"ms": ms, "algorithmic_bytes": stage_bytes(name, st),
-                          "GBps": stage_bytes(name, st) / (ms * 1e-3) / 1e9}
+                          "GBps": stage_bytes(name, st) / (ms * 1e-3) / 1e9,
+                          "frac_of_hbm": stage_bytes(name, st) / (ms * 1e-3) / 1e9 / peak,
+                          "frac_of_l2_read": stage_bytes(name, st) / (ms * 1e-3) / 1e9 / caches["l2_read_GBps"]}
                      for st, ms in v.items()} for name, v in stage_ms.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -395,7 +398,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": ab, "launch_ms": dom_ms, "peak_kind": f"of {peak_kind}",
                      "step": {"algorithmic_bytes": stage_bytes("combined", "all"),
                               "GBps": stage_bytes("combined", "all") / (ms_mid * 1e-3) / 1e9},
-                     "random_gather": gather_ceiling(rq, peak)},
+                     "random_gather": gather_ceiling(peak), "caches": caches},
         "e2e": {"value": world * n_rays / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(rays.nbytes),
                 "d2h_bytes_per_step": int(n_rays * 24), "ms_per_step": ms_e2e},
         "gpu_launches": K * len(stage_ms["combined"]),
@@ -539,20 +542,22 @@ def cpu_baseline(s, rays, gpu_hits, sample, reps, grid_dev_h=None):
     return cb, err
 
 
-def gather_ceiling(rq, peak, K=10, W=2):
+def gather_ceiling(peak, K=10, W=2):
     """Rate of chains of dependent random 32-byte gathers over 2^24 cells (537 MB,
     beyond the L2), one chain per thread at the field stage's occupancy (12 blocks
     of 128 per SM), 64 gathers a chain: the access a march step makes, with no
     locality.  Context for the field stage's fraction of the copy bandwidth."""
     import torch
+
+    from paper_2305_07253_gb300 import mem_probe
     n_cells, steps = 1 << 24, 64
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     blocks = sms * 12
     g = torch.Generator(device="cuda")
     g.manual_seed(11)
     cells = torch.rand(n_cells * 8, device="cuda", generator=g)
     out = torch.empty(blocks * 128, dtype=torch.float32, device="cuda")
-    ms = _time_ms(lambda: rq.rt_gather_probe(cells, steps, blocks, out), K, W)
+    ms = _time_ms(lambda: mem_probe.random_gather(cells, steps, blocks, out), K, W)
     nbytes = blocks * 128 * steps * 32
     del cells, out
     gbps = nbytes / (ms * 1e-3) / 1e9
@@ -560,16 +565,40 @@ def gather_ceiling(rq, peak, K=10, W=2):
             "cells": n_cells, "chains": blocks * 128, "gathers_per_chain": steps}
 
 
-def run_gather(args):
-    """Only the gather probe (for a profiler): K timed launches after W."""
+def cache_ceilings(K=10, W=2):
+    """Read bandwidth of the L2 (a 64 MiB buffer read 10 times over with
+    coalesced 16-byte loads that bypass L1) and of the L1 (each block re-reading
+    its own 64 KiB window 50 times, two blocks per SM): the ceilings of the
+    triangle stages, whose node and triangle reads are mostly L1 and L2 hits."""
     import torch
-    import paper_2305_07253_gb300 as rq
+
+    from paper_2305_07253_gb300 import mem_probe
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    l2_bytes, l2_reps, l2_blocks = 64 << 20, 10, sms * 8
+    buf = torch.ones(l2_bytes // 4, dtype=torch.float32, device="cuda")
+    out = torch.empty(l2_blocks * mem_probe.READ_BLOCK, dtype=torch.float32, device="cuda")
+    ms_l2 = _time_ms(lambda: mem_probe.l2_read(buf, l2_reps, l2_blocks, out), K, W)
+    window, l1_reps, l1_blocks = 64 << 10, 50, sms * 2
+    out1 = torch.empty(l1_blocks * mem_probe.READ_BLOCK, dtype=torch.float32, device="cuda")
+    ms_l1 = _time_ms(lambda: mem_probe.l1_read(buf, window, l1_reps, l1_blocks, out1), K, W)
+    del buf, out, out1
+    l2 = l2_bytes * l2_reps / (ms_l2 * 1e-3) / 1e9
+    l1 = window * l1_blocks * l1_reps / (ms_l1 * 1e-3) / 1e9
+    return {"l2_read_GBps": l2, "l1_read_GBps": l1,
+            "l2": {"bytes": l2_bytes, "reps": l2_reps, "blocks": l2_blocks, "launch_ms": ms_l2},
+            "l1": {"window_bytes": window, "reps": l1_reps, "blocks": l1_blocks, "launch_ms": ms_l1}}
+
+
+def run_gather(args):
+    """Only the memory-system probes (for a profiler): K timed launches after W."""
+    import torch
     torch.cuda.set_device(0)
     peak, peak_kind = peaks()
-    r = gather_ceiling(rq, peak, K=args.steps, W=args.warmup)
+    r = gather_ceiling(peak, K=args.steps, W=args.warmup)
     print(json.dumps({"metric": "dependent random 32-byte gathers, 537 MB", "value": r["useful_GBps"], "unit": "GB/s",
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                       "dtype": "f32", "data": "synthetic", "peak_kind": f"of {peak_kind}", **r,
+                      "caches": cache_ceilings(K=args.steps, W=args.warmup),
                       "config": {"workload": "gather-probe-537MB"}}), flush=True)
 
 

@@ -220,7 +220,9 @@ rt_status rt_sdf_bake(const rt_scene* scene, rt_sdf* sdf, int32_t method, void* 
  *      sample's
  * "Best" is the smallest (squared distance to the triangle, triangle index),
  * evaluated in single precision with every operation rounded once.  Cascade
- * levels are built coarsest first.  d_sites: caller memory, one int32 per
+ * levels are built one at a time, coarsest first: a level runs steps 1..stage
+ * before the next finer level takes its sites as seeds.  d_sites: caller
+ * memory, one int32 per
  * sample.  The grid values are not touched.  Enqueued on `stream`. */
 rt_status rt_sdf_sites(const rt_scene* scene, const rt_sdf* sdf, int32_t stage, int32_t* d_sites, void* stream);
 
@@ -442,23 +444,6 @@ enum { RT_LAYOUT_CELLS = 0, RT_LAYOUT_PLAIN = 1, RT_LAYOUT_PAIRS = 2 };
 
 rt_status rt_set_tuning(const rt_tuning* tuning);
 rt_status rt_get_tuning(rt_tuning* tuning);
-
-/* Memory-system probe (measurement, not part of a query).  A march step of
- * the field tracer (Section 3) reads one 32-byte cell whose address depends on
- * the previous step's value.  This runs blocks x 128 chains of `steps` such
- * dependent 32-byte gathers with addresses spread uniformly over d_cells, so
- * no locality helps; bytes / time is the device's ceiling for that access.
- *   d_cells  n_cells x 32 bytes (8 float32), device, 32-byte aligned; n_cells
- *            a power of two in [1, 2^31]
- *   chain i  starts at cell fmix32(i + 1) & (n_cells - 1) (fmix32: the 32-bit
- *            finaliser of MurmurHash3); a step at cell c loads its 8 floats v,
- *            adds v[0] + v[7] to the chain's sum (float32, in order) and moves
- *            to fmix32(c ^ bits(v[3]) ^ s) & (n_cells - 1), s the step number
- *   d_out    blocks x 128 float32, device: each chain's sum
- * Enqueued on `stream`.  Errors: RT_ERR_INVALID_ARG (null or misaligned
- * buffers, n_cells not a power of two, steps < 1, blocks outside [1, 2^20]). */
-rt_status rt_gather_probe(const void* d_cells, int64_t n_cells, int32_t steps, int32_t blocks, float* d_out,
-                          void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* rt_last_error(void);

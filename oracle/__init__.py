@@ -345,12 +345,10 @@ def _level_grid(grid, k=None):
 def df_sites(bvh: BVH, grid, stage: int = 3, nthreads: int | None = None):
     """Sites (triangle index per sample, -1 for none) of the paper's field build
     after `stage` (1 voxelisation, 2 jump flooding, 3 sweeps).  One grid: an
-    array of n0*n1*n2; a cascade: (levels, n^3), built coarsest level first, each
-    level seeded also from the next coarser one's sites after its jump flooding,
-    and swept after all levels are flooded."""
+    array of n0*n1*n2; a cascade: (levels, n^3), built one level at a time,
+    coarsest first: each level runs steps 1..stage, seeded also from the next
+    coarser level's sites as they stand after that level's own steps 1..stage."""
     if isinstance(grid, Cascade):
-        # coarsest level first, each seeded from the coarser level's sites after
-        # jump flooding (or after voxelisation for stage 1); then the sweeps of all levels
         out = np.zeros((grid.levels, grid.n ** 3), dtype=np.int32)
         for k in reversed(range(grid.levels)):
             g, _, _ = _level_grid(grid, k)
@@ -358,12 +356,7 @@ def df_sites(bvh: BVH, grid, stage: int = 3, nthreads: int | None = None):
             if k + 1 < grid.levels:
                 coarse = _ptr(out[k + 1])
                 gc, _, _ = _level_grid(grid, k + 1)
-            lib().or_df_sites(bvh.h, g, coarse, gc, int(min(stage, 2)), nthreads or default_threads(),
-                              _ptr(out[k]))
-        if stage >= 3:
-            for k in range(grid.levels):
-                g, _, _ = _level_grid(grid, k)
-                lib().or_df_sweep(bvh.h, g, _ptr(out[k]))
+            lib().or_df_sites(bvh.h, g, coarse, gc, int(stage), nthreads or default_threads(), _ptr(out[k]))
         return out
     g, count, _ = _level_grid(grid)
     out = np.zeros(count, dtype=np.int32)

@@ -132,8 +132,9 @@ void or_trace_combined_cascade(const or_bvh* b, const or_cascade* c, const float
  * steps).  or_df_sites writes the site (triangle index, -1 for none) of every
  * sample of g after step `stage` (1 voxelisation, 2 jump flooding, 3 sweeps);
  * coarse / gc: the sites and grid of the next coarser cascade level (NULL
- * otherwise; a cascade seeds from the coarser level's sites after its jump
- * flooding).  or_df_sweep: step 3 alone, in place.  or_df_field: signed distance (double) from each sample to its
+ * otherwise; a cascade is built one level at a time, coarsest first, and a
+ * level is seeded from the coarser level's finished sites).  or_df_sweep:
+ * step 3 alone, in place.  or_df_field: signed distance (double) from each sample to its
  * site triangle.  or_tri_box_overlap and or_tri_dist2_f expose the single
  * precision triangle/box test and point/triangle squared distance. */
 void or_df_sites(const or_bvh* b, const or_grid* g, const int32_t* coarse, const or_grid* gc, int32_t stage,

@@ -38,7 +38,7 @@ EXPORTS = ("rt_scene_build", "rt_scene_info_get", "rt_scene_destroy", "rt_sdf_cr
            "rt_sdf_prepare", "rt_sdf_bake", "rt_trace_bvh", "rt_trace_sdf", "rt_trace_combined",
            "rt_trace_combined_counted", "rt_trace_combined_timed", "rt_trace_combined_noalloc",
            "rt_trace_combined_backward", "rt_trace_batches", "rt_set_tuning", "rt_get_tuning",
-           "rt_cascade_create", "rt_cascade_recenter", "rt_cascade_level", "rt_sdf_sites", "rt_trace_combined_host", "rt_scene_export", "rt_gather_probe", "rt_last_error",
+           "rt_cascade_create", "rt_cascade_recenter", "rt_cascade_level", "rt_sdf_sites", "rt_trace_combined_host", "rt_scene_export", "rt_last_error",
            "rt_version")
 
 
@@ -117,7 +117,6 @@ def lib() -> ctypes.CDLL:
             "rt_sdf_sites": [P, P, i32, P, P],
             "rt_trace_combined_host": [P, P, P, i64, P, P, P, P, i32, P],
             "rt_scene_export": [P, P, P, P],
-            "rt_gather_probe": [P, i64, i32, i32, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -212,22 +211,6 @@ def rt_scene_export(scene: Scene, stream=None):
     _check(lib().rt_scene_export(scene.handle, _dptr(nodes) if nodes.numel() else None, _dptr(tris),
                                  _stream(stream)))
     return nodes, tris
-
-
-def rt_gather_probe(cells: torch.Tensor, steps: int, blocks: int, out: torch.Tensor | None = None,
-                    stream=None) -> torch.Tensor:
-    """Chains of dependent random 32-byte gathers over `cells` (CUDA, 32-byte
-    aligned, a power-of-two number of 32-byte cells); returns each chain's sum
-    (blocks * 128 float32).  Measurement of the memory system, not a query."""
-    if not cells.is_cuda or not cells.is_contiguous():
-        raise ValueError("cells must be a contiguous CUDA tensor")
-    nbytes = cells.numel() * cells.element_size()
-    if nbytes % 32:
-        raise ValueError("cells must hold a whole number of 32-byte cells")
-    if out is None:
-        out = torch.empty(blocks * 128, dtype=torch.float32, device=cells.device)
-    _check(lib().rt_gather_probe(_dptr(cells), nbytes // 32, int(steps), int(blocks), _dptr(out), _stream(stream)))
-    return out
 
 
 def rt_scene_build(verts: torch.Tensor, tris: torch.Tensor, stream=None) -> Scene:

@@ -1,4 +1,6 @@
-"""Build the device library in-tree: csrc/*.cu -> _build/librt_gb300.so (sm_103a only).
+"""Build the device libraries in-tree (sm_103a only): the query library
+csrc/*.cu -> _build/librt_gb300.so, and the measurement probes
+csrc/probe/mem_probe.cu -> _build/libmem_probe.so.
 
 Translation units compile in parallel; only changed ones are rebuilt.  Run as
 `python -m paper_2305_07253_gb300.build` or through `__graft_entry__.build()`.
@@ -17,7 +19,9 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librt_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["rt_api.cu", "rt_scene.cu", "rt_treelet.cu", "rt_wide.cu", "rt_bake.cu", "rt_dfgen.cu", "rt_trace.cu",
-           "rt_backward.cu", "rt_batch.cu", "rt_probe.cu"]
+           "rt_backward.cu", "rt_batch.cu"]
+PROBE_SOURCE = os.path.join("probe", "mem_probe.cu")
+PROBE_LIB = os.path.join(OUT, "libmem_probe.so")
 HEADERS = ["rt_internal.cuh", "rt_trace_dev.cuh", "rt_bake_dev.cuh"]
 
 NVCC_FLAGS = [
@@ -36,12 +40,13 @@ def nvcc() -> str:
 
 
 def _deps_mtime() -> float:
-    files = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "rt_api.h"), __file__]
+    files = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "rt_api.h"),
+                                                        os.path.join(INCLUDE, "mem_probe.h"), __file__]
     return max(os.path.getmtime(f) for f in files)
 
 
 def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(OUT, src.replace(".cu", ".o"))
+    obj = os.path.join(OUT, os.path.basename(src).replace(".cu", ".o"))
     s = os.path.join(CSRC, src)
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(s), _deps_mtime()):
         return obj
@@ -55,21 +60,26 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+def _link(lib: str, objs: list, verbose: bool) -> str:
+    if os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(o) for o in objs):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(verbose: bool = False) -> str:
+    os.makedirs(OUT, exist_ok=True)
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES + [PROBE_SOURCE]))
+    _link(PROBE_LIB, objs[-1:], verbose)
+    return _link(LIB, objs[:-1], verbose)
 
 
 if __name__ == "__main__":

@@ -476,11 +476,12 @@ unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
 // Steps 1..stage for the levels `lv[0..nl)` (0 for a single grid), given in
 // the order they are built (coarsest first).  All levels are voxelised in one
-// pass over the triangles; then each level is seeded (on a cascade also from
-// the next coarser level's sites in `jfa`) and flooded, leaving its sites in
-// `jfa`; the final sites go to `out` after the sweeps of all levels, which
-// run together.  jfa, out: one int32 per sample of every level (indexed by
-// level), device.
+// pass over the triangles (a level's voxel candidates do not depend on the
+// other levels); then each level in turn is seeded (on a cascade also from the
+// next coarser level's finished sites in `jfa`), flooded and swept, leaving its
+// sites in `jfa` before the next finer level reads them.  The sites of every
+// listed level also go to `out`.  jfa, out: one int32 per sample of every
+// level (indexed by level), device.
 rt_status df_build(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t stage, int32_t* jfa,
                    int32_t* out, cudaStream_t s)
 {
@@ -524,7 +525,7 @@ rt_status df_build(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl,
         k_df_vox_small<<<blocks_for(T.n), kBlock, 0, s>>>(vp, T, big, n_big);
         k_df_vox_big<<<(unsigned)(sms > 0 ? sms * 4 : 512), kBlock, 0, s>>>(vp, T, big, n_big);
     }
-    // 2. per level, coarsest first: seeding and jump flooding
+    // 2.-3. per level, coarsest first: seeding, jump flooding, the six sweeps
     for (int l = 0; l < nl && st == RT_OK; ++l) {
         const int k = lv[l];
         int32_t* sites = jfa + (int64_t)k * per;
@@ -555,26 +556,22 @@ rt_status df_build(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl,
                 if (e != cudaSuccess) st = rt_cuda_fail(e, "cudaMemcpyAsync");
             }
         }
+        if (st == RT_OK && stage >= 3) {
+            for (int axis = 0; axis < 3; ++axis) {
+                const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
+                SweepPass sp;
+                memset(&sp, 0, sizeof(sp));
+                sp.count = 1;
+                sp.g[0] = g;
+                sp.sites[0] = sites;
+                sp.first_line[1] = (int64_t)g.n[oa] * g.n[ob];
+                for (int dir = 1; dir >= -1; dir -= 2)
+                    k_df_sweep<<<(unsigned)((sp.first_line[1] + 63) / 64), 64, 0, s>>>(sp, T, axis, dir);
+            }
+        }
         if (st == RT_OK && out != jfa) {
             e = cudaMemcpyAsync(out + (int64_t)k * per, sites, (size_t)g.count * 4, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) st = rt_cuda_fail(e, "cudaMemcpyAsync");
-        }
-    }
-    // 3. the sweeps of all listed levels, six launches
-    if (st == RT_OK && stage >= 3) {
-        for (int axis = 0; axis < 3; ++axis) {
-            const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
-            SweepPass sp;
-            memset(&sp, 0, sizeof(sp));
-            sp.count = nl;
-            for (int l = 0; l < nl; ++l) {
-                sp.g[l] = df_grid(sdf, lv[l]);
-                sp.sites[l] = out + (int64_t)lv[l] * per;
-                sp.first_line[l + 1] = sp.first_line[l] + (int64_t)sp.g[l].n[oa] * sp.g[l].n[ob];
-            }
-            const int64_t lines = sp.first_line[nl];
-            for (int dir = 1; dir >= -1; dir -= 2)
-                k_df_sweep<<<(unsigned)((lines + 63) / 64), 64, 0, s>>>(sp, T, axis, dir);
         }
     }
     if (st == RT_OK) {
@@ -605,8 +602,9 @@ rt_status field_values(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int
 
 }  // namespace
 
-// Sites of every sample after step `stage` (1..3), coarsest cascade level first
-// (each level seeded also from the next coarser level's flooded sites).
+// Sites of every sample after step `stage` (1..3), cascade levels one at a
+// time, coarsest first (each seeded also from the next coarser level's sites
+// after its steps 1..stage).
 // d_sites holds levels * n^3 (or n0 n1 n2) entries.
 rt_status rt_launch_df_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t stage, int32_t* d_sites, cudaStream_t s)
 {
@@ -623,8 +621,8 @@ rt_status rt_launch_df_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t stag
 }
 
 // The listed levels (all of them for a full build; the moved ones of a rolling
-// update), coarsest first: sites into `jfa_store` (kept by the handle: the
-// seeds of finer levels later), field values from the swept sites.
+// update), coarsest first: finished sites into `jfa_store` (kept by the
+// handle: the seeds of finer levels later), field values from them.
 rt_status rt_launch_df_levels(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl, int32_t* jfa_store,
                               cudaStream_t s)
 {

@@ -84,7 +84,7 @@ struct rt_sdf {
     void* scratch;      // one level, for rt_cascade_recenter
     int64_t scratch_bytes;
     int32_t bake_method;  // method of the last rt_sdf_bake (RT_BAKE_JFA: sites kept)
-    int32_t* sites;       // flooded site of every sample after a field build (RT_BAKE_JFA): the
+    int32_t* sites;       // finished site of every sample after a field build (RT_BAKE_JFA): the
                           // seeds of finer levels when a rolling update rebuilds them
     int64_t sites_count;
 };

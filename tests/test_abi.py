@@ -120,16 +120,66 @@ def test_argument_errors_without_a_gpu(rtlib):
     rtlib.rt_sdf_destroy(out)
 
 
-def test_gather_probe_arguments_without_a_gpu(rtlib):
-    rtlib.rt_last_error.restype = ctypes.c_char_p
-    f = rtlib.rt_gather_probe
-    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+PROBE_HEADER = os.path.join(ROOT, "include", "mem_probe.h")
+
+
+def _declared_probe():
+    src = re.sub(r"/\*.*?\*/", "", open(PROBE_HEADER).read(), flags=re.S)
+    return sorted(set(re.findall(r"\b(mp_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def probelib(rtlib):
+    from paper_2305_07253_gb300 import mem_probe
+    return mem_probe.lib()
+
+
+def test_probe_library_exports_every_declared_symbol(probelib):
+    from paper_2305_07253_gb300 import mem_probe
+    names = _declared_probe()
+    assert names == sorted(mem_probe.EXPORTS)
+    assert not [n for n in names if not hasattr(probelib, n)]
+
+
+def test_query_library_exports_no_probe(rtlib):
+    """The memory-system probes live in their own library, not in the query ABI."""
+    assert not [n for n in _declared() if "probe" in n]
+    assert not hasattr(rtlib, "rt_gather_probe")
+
+
+def test_probe_arguments_without_a_gpu(probelib):
+    L = probelib
     buf, out = ctypes.c_void_p(4096), ctypes.c_void_p(8192)
-    assert f(None, 16, 4, 1, out, None) == 1 and b"null" in rtlib.rt_last_error()
-    assert f(ctypes.c_void_p(4112), 16, 4, 1, out, None) == 1 and b"32-byte" in rtlib.rt_last_error()
-    assert f(buf, 24, 4, 1, out, None) == 1 and b"power of two" in rtlib.rt_last_error()
-    assert f(buf, 16, 0, 1, out, None) == 1 and b"steps" in rtlib.rt_last_error()
-    assert f(buf, 16, 4, 0, out, None) == 1 and b"blocks" in rtlib.rt_last_error()
+    f = L.mp_random_gather
+    assert f(None, 16, 4, 1, out, None) == 1 and b"null" in L.mp_last_error()
+    assert f(ctypes.c_void_p(4112), 16, 4, 1, out, None) == 1 and b"32-byte" in L.mp_last_error()
+    assert f(buf, 24, 4, 1, out, None) == 1 and b"power of two" in L.mp_last_error()
+    assert f(buf, 16, 0, 1, out, None) == 1 and b"steps" in L.mp_last_error()
+    assert f(buf, 16, 4, 0, out, None) == 1 and b"blocks" in L.mp_last_error()
+    g = L.mp_l2_read
+    assert g(ctypes.c_void_p(4100), 4096, 1, 1, out, None) == 1 and b"16-byte" in L.mp_last_error()
+    assert g(buf, 4100, 1, 1, out, None) == 1 and b"multiple of 16" in L.mp_last_error()
+    assert g(buf, 4096, 0, 1, out, None) == 1 and b"reps" in L.mp_last_error()
+    h = L.mp_l1_read
+    assert h(buf, 5000, 1, 1, out, None) == 1 and b"window" in L.mp_last_error()
+    assert h(buf, 4096, 1, 0, out, None) == 1 and b"blocks" in L.mp_last_error()
+
+
+def test_probe_binding_rejects_a_short_or_wrong_output():
+    """The binding checks a caller's output tensor before the library is asked
+    to write blocks x threads values into it."""
+    import torch
+
+    from paper_2305_07253_gb300 import mem_probe
+    cells = torch.zeros(64, dtype=torch.float32)  # CPU tensor: refused before any device call
+    with pytest.raises(ValueError):
+        mem_probe.random_gather(cells, 4, 1)
+    with pytest.raises(ValueError):
+        mem_probe._out(torch.zeros(10, dtype=torch.float32), 128, torch.device("cpu"))
+    with pytest.raises(ValueError):
+        mem_probe._out(torch.zeros(256, dtype=torch.float64), 128, torch.device("cpu"))
+    with pytest.raises(ValueError):
+        mem_probe._out(torch.zeros(256, dtype=torch.float32)[::2], 128, torch.device("cpu"))
 
 
 def test_bad_split_params_rejected(rtlib):
