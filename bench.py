@@ -1026,6 +1026,11 @@ def run_cascade(args):
         d = ao - ref_ao
         out["ao"][name] = {"ms": ms, "mean_abs_dAO": float(d.abs().mean()), "mean_dAO": float(d.mean()),
                            "share_off_0.1": float((d.abs() > 0.1).float().mean())}
+    # the split multiplier on the combined-mode cascade (Section 3: t_1 from the
+    # voxel at the ray's start point), and the same split with the finest voxel
+    # h0 instead: a query whose start point lies in level k is traced with
+    # m * 2^-k, so that t_1 = t_min + m h0 exactly (h_k = h0 2^k)
+    out["m_sweep"] = cascade_m_sweep(rq, scene, cas, gi, ao_rays, hits, ao_hits, K)
     # rolling updates: the camera walks one finest voxel per frame along x, y and z
     roll = {}
     for (name, mname), (g, sdf) in cas.items():
@@ -1058,6 +1063,75 @@ def run_cascade(args):
                        "gi_rays": int(gi.shape[0]), "ao_rays": int(ao_rays.shape[0]), "m": M_MIDDLE},
             "cascade": out}
     print(json.dumps(line), flush=True)
+
+
+def _start_levels(rq, sdf, rays):
+    """Cascade level holding each query's start point o + t_min d (the finest
+    whose closed box holds it; the coarsest otherwise), on the host."""
+    r = rays.cpu().numpy().astype(np.float64)
+    p = r[:, 0:3] + r[:, 3:4] * r[:, 4:7]
+    lv = np.full(r.shape[0], sdf.levels - 1, dtype=np.int64)
+    for k in range(sdf.levels - 2, -1, -1):
+        lo, hi = (np.asarray(b, dtype=np.float64) for b in rq.rt_cascade_box(sdf, k))
+        lv = np.where(np.all((p >= lo) & (p <= hi), axis=1), k, lv)
+    return lv
+
+
+def cascade_m_sweep(rq, scene, cas, gi, ao_rays, hits, ao_hits, K, spp=16):
+    """Combined query on the 5 x 64^3 cascade for m in {0.5, 1, 2, 4}: GI and
+    AO (t_ao 2 m) time and error against triangles only, with t_1 from the voxel
+    at the start point (the paper's rule) and from the finest voxel."""
+    import torch
+    res = {}
+    p_bvh = rq.split_params(mode=rq.MODE_BVH)
+    ref = {}
+    for name, rays, h in (("gi", gi, hits), ("ao", ao_rays, ao_hits)):
+        ms = _time_ms(lambda: rq.rt_trace_combined(scene, None, rays, p_bvh, h), K)
+        f = rq.hit_fields(h)
+        ref[name] = (f["t"].double().clone(), (f["tracer"] > 0).clone())
+        res[f"triangles_only/{name}_ms"] = ms
+    for mname in ("exact", "jfa"):
+        sdf = cas[("combined", mname)][1]
+        groups = {}
+        for name, rays in (("gi", gi), ("ao", ao_rays)):
+            lv = _start_levels(rq, sdf, rays)
+            order = np.argsort(lv, kind="stable")
+            idx = torch.from_numpy(order).to(rays.device)
+            bounds = np.searchsorted(lv[order], np.arange(sdf.levels + 1))
+            groups[name] = (rays[idx].contiguous(), idx, bounds)
+        for rule in ("start_voxel", "finest_voxel"):
+            for m in (0.5, 1.0, 2.0, 4.0):
+                for name, rays, h in (("gi", gi, hits), ("ao", ao_rays, ao_hits)):
+                    if rule == "start_voxel":
+                        prm = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
+                        fn = lambda: rq.rt_trace_combined(scene, sdf, rays, prm, h)  # noqa: E731
+                        fn()
+                        hh = h
+                    else:
+                        rs, idx, bounds = groups[name]
+                        out_h = torch.empty_like(h)
+                        specs = [(rs[bounds[k]:bounds[k + 1]], rq.split_params(mode=rq.MODE_SPLIT1, m_near=m * 2.0 ** -k),
+                                  out_h[bounds[k]:bounds[k + 1]]) for k in range(sdf.levels) if bounds[k + 1] > bounds[k]]
+                        fn = lambda: rq.rt_trace_batches(scene, sdf, specs)  # noqa: E731
+                        fn()
+                        hh = torch.empty_like(h)
+                        hh[idx] = out_h
+                    ms = _time_ms(fn, K)
+                    f = rq.hit_fields(hh)
+                    e = {"ms": ms, "speedup_vs_triangles": res[f"triangles_only/{name}_ms"] / ms}
+                    if name == "gi":
+                        t, rt = f["t"].double(), ref["gi"][0]
+                        both = torch.isfinite(t) & torch.isfinite(rt)
+                        rel = ((t - rt).abs() / rt.clamp(min=1e-6))[both]
+                        e["mean_rel_dt"] = float(rel.mean())
+                    else:
+                        ao = 1.0 - (f["tracer"] > 0).double().reshape(-1, spp).mean(dim=1)
+                        ao_ref = 1.0 - ref["ao"][1].double().reshape(-1, spp).mean(dim=1)
+                        d = ao - ao_ref
+                        e["mean_abs_dAO"] = float(d.abs().mean())
+                        e["share_off_0.1"] = float((d.abs() > 0.1).double().mean())
+                    res[f"{mname}/{rule}/m={m}/{name}"] = e
+    return res
 
 
 def _write_png(path, img):
