@@ -414,6 +414,109 @@ __global__ void k_df_sweep(const SweepPass sp, const Tris T, int axis, int dir)
     }
 }
 
+// Both sweeps of one axis for one level: a thread takes one grid line, loads it
+// into shared memory, sweeps it in the + direction and then in the - direction
+// (lines of one axis are independent, so this equals all + sweeps followed by
+// all - sweeps), and writes it back.  The line is stored interleaved
+// (sample q of thread t at q * blockDim + t), so a warp's accesses to one q
+// fall in different banks.  The site carried along the line keeps its triangle
+// in registers: a step loads only the triangle of its own sample's site, and
+// only when the two sites differ.  Same operations, same order, same sites as
+// k_df_sweep.
+constexpr int kLineMax = 1024;  // longest line swept in shared memory
+
+// One step of a sweep at sample q.  CA/CB/CC hold the triangle of the sample's
+// own site `cur` (loaded one step ahead by the caller); PA/PB/PC the carried
+// site's, valid when prev_loaded.
+__device__ __forceinline__ void sweep_step(const DfGrid& g, const Tris& T, int64_t ii[3], int axis, int64_t q,
+                                           int32_t cur, const float CA[3], const float CB[3], const float CC[3],
+                                           int32_t& prev, float PA[3], float PB[3], float PC[3], bool& prev_loaded,
+                                           int32_t* slot)
+{
+    if (prev >= 0 && prev != cur) {
+        ii[axis] = q;
+        float p[3];
+        df_pos(g, ii[0], ii[1], ii[2], p);
+        const float cd2 = cur >= 0 ? tri_d2_rn(p, CA, CB, CC) : 0.f;
+        if (!prev_loaded) {
+            tri_verts(T, prev, PA, PB, PC);
+            prev_loaded = true;
+        }
+        const float d2 = tri_d2_rn(p, PA, PB, PC);
+        if (cur < 0 || d2 < cd2 || (d2 == cd2 && prev < cur)) {
+            cur = prev;  // the carried site wins and stays carried
+            *slot = cur;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {  // the sample's own site is carried on
+                PA[k] = CA[k];
+                PB[k] = CB[k];
+                PC[k] = CC[k];
+            }
+        }
+    } else if (cur != prev) {
+        prev_loaded = false;  // a new carried site whose triangle is not loaded yet
+    }
+    prev = cur;
+}
+
+// the triangle of site t (nothing for t < 0)
+__device__ __forceinline__ void site_verts(const Tris& T, int32_t t, float A[3], float B[3], float C[3])
+{
+    if (t >= 0) tri_verts(T, t, A, B, C);
+}
+
+// one direction of a line's sweep: samples q0, q0 + dq, ... (len - 1 of them),
+// carrying from q0 - dq; the next sample's triangle is loaded a step ahead
+__device__ __forceinline__ void sweep_dir(const DfGrid& g, const Tris& T, int64_t ii[3], int axis, int32_t* L,
+                                          int64_t B, int64_t q0, int64_t dq, int64_t count)
+{
+    float PA[3], PB[3], PC[3], CA[3], CB[3], CC[3];
+    bool prev_loaded = false;
+    int32_t prev = L[(q0 - dq) * B];
+    int32_t cur = L[q0 * B];
+    site_verts(T, cur, CA, CB, CC);
+    for (int64_t k = 0; k < count; ++k) {
+        const int64_t q = q0 + k * dq;
+        int32_t nxt = -1;
+        float NA[3], NB[3], NC[3];
+        if (k + 1 < count) {
+            nxt = L[(q + dq) * B];
+            site_verts(T, nxt, NA, NB, NC);
+        }
+        sweep_step(g, T, ii, axis, q, cur, CA, CB, CC, prev, PA, PB, PC, prev_loaded, L + q * B);
+        cur = nxt;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            CA[c] = NA[c];
+            CB[c] = NB[c];
+            CC[c] = NC[c];
+        }
+    }
+}
+
+__global__ void k_df_sweep_line(const DfGrid g, const Tris T, int32_t* sites, int axis)
+{
+    extern __shared__ int32_t s_line[];
+    const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
+    const int64_t n[3] = {g.n[0], g.n[1], g.n[2]};
+    const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= n[oa] * n[ob]) return;
+    const int64_t stride[3] = {1, n[0], n[0] * n[1]};
+    int64_t ii[3];
+    ii[oa] = line % n[oa];
+    ii[ob] = line / n[oa];
+    ii[axis] = 0;
+    const int64_t base = ii[oa] * stride[oa] + ii[ob] * stride[ob];
+    const int64_t len = n[axis];
+    const int64_t B = blockDim.x;
+    int32_t* L = s_line + threadIdx.x;
+    for (int64_t q = 0; q < len; ++q) L[q * B] = sites[base + q * stride[axis]];
+    sweep_dir(g, T, ii, axis, L, B, 1, 1, len - 1);         // + direction: samples 1 .. len-1
+    sweep_dir(g, T, ii, axis, L, B, len - 2, -1, len - 1);  // - direction: samples len-2 .. 0
+    for (int64_t q = 0; q < len; ++q) sites[base + q * stride[axis]] = L[q * B];
+}
+
 // signed distance to the site triangle (the exact bake's closest point and sign)
 __global__ void k_df_field(const DfGrid g, const Tris T, const float4* pn, const int32_t* sites, void* grid,
                            int32_t f16)
@@ -559,14 +662,30 @@ rt_status df_build(const rt_scene* sc, const rt_sdf* sdf, const int* lv, int nl,
         if (st == RT_OK && stage >= 3) {
             for (int axis = 0; axis < 3; ++axis) {
                 const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
-                SweepPass sp;
-                memset(&sp, 0, sizeof(sp));
-                sp.count = 1;
-                sp.g[0] = g;
-                sp.sites[0] = sites;
-                sp.first_line[1] = (int64_t)g.n[oa] * g.n[ob];
-                for (int dir = 1; dir >= -1; dir -= 2)
-                    k_df_sweep<<<(unsigned)((sp.first_line[1] + 63) / 64), 64, 0, s>>>(sp, T, axis, dir);
+                const int64_t lines = (int64_t)g.n[oa] * g.n[ob];
+                if (g.n[axis] <= kLineMax) {
+                    const int threads = g.n[axis] <= 512 ? 64 : 32;
+                    const size_t smem = (size_t)threads * g.n[axis] * sizeof(int32_t);
+                    if (smem > 48 * 1024) {
+                        e = cudaFuncSetAttribute(k_df_sweep_line, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+                        if (e != cudaSuccess) {
+                            st = rt_cuda_fail(e, "cudaFuncSetAttribute");
+                            break;
+                        }
+                    }
+                    k_df_sweep_line<<<(unsigned)((lines + threads - 1) / threads), threads, smem, s>>>(g, T, sites,
+                                                                                                      axis);
+                } else {
+                    SweepPass sp;
+                    memset(&sp, 0, sizeof(sp));
+                    sp.count = 1;
+                    sp.g[0] = g;
+                    sp.sites[0] = sites;
+                    sp.first_line[1] = lines;
+                    for (int dir = 1; dir >= -1; dir -= 2)
+                        k_df_sweep<<<(unsigned)((lines + 63) / 64), 64, 0, s>>>(sp, T, axis, dir);
+                }
             }
         }
         if (st == RT_OK && out != jfa) {
