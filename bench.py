@@ -667,6 +667,17 @@ def extra_batching(rq, scene, sdf, grid, frames_np, reps=2, tune=True):
         best, results = autotune.autotune(lambda: rq.rt_trace_batches(scene, sdf, f0), reps=2, warmup=1)
         top = sorted(([r[1], r[0]] for r in results), key=lambda x: x[0])[:5]
         forms["batched_autotuned"] = _time_ms(batched, reps, warm=1)
+    # the autotuner's pick for each batch kind of the first frame alone (one call per batch)
+    per_kind = {}
+    if tune:
+        for name, rd, p, h in frames[0]:
+            rq.rt_set_tuning(prev)
+            ms_default = _time_ms(lambda: rq.rt_trace_combined(scene, sdf, rd, p, h), 3, warm=1)
+            kbest, kres = autotune.autotune(lambda: rq.rt_trace_combined(scene, sdf, rd, p, h), reps=2, warmup=1,
+                                            apply=False)
+            per_kind[name] = {"rays": int(rd.shape[0]), "default_ms": ms_default,
+                              "autotuned_ms": min(r[1] for r in kres), "pick": kbest}
+        rq.rt_set_tuning(**best)
     graphs = []
     st = torch.cuda.Stream()
     st.wait_stream(torch.cuda.current_stream())
@@ -691,7 +702,8 @@ def extra_batching(rq, scene, sdf, grid, frames_np, reps=2, tune=True):
     rq.rt_set_tuning(prev)
     out = {"frames": len(frames), "rays_total": int(n_total), "batch_sizes_per_frame": sizes,
            "forms": {k: {"ms_total": v, "value": rate(v)} for k, v in forms.items()},
-           "tuning_default": default, "tuning_autotuned": best, "autotune_top5": top}
+           "tuning_default": default, "tuning_autotuned": best, "autotune_top5": top,
+           "autotune_per_kind": per_kind}
     out["persistent_graph_beats_per_batch"] = bool(forms["batched_cuda_graph"] < forms["one_call_per_batch"])
     out["f16_beats_per_batch"] = bool(forms["batched_f16_grid"] < forms["one_call_per_batch"])
     del g16, sdf16, frames
