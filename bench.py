@@ -287,20 +287,25 @@ def run_ours(args):
 
     def stage_bytes(name, stage):
         """Algorithmic bytes one launch of `stage` moves (reads of rays, nodes, triangles,
-        grid cells and queue entries; writes of hit records and queue entries)."""
+        grid cells and queue entries; writes of hit records and queue entries).  The query
+        order (one kernel) reads each query's origin (16 B) and writes its 4-byte entry of
+        the order, which the first stage reads."""
         nodes, tris, steps, _ = counts[name]
         n_bvh_hits = outcome[name]["bvh_hits"]
+        q_in = 4 * n_rays if "order" in stage_ms.get(name, {}) else 0
+        if stage == "order":
+            return (16 + 4) * n_rays
         if stage == "all":
-            return 32 * n_rays + 24 * n_rays + 64 * nodes + 48 * tris + step_bytes * steps
+            return 32 * n_rays + 24 * n_rays + 64 * nodes + 48 * tris + step_bytes * steps + q_in
         if stage == "bvh_full":
-            return 32 * n_rays + 24 * n_rays + 64 * nodes + 48 * tris
+            return 32 * n_rays + 24 * n_rays + 64 * nodes + 48 * tris + q_in
         if stage == "field_full":
-            return 32 * n_rays + 24 * n_rays + step_bytes * steps
+            return 32 * n_rays + 24 * n_rays + step_bytes * steps + q_in
         if stage == "bvh_near":  # all rays in; hits written; the rest queued
             fwd = n_rays - n_bvh_hits
-            return 32 * n_rays + 64 * nodes + 48 * tris + 24 * n_bvh_hits + 8 * fwd
+            return 32 * n_rays + 64 * nodes + 48 * tris + 24 * n_bvh_hits + 8 * fwd + q_in
         if stage == "field_split" and name == "sdf":  # m = 0: no triangle stage, every ray in
-            return 32 * n_rays + step_bytes * steps + 24 * n_rays
+            return 32 * n_rays + step_bytes * steps + 24 * n_rays + q_in
         if stage == "field_split":  # queued rays in; every record written here
             fwd = n_rays - n_bvh_hits
             return (8 + 32) * fwd + step_bytes * steps + 24 * fwd
@@ -365,7 +370,8 @@ def run_ours(args):
     caches = cache_ceilings()
     kernel_names = {"bvh_near": "k_stage_bvh (near triangle sub-interval)",
                     "field_split": "k_stage_field (distance-field sub-interval)",
-                    "bvh_full": "k_stage_bvh", "field_full": "k_stage_field", "all": "k_trace"}
+                    "bvh_full": "k_stage_bvh", "field_full": "k_stage_field", "all": "k_trace",
+                    "order": "k_order_local (query order)"}
     stages = {name: {st: {"ms": ms, "algorithmic_bytes": stage_bytes(name, st),
                           "GBps": stage_bytes(name, st) / (ms * 1e-3) / 1e9,
                           "frac_of_hbm": stage_bytes(name, st) / (ms * 1e-3) / 1e9 / peak,

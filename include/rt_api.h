@@ -325,25 +325,28 @@ rt_status rt_trace_combined_counted(const rt_scene* scene, const rt_sdf* sdf, co
                                     unsigned long long* d_counters, void* stream);
 
 /* Same as rt_trace_combined, and also reports how long each kernel of the
- * call ran: stage_ms[k] for the k-th launch (at most 3: one per sub-interval
- * kind with the wavefront kernels, 1 with the simple kernel), *n_stages the
- * number of launches, stage_kind[k] RT_STAGE_* (nullable).  Times come from
- * CUDA events recorded on `stream` between the launches; the call
- * synchronises `stream`.  Used to measure per-kernel throughput. */
+ * call ran: stage_ms[k] for the k-th part (at most 4: the query order when
+ * rt_tuning.order_bits > 0 and n >= 64, then one launch per
+ * sub-interval kind with the wavefront kernels, or the one launch of the
+ * simple kernel), *n_stages the number of parts, stage_kind[k] RT_STAGE_*
+ * (nullable).  stage_ms and stage_kind hold 4 entries.  Times come from CUDA
+ * events recorded on `stream` between the launches; the call synchronises
+ * `stream`.  Used to measure per-kernel throughput. */
 enum { RT_STAGE_ALL = 0, RT_STAGE_BVH_FULL = 1, RT_STAGE_BVH_NEAR = 2, RT_STAGE_BVH_FAR = 3,
-       RT_STAGE_FIELD_FULL = 4, RT_STAGE_FIELD_SPLIT = 5 };
+       RT_STAGE_FIELD_FULL = 4, RT_STAGE_FIELD_SPLIT = 5, RT_STAGE_ORDER = 6 };
 rt_status rt_trace_combined_timed(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
-                                  const rt_split_params* params, rt_hit* d_hits, float stage_ms[3],
-                                  int32_t stage_kind[3], int32_t* n_stages, void* stream);
+                                  const rt_split_params* params, rt_hit* d_hits, float stage_ms[4],
+                                  int32_t stage_kind[4], int32_t* n_stages, void* stream);
 
 /* The combined query of rt_trace_combined, for callers that cannot allocate
  * device memory during the call: for example a renderer whose frame loop
  * forbids allocation, or a host that hands the library a fixed device-memory
  * budget and must not see it grow.  rt_trace_combined takes its per-call
- * scratch (work counters and two ray queues) from a memory pool; this entry
- * point allocates nothing and uses one fixed array compiled into the library
- * instead.  The paper has no counterpart: this is a deployment variant.
- *   - At most 1,048,576 queries per call (the array holds 16 MiB + 256 bytes
+ * scratch (work counters, the query order and two ray queues) from a memory
+ * pool; this entry point allocates nothing and uses one fixed array compiled
+ * into the library instead.  The paper has no counterpart: this is a
+ * deployment variant.
+ *   - At most 1,048,576 queries per call (the array holds 20 MiB + 256 bytes
  *     and every GPU that loads the library keeps it until the process ends);
  *     a larger n is rejected with RT_ERR_INVALID_ARG before any work.
  *   - The first call on a device looks up the array's device address
@@ -354,7 +357,7 @@ rt_status rt_trace_combined_timed(const rt_scene* scene, const rt_sdf* sdf, cons
  *     results: serialise them, e.g. on one stream.  The counters are cleared
  *     on `stream` at the start of every call.
  *   - Always runs the wavefront stage kernels (the tuning's block, residency,
- *     refill and layout apply); results equal rt_trace_combined's.
+ *     refill, layout and query order apply); results equal rt_trace_combined's.
  *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
 rt_status rt_trace_combined_noalloc(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
                                     const rt_split_params* params, rt_hit* d_hits, void* stream);
@@ -428,6 +431,18 @@ rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, c
  *                 exists; RT_LAYOUT_PLAIN: always read the plain grid;
  *                 RT_LAYOUT_PAIRS: the copy of x-neighbour pairs (4 loads a
  *                 step, twice the grid's size) when it exists
+ *   order_bits    0: the first kernel takes the queries in input order.
+ *                 1..5 (default 4): it takes each window of 1024
+ *                 consecutive queries sorted by the cell that holds the
+ *                 query's origin, in a 2^b x 2^b x 2^b lattice over the
+ *                 scene's box (the grid's box without a scene), cells in
+ *                 Morton order, equal cells in input order; windows keep
+ *                 their order.  A warp's queries then start in one region and
+ *                 read the same nodes, triangles and cells.  It pays when
+ *                 input neighbours start at different depths (a screen tile
+ *                 over several surfaces); it costs one kernel per call that
+ *                 reads every ray and writes 4 bytes per query.  Calls with
+ *                 fewer than 64 queries are not ordered.
  * Results do not depend on the tuning. */
 typedef struct {
     int32_t kernel;
@@ -437,6 +452,7 @@ typedef struct {
     int32_t grid_layout;
     int32_t refill_min_field;
     int32_t bvh_width;
+    int32_t order_bits;
 } rt_tuning;
 
 enum { RT_KERNEL_WAVEFRONT = 0, RT_KERNEL_SIMPLE = 1, RT_KERNEL_AUTO = 2 };

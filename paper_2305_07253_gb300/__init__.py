@@ -57,7 +57,7 @@ class rt_split_params(ctypes.Structure):
 class rt_tuning(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("refill_min", ctypes.c_int32), ("grid_layout", ctypes.c_int32), ("refill_min_field", ctypes.c_int32),
-                ("bvh_width", ctypes.c_int32)]
+                ("bvh_width", ctypes.c_int32), ("order_bits", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -397,15 +397,15 @@ def rt_trace_batches(scene: Scene | None, sdf: Sdf | None, batches, stream=None)
     return outs
 
 
-STAGE_NAMES = {0: "all", 1: "bvh_full", 2: "bvh_near", 3: "bvh_far", 4: "field_full", 5: "field_split"}
+STAGE_NAMES = {0: "all", 1: "bvh_full", 2: "bvh_near", 3: "bvh_far", 4: "field_full", 5: "field_split", 6: "order"}
 
 
 def rt_trace_combined_timed(scene: Scene | None, sdf: Sdf | None, rays: torch.Tensor, params: rt_split_params,
                             hits: torch.Tensor | None = None, stream=None):
     """Returns (hits, [(stage name, ms), ...]) with the device time of each kernel launch."""
     hits = _rays_hits(rays, hits)
-    ms = (ctypes.c_float * 3)()
-    kinds = (ctypes.c_int32 * 3)()
+    ms = (ctypes.c_float * 4)()
+    kinds = (ctypes.c_int32 * 4)()
     n = ctypes.c_int32()
     _check(lib().rt_trace_combined_timed(scene.handle if scene else None, sdf.handle if sdf else None, _dptr(rays),
                                          rays.shape[0], ctypes.byref(params), _dptr(hits), ms, kinds,

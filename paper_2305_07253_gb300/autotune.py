@@ -2,8 +2,9 @@
 
 The candidates cover the knobs of rt_set_tuning: kernel (wavefront stages with
 per-lane refill, or one thread per query), threads per block, resident blocks
-per SM, the refill threshold, and the grid layout (cell-corner copy or plain
-grid).  Results never depend on the tuning, only the time does.
+per SM, the refill threshold, the grid layout (cell-corner copy or plain
+grid), the tree width, and the query order (bits of the origin lattice, or
+none).  Results never depend on the tuning, only the time does.
 """
 from __future__ import annotations
 
@@ -26,6 +27,13 @@ def default_space() -> list[dict]:
     for width, block, layout in itertools.product((8, 2), (64, 128, 256), (LAYOUT_CELLS, LAYOUT_PLAIN)):
         space.append(dict(kernel=KERNEL_SIMPLE, block=block, refill_min=16, refill_min_field=16, blocks_per_sm=0,
                           grid_layout=layout, bvh_width=width))
+    # the query order on the default launch shape of each kernel (the entries
+    # above keep the default order, 4 bits)
+    for kernel, bits in itertools.product((KERNEL_WAVEFRONT, KERNEL_SIMPLE), (0, 2, 3, 5)):
+        space.append(dict(kernel=kernel, block=128, refill_min=32, refill_min_field=16, blocks_per_sm=0,
+                          grid_layout=LAYOUT_CELLS, bvh_width=2, order_bits=bits))
+    for cand in space:
+        cand.setdefault("order_bits", 4)
     return space
 
 

@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librt_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["rt_api.cu", "rt_scene.cu", "rt_treelet.cu", "rt_wide.cu", "rt_bake.cu", "rt_dfgen.cu", "rt_trace.cu",
-           "rt_backward.cu", "rt_batch.cu"]
+           "rt_backward.cu", "rt_batch.cu", "rt_order.cu"]
 PROBE_SOURCE = os.path.join("probe", "mem_probe.cu")
 PROBE_LIB = os.path.join(OUT, "libmem_probe.so")
 HEADERS = ["rt_internal.cuh", "rt_trace_dev.cuh", "rt_bake_dev.cuh"]

@@ -15,7 +15,7 @@
 static thread_local char g_err[512] = "";
 
 // process-wide launch tuning (see rt_set_tuning)
-static rt_tuning g_tuning = {RT_KERNEL_AUTO, 128, 0, 32, RT_LAYOUT_CELLS, 16, 2};
+static rt_tuning g_tuning = {RT_KERNEL_AUTO, 128, 0, 32, RT_LAYOUT_CELLS, 16, 2, 4};
 
 const rt_tuning& rt_current_tuning() { return g_tuning; }
 
@@ -33,6 +33,8 @@ extern "C" rt_status rt_set_tuning(const rt_tuning* t)
     if (t->bvh_width != 2 && t->bvh_width != 8) return rt_fail(RT_ERR_INVALID_ARG, "bvh_width %d", t->bvh_width);
     if (t->grid_layout != RT_LAYOUT_CELLS && t->grid_layout != RT_LAYOUT_PLAIN && t->grid_layout != RT_LAYOUT_PAIRS)
         return rt_fail(RT_ERR_INVALID_ARG, "grid_layout %d", t->grid_layout);
+    if (t->order_bits < 0 || t->order_bits > kOrderMaxBits)
+        return rt_fail(RT_ERR_INVALID_ARG, "order_bits %d not in 0..%d", t->order_bits, kOrderMaxBits);
     g_tuning = *t;
     return RT_OK;
 }
@@ -152,6 +154,17 @@ rt_status rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf
     a.refine_root = p->refine_root;
     a.m_near = p->m_near;
     a.m_far = p->m_far;
+    // query order: cells over the scene's box, else the grid's (the coarsest level's)
+    const float* lo = sc ? sc->lo : (sdf ? sdf->lo : nullptr);
+    const float* hi = sc ? sc->hi : (sdf ? sdf->hi : nullptr);
+    if (g_tuning.order_bits > 0 && lo) {
+        a.ob.bits = g_tuning.order_bits;
+        for (int k = 0; k < 3; ++k) {
+            const float ext = hi[k] - lo[k];
+            a.ob.lo[k] = lo[k];
+            a.ob.scale[k] = ext > 0.f ? (float)(1 << a.ob.bits) / ext : 0.f;
+        }
+    }
     return RT_OK;
 }
 
@@ -494,8 +507,8 @@ static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ra
 }
 
 extern "C" rt_status rt_trace_combined_timed(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
-                                             const rt_split_params* params, rt_hit* hits, float stage_ms[3],
-                                             int32_t stage_kind[3], int32_t* n_stages, void* stream)
+                                             const rt_split_params* params, rt_hit* hits, float stage_ms[4],
+                                             int32_t stage_kind[4], int32_t* n_stages, void* stream)
 {
     if (!stage_ms || !n_stages) return rt_fail(RT_ERR_INVALID_ARG, "null stage_ms or n_stages");
     *n_stages = 0;
@@ -503,7 +516,7 @@ extern "C" rt_status rt_trace_combined_timed(const rt_scene* sc, const rt_sdf* s
     StageTiming tm = {};
     int made = 0;
     rt_status st = RT_OK;
-    for (; made < 4; ++made) {
+    for (; made < 5; ++made) {
         cudaError_t e = cudaEventCreate(&tm.events[made]);
         if (e != cudaSuccess) { st = rt_cuda_fail(e, "cudaEventCreate"); break; }
     }

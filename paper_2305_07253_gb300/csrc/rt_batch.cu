@@ -139,7 +139,7 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
         take(pp, n_in, !live, drained, got, slot);
         bool done = false, found = false, pass = false;
         if (got) {
-            const int2 item = pp.in_items ? pp.in_items[slot] : make_int2((int)slot, 0);
+            const int2 item = pp.in_items ? pp.in_items[slot] : make_int2((int)first_query(a, slot), 0);
             g = item.x;
             flags = (uint32_t)item.y & 0xffu;
             p = (item.y >> 8) & 0xff;
@@ -222,7 +222,7 @@ __global__ void __maxnreg__(40) k_batch_field(const TraceArgs a, const BatchTabl
         take(pp, n_in, !live, drained, got, slot);
         bool done = false, found = false, pass = false;
         if (got) {
-            const int2 item = pp.in_items ? pp.in_items[slot] : make_int2((int)slot, 0);
+            const int2 item = pp.in_items ? pp.in_items[slot] : make_int2((int)first_query(a, slot), 0);
             g = item.x;
             flags = (uint32_t)item.y & 0xffu;
             p = (item.y >> 8) & 0xff;
@@ -398,15 +398,26 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
     a.counters = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
 
-    const size_t ctr_bytes = 256, qbytes = (size_t)total * sizeof(int2);
+    const size_t ctr_bytes = 256, qbytes = (size_t)total * sizeof(int2), order_bytes = rt_order_bytes(a.ob, total);
     void* scratch = nullptr;
-    RT_CUDA_TRY(cudaMallocFromPoolAsync(&scratch, ctr_bytes + 2 * qbytes, dev->pool, s));
-    unsigned* ctr = static_cast<unsigned*>(scratch);
-    int2* q[2] = {reinterpret_cast<int2*>(static_cast<char*>(scratch) + ctr_bytes),
-                  reinterpret_cast<int2*>(static_cast<char*>(scratch) + ctr_bytes + qbytes)};
+    RT_CUDA_TRY(cudaMallocFromPoolAsync(&scratch, ctr_bytes + order_bytes + 2 * qbytes, dev->pool, s));
+    char* base = static_cast<char*>(scratch);
+    unsigned* ctr = reinterpret_cast<unsigned*>(base);
+    int2* q[2] = {reinterpret_cast<int2*>(base + ctr_bytes + order_bytes),
+                  reinterpret_cast<int2*>(base + ctr_bytes + order_bytes + qbytes)};
     rt_status rs = RT_OK;
     cudaError_t e = cudaMemsetAsync(ctr, 0, ctr_bytes, s);
     if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaMemsetAsync");
+    if (order_bytes && rs == RT_OK) {
+        // the queries of every batch in one order, as one index space
+        OrderRays src = {};
+        for (int k = 0; k < n_batches; ++k) {
+            src.rays[k] = tb.e[k].rays;
+            src.offset[k] = tb.e[k].offset;
+        }
+        src.count = n_batches;
+        rs = rt_launch_order(a, src, base + ctr_bytes, s);
+    }
     // launches: triangles, field, triangles, triangles; ctr[k] = fetch counter of
     // launch k, ctr[8 + k] = number of queries launch k hands on (queues ping-pong)
     for (int k = 0; k < kLaunches && rs == RT_OK; ++k) {

@@ -95,6 +95,17 @@ struct CascLevel {
     float ih, h, eps_hit, eps_min;
 };
 
+// Query order (rt_tuning.order_bits): each window of consecutive queries
+// stably sorted by the cell of a 2^bits lattice over the box
+// lo + [0, 2^bits / scale] that holds the query's origin (rt_order.cu).
+// bits = 0, or fewer than kOrderMin queries: no ordering.
+struct OrderBox {
+    float lo[3], scale[3];
+    int32_t bits;
+};
+constexpr int32_t kOrderMaxBits = 5;
+constexpr int64_t kOrderMin = 64;
+
 // Everything one trace kernel needs, passed by value.
 struct TraceArgs {
     const BNode* nodes;
@@ -119,6 +130,8 @@ struct TraceArgs {
     rt_hit* hits;
     int64_t n;
     unsigned long long* counters;
+    OrderBox ob;             // ob.bits = 0: queries in input order
+    const int32_t* qorder;   // null: input order; else the first kernel's slot i traces query qorder[i]
 };
 
 // ---------------------------------------------------------------------------
@@ -150,10 +163,24 @@ inline void rt_apply_layout(TraceArgs& a, const rt_tuning& tu)
 // timing: when non-null, events[k] is recorded before launch k and events[n] after
 // the last; kinds[k] receives the RT_STAGE_* of launch k; *n_launches the count
 struct StageTiming {
-    cudaEvent_t events[4];
-    int32_t kinds[3];
+    cudaEvent_t events[5];
+    int32_t kinds[4];
     int32_t n_launches;
 };
+
+// The queries' ray arrays as one index space: query g lies in segment b, the
+// last with offset[b] <= g, at rays[b] + 2 (g - offset[b]).
+struct OrderRays {
+    const float4* rays[RT_MAX_BATCHES];
+    int64_t offset[RT_MAX_BATCHES];
+    int32_t count;
+};
+// Scratch bytes of the query order of n queries (a multiple of 256; 0 when
+// there is nothing to order).
+size_t rt_order_bytes(const OrderBox& ob, int64_t n);
+// Order queries 0..n-1 of a (rt_order.cu) into `scratch` (rt_order_bytes,
+// 256-byte aligned); on success a.qorder points into it.  Enqueued on s.
+rt_status rt_launch_order(TraceArgs& a, const OrderRays& src, void* scratch, cudaStream_t s);
 rt_status rt_launch_trace(const TraceArgs& a, bool counted, cudaStream_t s, StageTiming* timing = nullptr);
 rt_status rt_launch_backward(const TraceArgs& a, const float* grad_t, float* grad_grid, cudaStream_t s);
 rt_status rt_build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, cudaStream_t s,

@@ -99,7 +99,7 @@ __global__ void k_trace(const TraceArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     Counts cnt = {0, 0, 0, 0};
-    if (i < a.n) trace_one<COUNT, L, WIDE>(a, i, cnt);
+    if (i < a.n) trace_one<COUNT, L, WIDE>(a, first_query(a, i), cnt);
     if (COUNT) flush_counts(a, cnt);
 }
 
@@ -213,7 +213,7 @@ __global__ void __maxnreg__(RT_BVH_REGS) k_stage_bvh(const TraceArgs a, const St
         refill(st, n_in, !live, drained, got, slot);
         bool done = false, found = false, final_miss = false;
         if (got) {
-            int2 item = st.first ? make_int2((int)slot, 0) : st.in_items[slot];
+            int2 item = st.first ? make_int2((int)first_query(a, slot), 0) : st.in_items[slot];
             query = item.x;
             flags = (uint32_t)item.y;
             float3 o, d;
@@ -269,7 +269,7 @@ __global__ void __maxnreg__(RT_FIELD_REGS) k_stage_field(const TraceArgs a, cons
         refill(st, n_in, !live, drained, got, slot);
         bool done = false, found = false, final_miss = false;
         if (got) {
-            int2 item = st.first ? make_int2((int)slot, 0) : st.in_items[slot];
+            int2 item = st.first ? make_int2((int)first_query(a, slot), 0) : st.in_items[slot];
             query = item.x;
             flags = (uint32_t)item.y;
             float ta;
@@ -443,18 +443,34 @@ rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s,
     if (a.n > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "at most 2^31-1 queries per call");
     int kinds[3];
     const int n_st = stage_program(a, kinds);
-    // scratch: counters (fetch x3, queue sizes x2) and two ping-pong queues
+    // scratch: counters (fetch x3, queue sizes x2), the query order, and two
+    // ping-pong queues
     const size_t counters_bytes = 256;
+    const size_t order_bytes = rt_order_bytes(a.ob, a.n);
     const size_t queue_bytes = n_st > 1 ? (size_t)a.n * sizeof(int2) : 0;
-    const size_t total = counters_bytes + (n_st > 1 ? queue_bytes : 0) + (n_st > 2 ? queue_bytes : 0);
+    const size_t total = counters_bytes + order_bytes + (n_st > 1 ? queue_bytes : 0) + (n_st > 2 ? queue_bytes : 0);
     void* scratch = nullptr;
     RT_CUDA_TRY(cudaMallocFromPoolAsync(&scratch, total, dev->pool, s));
-    unsigned* ctr = static_cast<unsigned*>(scratch);
-    int2* q[2] = {reinterpret_cast<int2*>(static_cast<char*>(scratch) + counters_bytes),
-                  reinterpret_cast<int2*>(static_cast<char*>(scratch) + counters_bytes + queue_bytes)};
+    char* base = static_cast<char*>(scratch);
+    unsigned* ctr = reinterpret_cast<unsigned*>(base);
+    int2* q[2] = {reinterpret_cast<int2*>(base + counters_bytes + order_bytes),
+                  reinterpret_cast<int2*>(base + counters_bytes + order_bytes + queue_bytes)};
     rt_status rs = RT_OK;
     cudaError_t e = cudaMemsetAsync(ctr, 0, counters_bytes, s);
     if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaMemsetAsync");
+    TraceArgs ao = a;  // with the query order
+    int part = 0;      // timed parts: the order, then the stages
+    if (order_bytes && rs == RT_OK) {
+        if (timing) {
+            e = cudaEventRecord(timing->events[part], s);
+            if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaEventRecord");
+            timing->kinds[part++] = RT_STAGE_ORDER;
+        }
+        OrderRays src = {};
+        src.rays[0] = a.rays;
+        src.count = 1;
+        if (rs == RT_OK) rs = rt_launch_order(ao, src, base + counters_bytes, s);
+    }
     for (int k = 0; k < n_st && rs == RT_OK; ++k) {
         StageArgs sa;
         sa.kind = kinds[k];
@@ -467,16 +483,16 @@ rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s,
         sa.refill_min = (kinds[k] == ST_FIELD_FULL || kinds[k] == ST_FIELD_SPLIT) ? tu.refill_min_field : tu.refill_min;
         sa.trip = trip_budget(sa.refill_min);
         if (timing) {
-            e = cudaEventRecord(timing->events[k], s);
+            e = cudaEventRecord(timing->events[part], s);
             if (e != cudaSuccess) { rs = rt_cuda_fail(e, "cudaEventRecord"); break; }
-            timing->kinds[k] = public_kind(kinds[k]);
+            timing->kinds[part++] = public_kind(kinds[k]);
         }
-        rs = launch_stage<COUNT>(a, sa, tu, dev->sms, s);
+        rs = launch_stage<COUNT>(ao, sa, tu, dev->sms, s);
     }
     if (timing && rs == RT_OK) {
-        e = cudaEventRecord(timing->events[n_st], s);
+        e = cudaEventRecord(timing->events[part], s);
         if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaEventRecord");
-        timing->n_launches = n_st;
+        timing->n_launches = part;
     }
     e = cudaFreeAsync(scratch, s);
     if (rs == RT_OK && e != cudaSuccess) rs = rt_cuda_fail(e, "cudaFreeAsync");
@@ -514,11 +530,35 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
         return counted ? run_wavefront<true>(a, tu, s, timing) : run_wavefront<false>(a, tu, s, timing);
     const int64_t blocks = (a.n + tu.block - 1) / tu.block;
     if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "too many rays");
-    if (timing) {
-        RT_CUDA_TRY(cudaEventRecord(timing->events[0], s));
-        timing->kinds[0] = RT_STAGE_ALL;
+    int part = 0;
+    void* scratch = nullptr;
+    const size_t order_bytes = rt_order_bytes(a.ob, a.n);
+    if (order_bytes) {
+        // the query order, read by the kernel through a.qorder
+        DeviceInfo* dev = nullptr;
+        rt_status st = device_info(dev);
+        if (st != RT_OK) return st;
+        RT_CUDA_TRY(cudaMallocFromPoolAsync(&scratch, order_bytes, dev->pool, s));
+        cudaError_t e0 = cudaSuccess;
+        if (timing) {
+            e0 = cudaEventRecord(timing->events[part], s);
+            timing->kinds[part++] = RT_STAGE_ORDER;
+        }
+        OrderRays src = {};
+        src.rays[0] = a.rays;
+        src.count = 1;
+        st = e0 == cudaSuccess ? rt_launch_order(a, src, scratch, s) : rt_cuda_fail(e0, "cudaEventRecord");
+        if (st != RT_OK) {
+            cudaFreeAsync(scratch, s);
+            return st;
+        }
     }
-    {
+    cudaError_t e = cudaSuccess;
+    if (timing) {
+        e = cudaEventRecord(timing->events[part], s);
+        timing->kinds[part++] = RT_STAGE_ALL;
+    }
+    if (e == cudaSuccess) {
         const unsigned nb = (unsigned)blocks;
         const int L = grid_layout_of(a);
         if (a.wnodes) {
@@ -528,12 +568,17 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
             if (counted) launch_simple<true, false>(a, L, nb, tu.block, s);
             else launch_simple<false, false>(a, L, nb, tu.block, s);
         }
+        e = cudaGetLastError();
     }
-    RT_CUDA_TRY(cudaGetLastError());
-    if (timing) {
-        RT_CUDA_TRY(cudaEventRecord(timing->events[1], s));
-        timing->n_launches = 1;
+    if (e == cudaSuccess && timing) {
+        e = cudaEventRecord(timing->events[part], s);
+        timing->n_launches = part;
     }
+    if (scratch) {
+        const cudaError_t ef = cudaFreeAsync(scratch, s);
+        if (e == cudaSuccess) e = ef;
+    }
+    if (e != cudaSuccess) return rt_cuda_fail(e, "simple trace launch");
     return RT_OK;
 }
 
@@ -550,8 +595,11 @@ namespace {
 
 constexpr int64_t kNoAllocMaxRays = (int64_t)1 << 20;
 constexpr size_t kNoAllocCounterBytes = 256;
+// the query order at its largest: one 4-byte entry per query of the largest call
+constexpr size_t kNoAllocOrderBytes = (size_t)kNoAllocMaxRays * sizeof(int32_t);
 constexpr size_t kNoAllocQueueBytes = (size_t)kNoAllocMaxRays * sizeof(int2);
-constexpr size_t kNoAllocBytes = kNoAllocCounterBytes + 2 * kNoAllocQueueBytes;
+constexpr size_t kNoAllocBytes = kNoAllocCounterBytes + kNoAllocOrderBytes + 2 * kNoAllocQueueBytes;
+static_assert(kNoAllocOrderBytes % 256 == 0, "the queues stay 256-byte aligned");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -633,10 +681,17 @@ extern "C" rt_status rt_trace_combined_noalloc(const rt_scene* sc, const rt_sdf*
     const int n_st = stage_program(a, kinds);
     unsigned char* base = static_cast<unsigned char*>(dev->scratch);
     unsigned* ctr = reinterpret_cast<unsigned*>(base);
-    int2* q[2] = {reinterpret_cast<int2*>(base + kNoAllocCounterBytes),
-                  reinterpret_cast<int2*>(base + kNoAllocCounterBytes + kNoAllocQueueBytes)};
+    int2* q[2] = {reinterpret_cast<int2*>(base + kNoAllocCounterBytes + kNoAllocOrderBytes),
+                  reinterpret_cast<int2*>(base + kNoAllocCounterBytes + kNoAllocOrderBytes + kNoAllocQueueBytes)};
     // every call starts from zeroed counters (the array keeps the last call's contents)
     RT_CUDA_TRY(cudaMemsetAsync(ctr, 0, kNoAllocCounterBytes, s));
+    if (rt_order_bytes(a.ob, a.n) > kNoAllocOrderBytes)
+        return rt_fail(RT_ERR_INVALID_ARG, "query order larger than its fixed scratch");
+    OrderRays src = {};
+    src.rays[0] = a.rays;
+    src.count = 1;
+    st = rt_launch_order(a, src, base + kNoAllocCounterBytes, s);
+    if (st != RT_OK) return st;
     for (int k = 0; k < n_st; ++k) {
         StageArgs sa;
         sa.kind = kinds[k];

@@ -792,6 +792,13 @@ __device__ __forceinline__ bool valid_query(float3 o, float3 d, float tmin, floa
     return !(isnan(o.x) || isnan(o.y) || isnan(o.z) || isnan(d.x) || isnan(d.y) || isnan(d.z)) && (tmin <= tmax);
 }
 
+// The query that slot `slot` of a call's first kernel traces (the query
+// order, or input order)
+__device__ __forceinline__ int64_t first_query(const TraceArgs& a, int64_t slot)
+{
+    return a.qorder ? (int64_t)__ldg(a.qorder + slot) : slot;
+}
+
 __device__ __forceinline__ void store_hit(rt_hit* out, float t, int32_t prim, float u, float v, int32_t tracer,
                                           uint32_t flags)
 {

@@ -45,7 +45,7 @@ def test_struct_sizes_match_header():
     import paper_2305_07253_gb300 as rq
     assert ctypes.sizeof(rq.rt_split_params) == 32
     assert ctypes.sizeof(rq.rt_scene_info) == 8 * 3 + 4 * 2 + 8 + 4 * 2 + 4 * 6 + 8
-    assert ctypes.sizeof(rq.rt_tuning) == 28
+    assert ctypes.sizeof(rq.rt_tuning) == 32
     assert ctypes.sizeof(rq.rt_batch) == 8 * 3 + 32
 
 
@@ -86,7 +86,8 @@ def test_tuning_roundtrip_and_validation(rtlib):
         t = rq.rt_get_tuning()
         assert (t.kernel, t.block, t.refill_min) == (rq.KERNEL_SIMPLE, 256, 4)
         for bad in (dict(block=48), dict(block=0), dict(refill_min=0), dict(refill_min=33), dict(kernel=7),
-                    dict(grid_layout=5), dict(blocks_per_sm=-1), dict(refill_min_field=0), dict(bvh_width=4)):
+                    dict(grid_layout=5), dict(blocks_per_sm=-1), dict(refill_min_field=0), dict(bvh_width=4),
+                    dict(order_bits=-1), dict(order_bits=6)):
             with pytest.raises(rq.RtError):
                 rq.rt_set_tuning(**bad)
         assert rq.rt_get_tuning().block == 256  # a rejected call changes nothing

@@ -70,6 +70,8 @@ TUNINGS = {
     "wavefront-refill1-b64": dict(kernel=0, refill_min=1, refill_min_field=1, block=64),
     "wavefront-bvh8": dict(kernel=0, bvh_width=8),
     "simple-plain-layout": dict(kernel=1, grid_layout=1),
+    "wavefront-input-order": dict(kernel=0, order_bits=0),
+    "simple-order2": dict(kernel=1, order_bits=2),
 }
 
 

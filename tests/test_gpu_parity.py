@@ -71,6 +71,10 @@ TUNINGS = {
     "wavefront-pairs": dict(kernel=0, grid_layout=2),
     "simple-pairs": dict(kernel=1, grid_layout=2),
     "simple-bvh8": dict(kernel=1, bvh_width=8),
+    "wavefront-input-order": dict(kernel=0, order_bits=0),
+    "simple-input-order": dict(kernel=1, order_bits=0),
+    "wavefront-order1": dict(kernel=0, order_bits=1),
+    "simple-order5": dict(kernel=1, order_bits=5),
 }
 
 
@@ -394,14 +398,20 @@ def test_timed_variant_reports_each_launch(tiny):
     a = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p)
     b, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
     assert torch.equal(a, b)
-    assert [x[0] for x in st] == ["bvh_near", "field_split", "bvh_far"]
+    assert [x[0] for x in st] == ["order", "bvh_near", "field_split", "bvh_far"]  # the default query order
     assert all(ms > 0 for _, ms in st)
     prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
     try:
         c, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
     finally:
         rq.rt_set_tuning(prev)
-    assert torch.equal(a, c) and [x[0] for x in st] == ["all"]
+    assert torch.equal(a, c) and [x[0] for x in st] == ["order", "all"]
+    prev = rq.rt_set_tuning(order_bits=0)
+    try:
+        c, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
+    finally:
+        rq.rt_set_tuning(prev)
+    assert torch.equal(a, c) and [x[0] for x in st] == ["bvh_near", "field_split", "bvh_far"]
 
 
 @pytest.mark.parametrize("any_hit", [False, True])
@@ -418,7 +428,7 @@ def test_zero_multipliers_launch_no_triangle_stage(tiny, any_hit):
     for kw, stages in cases:
         p = rq.split_params(any_hit=any_hit, **kw)
         a, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
-        assert [x[0] for x in st] == stages, kw
+        assert [x[0] for x in st] == ["order"] + stages, kw
         prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
         try:
             b = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p)

@@ -174,3 +174,30 @@ def test_noalloc_calls_take_no_device_memory():
     r = subprocess.run([sys.executable, "-c", _NO_GROWTH.format(root=ROOT)], capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("bits", [5, 1])
+def test_noalloc_query_order_changes_no_record(world, bits):
+    """With a query order the no-allocation entry point keeps the order in
+    its fixed array too; at the array's limit its records equal those of the
+    allocating entry point traced in input order, any-hit records included
+    (a query's traversal does not depend on which other queries run beside
+    it)."""
+    rq, s, scene, sdf = world
+    rays = R.gi_rays(s, rq.NOALLOC_MAX_RAYS, 49, s.diagonal)
+    rd = torch.from_numpy(rays).cuda()
+    for p in (rq.split_params(mode=rq.MODE_SPLIT2, m_near=2.0, m_far=2.0),
+              rq.split_params(mode=rq.MODE_SPLIT2, m_near=2.0, m_far=2.0, any_hit=True)):
+        prev = rq.rt_set_tuning(order_bits=0)
+        try:
+            ref = rq.rt_trace_combined(scene, sdf, rd, p)
+        finally:
+            rq.rt_set_tuning(prev)
+        prev = rq.rt_set_tuning(order_bits=bits)
+        try:
+            got = torch.full_like(ref, -7)
+            assert _noalloc_via_abi(rq, scene, sdf, rd, p, got) == rq.RT_OK, rq.lib().rt_last_error()
+            torch.cuda.synchronize()
+        finally:
+            rq.rt_set_tuning(prev)
+        assert torch.equal(got, ref)
