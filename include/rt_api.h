@@ -325,8 +325,8 @@ rt_status rt_trace_combined_counted(const rt_scene* scene, const rt_sdf* sdf, co
                                     unsigned long long* d_counters, void* stream);
 
 /* Same as rt_trace_combined, and also reports how long each kernel of the
- * call ran: stage_ms[k] for the k-th part (at most 4: the query order when
- * rt_tuning.order_bits > 0 and n >= 64, then one launch per
+ * call ran: stage_ms[k] for the k-th part (at most 4: the query order where
+ * it applies (see rt_tuning.order_bits), then one launch per
  * sub-interval kind with the wavefront kernels, or the one launch of the
  * simple kernel), *n_stages the number of parts, stage_kind[k] RT_STAGE_*
  * (nullable).  stage_ms and stage_kind hold 4 entries.  Times come from CUDA
@@ -433,16 +433,19 @@ rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, c
  *                 step, twice the grid's size) when it exists
  *   order_bits    0: the first kernel takes the queries in input order.
  *                 1..5 (default 4): it takes each window of 1024
- *                 consecutive queries sorted by the cell that holds the
+ *                 consecutive queries grouped by the cell that holds the
  *                 query's origin, in a 2^b x 2^b x 2^b lattice over the
- *                 scene's box (the grid's box without a scene), cells in
- *                 Morton order, equal cells in input order; windows keep
- *                 their order.  A warp's queries then start in one region and
- *                 read the same nodes, triangles and cells.  It pays when
- *                 input neighbours start at different depths (a screen tile
- *                 over several surfaces); it costs one kernel per call that
- *                 reads every ray and writes 4 bytes per query.  Calls with
- *                 fewer than 64 queries are not ordered.
+ *                 scene's box; windows keep their order.  A warp's queries
+ *                 then start in one region and read the same nodes and
+ *                 triangles.  It pays when input neighbours start at
+ *                 different depths (a screen tile over several surfaces) and
+ *                 costs one kernel per call that reads every ray's origin and
+ *                 writes 4 bytes per query.  Applied only where the first
+ *                 kernel traces near triangle sub-intervals (closest hit, a
+ *                 split with 0 < m_near < +inf; in rt_trace_batches, when a
+ *                 non-empty batch has such queries) and n >= 64; never to the
+ *                 pieces of rt_trace_combined_host, whose copy pipeline an
+ *                 extra kernel per piece slows down.
  * Results do not depend on the tuning. */
 typedef struct {
     int32_t kernel;

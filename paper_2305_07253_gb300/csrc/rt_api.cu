@@ -154,14 +154,13 @@ rt_status rt_fill_trace_args(TraceArgs& a, const rt_scene* sc, const rt_sdf* sdf
     a.refine_root = p->refine_root;
     a.m_near = p->m_near;
     a.m_far = p->m_far;
-    // query order: cells over the scene's box, else the grid's (the coarsest level's)
-    const float* lo = sc ? sc->lo : (sdf ? sdf->lo : nullptr);
-    const float* hi = sc ? sc->hi : (sdf ? sdf->hi : nullptr);
-    if (g_tuning.order_bits > 0 && lo) {
+    // query order (where rt_order_applies; the caller clears ob.bits elsewhere):
+    // cells over the scene's box
+    if (g_tuning.order_bits > 0 && sc) {
         a.ob.bits = g_tuning.order_bits;
         for (int k = 0; k < 3; ++k) {
-            const float ext = hi[k] - lo[k];
-            a.ob.lo[k] = lo[k];
+            const float ext = sc->hi[k] - sc->lo[k];
+            a.ob.lo[k] = sc->lo[k];
             a.ob.scale[k] = ext > 0.f ? (float)(1 << a.ob.bits) / ext : 0.f;
         }
     }
@@ -476,9 +475,11 @@ extern "C" rt_status rt_sdf_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t
     return rt_launch_df_sites(sc, sdf, stage, d_sites, (cudaStream_t)stream);
 }
 
+// allow_order = false: trace in input order whatever the tuning (the pieces of
+// rt_trace_combined_host, whose pipeline an extra kernel per piece slows down)
 static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
                               const rt_split_params* p, rt_hit* hits, unsigned long long* counters,
-                              void* stream, StageTiming* timing = nullptr)
+                              void* stream, StageTiming* timing = nullptr, bool allow_order = true)
 {
     rt_status st = check_params(p);
     if (st != RT_OK) return st;
@@ -503,6 +504,7 @@ static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ra
     a.hits = hits;
     a.n = n;
     a.counters = counters;
+    if (!allow_order || !rt_order_applies(*p)) a.ob.bits = 0;
     return rt_launch_trace(a, counters != nullptr, (cudaStream_t)stream, timing);
 }
 
@@ -639,7 +641,7 @@ extern "C" rt_status rt_trace_combined_host(const rt_scene* sc, const rt_sdf* sd
         RT_CUDA_TRY(cudaMemcpyAsync(d_rays + b, h_rays + b, (size_t)m * sizeof(rt_ray), cudaMemcpyHostToDevice, p->in));
         RT_CUDA_TRY(cudaEventRecord(p->ev_in[c], p->in));
         RT_CUDA_TRY(cudaStreamWaitEvent(cs, p->ev_in[c], 0));
-        st = trace_common(sc, sdf, d_rays + b, m, params, d_hits + b, nullptr, cs);
+        st = trace_common(sc, sdf, d_rays + b, m, params, d_hits + b, nullptr, cs, nullptr, false);
         if (st != RT_OK) return st;
         RT_CUDA_TRY(cudaEventRecord(p->ev_tr[c], cs));
         RT_CUDA_TRY(cudaStreamWaitEvent(p->out, p->ev_tr[c], 0));

@@ -396,6 +396,9 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
     rt_apply_layout(a, tu);
     a.n = total;
     a.counters = nullptr;
+    bool order = false;  // the query order, if some batch starts with near triangle sub-intervals
+    for (int k = 0; k < n_batches; ++k) order |= batches[k].n > 0 && rt_order_applies(batches[k].params);
+    if (!order) a.ob.bits = 0;
     cudaStream_t s = (cudaStream_t)stream;
 
     const size_t ctr_bytes = 256, qbytes = (size_t)total * sizeof(int2), order_bytes = rt_order_bytes(a.ob, total);

@@ -106,6 +106,16 @@ struct OrderBox {
 constexpr int32_t kOrderMaxBits = 5;
 constexpr int64_t kOrderMin = 64;
 
+// The query order is applied where it was measured to pay: to queries whose
+// first sub-interval is the near triangle one (closest hit, a split with
+// 0 < m_near < inf).  Triangles-only, field-only and any-hit calls start with
+// a kernel whose time the order does not change, and pay only its cost.
+inline bool rt_order_applies(const rt_split_params& p)
+{
+    return (p.mode == RT_MODE_SPLIT1 || p.mode == RT_MODE_SPLIT2) && p.any_hit == 0 && p.m_near > 0.f &&
+           !isinf(p.m_near);
+}
+
 // Everything one trace kernel needs, passed by value.
 struct TraceArgs {
     const BNode* nodes;

@@ -673,6 +673,7 @@ extern "C" rt_status rt_trace_combined_noalloc(const rt_scene* sc, const rt_sdf*
     a.hits = hits;
     a.n = n;
     a.counters = nullptr;
+    if (!rt_order_applies(*p)) a.ob.bits = 0;
     const rt_tuning& tu = rt_current_tuning();
     rt_apply_layout(a, tu);
     cudaStream_t s = (cudaStream_t)stream;

@@ -1,7 +1,7 @@
-"""The query order (rt_tuning.order_bits): the first kernel of a call takes
-each window of 1024 consecutive queries stably sorted by the cell of a coarse
-lattice over the scene's box that holds the query's origin, instead of in
-input order.
+"""The query order (rt_tuning.order_bits): where a call's first kernel
+traces near triangle sub-intervals, it takes each window of 1024 consecutive
+queries grouped by the cell of a coarse lattice over the scene's box that
+holds the query's origin, instead of in input order.
 
 A query's record does not depend on which queries run beside it or when, so
 every record must equal the one traced in input order, bit for bit, any-hit
@@ -11,7 +11,8 @@ shows.  Inputs include ragged sizes (1, 31, 32, 33, 257, 4173 queries: below
 the 64 the order skips, within one window, past it), invalid queries (NaN or
 infinite origins, zero directions, t_min > t_max), origins far outside the
 scene's box, and mixed batches with empty ones among them, whose windows
-straddle batches."""
+straddle batches.  Calls the order does not apply to (triangles only, field
+only, any hit, m_near of 0 or +inf) must run without it."""
 import math
 
 import numpy as np
@@ -133,14 +134,21 @@ def test_order_of_mixed_batches_changes_no_record(world):
             assert torch.equal(g, r), (bits, k)
 
 
-def test_order_on_a_grid_without_scene(world):
-    """A field-only call has no scene: the cells span the grid's box."""
+@pytest.mark.parametrize("pname,applies", [("one-split", True), ("two-splits", True), ("two-splits-any", False),
+                                           ("triangles", False), ("triangles-any", False), ("field", False),
+                                           ("no-near", False), ("near-inf", False)])
+def test_order_runs_only_where_it_applies(world, pname, applies):
     rq, s, scene, sdf = world
-    rd = torch.from_numpy(_rays(s, 4173, 90)).cuda()
-    p = rq.split_params(mode=rq.MODE_SDF)
-    ref = _trace(rq, None, sdf, rd, p, order_bits=0)
-    for bits in BITS:
-        assert torch.equal(_trace(rq, None, sdf, rd, p, order_bits=bits), ref)
+    rd = torch.from_numpy(_rays(s, 4173, 92)).cuda()
+    kw = PARAMS.get(pname, dict(mode=1, m_near=math.inf))
+    p = rq.split_params(**kw)
+    prev = rq.rt_set_tuning(order_bits=4, kernel=rq.KERNEL_WAVEFRONT)
+    try:
+        _, st = rq.rt_trace_combined_timed(scene if p.mode != rq.MODE_SDF else None,
+                                           sdf if p.mode != rq.MODE_BVH else None, rd, p)
+    finally:
+        rq.rt_set_tuning(prev)
+    assert (st[0][0] == "order") == applies, st
 
 
 def test_timed_call_reports_the_order(world):
