@@ -8,9 +8,8 @@
 // instance, can start on surfaces at very different depths.
 //
 // The order groups each window of kOrderWindow (1024) consecutive queries by
-// a key: the Morton code of the cell that holds the query's origin, in a
-// 2^b x 2^b x 2^b lattice over the scene's box (origins outside the box fall
-// in the nearest cell).  Windows keep their order, and within a window the
+// a key: the cell that holds the query's origin, in a 2^b x 2^b x 2^b lattice
+// over the scene's box (origins outside the box fall in the nearest cell).  Windows keep their order, and within a window the
 // queries of one cell become neighbours; the first kernel of the call then
 // takes query qorder[0], qorder[1], ...
 //
@@ -29,8 +28,11 @@
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kOrderThreads = 128;
-constexpr int kOrderItems = 8;
+#ifndef RT_ORDER_THREADS
+#define RT_ORDER_THREADS 128
+#endif
+constexpr int kOrderThreads = RT_ORDER_THREADS;
+constexpr int kOrderItems = 1024 / kOrderThreads;
 constexpr int kOrderWindow = kOrderThreads * kOrderItems;  // queries per window
 constexpr int kSlots = kOrderWindow;
 static_assert(kSlots == 1 << 10, "slot_of hashes to 10 bits");
@@ -46,13 +48,8 @@ __device__ __forceinline__ int32_t order_key(const OrderBox& ob, float4 r0)
         const float f = fminf(fmaxf((p[a] - ob.lo[a]) * ob.scale[a], 0.f), top);
         c[a] = (uint32_t)f;
     }
-    uint32_t m = 0;
-#pragma unroll
-    for (int b = 0; b < kOrderMaxBits; ++b)
-        if (b < ob.bits)
-            m |= (((c[0] >> b) & 1u) << (3 * b)) | (((c[1] >> b) & 1u) << (3 * b + 1)) |
-                 (((c[2] >> b) & 1u) << (3 * b + 2));
-    return (int32_t)m;
+    // only equality of keys matters within a window: the cell's coordinates, packed
+    return (int32_t)(c[0] | (c[1] << ob.bits) | (c[2] << (2 * ob.bits)));
 }
 
 // the slot of key (inserted if new; fresh = this call inserted it), -1 if
