@@ -38,6 +38,7 @@ M_MIDDLE = 2.0
 WORKLOAD = "frame-1080p-gi"
 # the sources of the stage kernels: the measured DRAM traffic applies while they are unchanged
 TRACE_SOURCES = ["paper_2305_07253_gb300/csrc/rt_trace.cu", "paper_2305_07253_gb300/csrc/rt_trace_dev.cuh",
+                 "paper_2305_07253_gb300/csrc/rt_order.cu",
                  "paper_2305_07253_gb300/csrc/rt_internal.cuh"]
 
 
