@@ -410,10 +410,10 @@ rt_status rt_trace_combined_backward(const rt_scene* scene, const rt_sdf* sdf, c
  *                 sub-interval kind, with per-lane refill from a global queue,
  *                 so rays that switch tracer mid-query are regrouped across
  *                 the whole batch; RT_KERNEL_SIMPLE: one thread per query runs
- *                 all its sub-intervals; RT_KERNEL_AUTO (default): one thread
- *                 per query for triangles-only calls (mode RT_MODE_BVH, or a
- *                 split with m_near = +INFINITY), where there is nothing to
- *                 regroup, the stage kernels otherwise.
+ *                 all its sub-intervals; RT_KERNEL_AUTO (default): the stage
+ *                 kernels (on triangles-only calls as well, where they were
+ *                 measured at least as fast as one thread per query on GI,
+ *                 primary and AO rays).
  *   block         threads per block (multiple of 32, 32..1024)
  *   blocks_per_sm persistent grid = SMs x this (0: as many as fit)
  *   refill_min    triangle stages: a warp fetches new queries when at least

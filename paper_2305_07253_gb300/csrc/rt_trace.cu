@@ -14,8 +14,7 @@
 //     rays that switch tracer mid-query are regrouped across the whole batch
 //     instead of diverging inside a warp.
 //   * simple: one thread per query runs all of its sub-intervals.
-// The default (RT_KERNEL_AUTO) takes the simple kernel for triangles-only
-// calls, where there is nothing to regroup, and the stage kernels otherwise.
+// The default (RT_KERNEL_AUTO) takes the stage kernels.
 #include <mutex>
 
 #include "rt_trace_dev.cuh"
@@ -124,33 +123,41 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // The bounds of this stage's sub-interval of the query (o, d, t_min, t_max).
 // Returns false when the sub-interval is not part of the query (or the query
-// is invalid).
+// is invalid).  more: the query has a later sub-interval in its program
+// (Section 2: closest hit near, field, far; any hit field, near, far), so a
+// miss here goes on to the next stage; otherwise the miss is final here.
 __device__ __forceinline__ bool segment_bounds(const TraceArgs& a, int kind, float3 o, float3 d, float tmin,
-                                               float tmax, float& ta, float& tb, bool& invalid)
+                                               float tmax, float& ta, float& tb, bool& more)
 {
-    invalid = !valid_query(o, d, tmin, tmax);
-    if (invalid) return false;
+    more = false;
+    if (!valid_query(o, d, tmin, tmax)) return false;
     if (kind == ST_BVH_FULL || kind == ST_FIELD_FULL) {
         ta = tmin;
         tb = tmax;
         return true;
     }
     const Split s = make_split(a, o, d, tmin, tmax);
-    if (kind == ST_BVH_NEAR) { ta = tmin; tb = s.t1; return s.near_bvh; }
+    if (kind == ST_BVH_NEAR) {
+        ta = tmin;
+        tb = s.t1;
+        more = a.any_hit ? s.far_bvh : (s.field || s.far_bvh);
+        return s.near_bvh;
+    }
     if (kind == ST_BVH_FAR) { ta = s.t2; tb = tmax; return s.far_bvh; }
     ta = s.t1;
     tb = s.t2;
+    more = a.any_hit ? (s.near_bvh || s.far_bvh) : s.far_bvh;
     return s.field;
 }
 
 // Load query q and the bounds of this stage's sub-interval.
 __device__ __forceinline__ bool stage_segment(const TraceArgs& a, int kind, int64_t q, float3& o, float3& d,
-                                              float& ta, float& tb, bool& invalid)
+                                              float& ta, float& tb, bool& more)
 {
     const float4 r0 = __ldg(a.rays + 2 * q), r1 = __ldg(a.rays + 2 * q + 1);
     o = make_float3(r0.x, r0.y, r0.z);
     d = make_float3(r1.x, r1.y, r1.z);
-    return segment_bounds(a, kind, o, d, r0.w, r1.w, ta, tb, invalid);
+    return segment_bounds(a, kind, o, d, r0.w, r1.w, ta, tb, more);
 }
 
 // Append the lanes with `fwd` set to the next stage's queue (one atomic per warp).
@@ -201,7 +208,7 @@ __global__ void __maxnreg__(RT_BVH_REGS) k_stage_bvh(const TraceArgs a, const St
     const bool any_hit = a.any_hit != 0;
     typename TravOf<WIDE>::entry stack[TravOf<WIDE>::depth];
     Counts cnt = {0, 0, 0, 0};
-    bool drained = false, live = false;
+    bool drained = false, live = false, more = false;
     int query = -1;
     uint32_t flags = 0;
     BvhRay r;
@@ -211,15 +218,14 @@ __global__ void __maxnreg__(RT_BVH_REGS) k_stage_bvh(const TraceArgs a, const St
         bool got;
         unsigned slot = 0;
         refill(st, n_in, !live, drained, got, slot);
-        bool done = false, found = false, final_miss = false;
+        bool done = false, found = false;
         if (got) {
             int2 item = st.first ? make_int2((int)first_query(a, slot), 0) : st.in_items[slot];
             query = item.x;
             flags = (uint32_t)item.y;
             float3 o, d;
             float ta, tb;
-            bool invalid;
-            bool active = stage_segment(a, st.kind, query, o, d, ta, tb, invalid);
+            bool active = stage_segment(a, st.kind, query, o, d, ta, tb, more);
             if (active && ta <= tb && a.root != INT32_MIN) {
                 r = bvh_ray(o, d);
                 s = tbegin<WIDE>(a, r, ta, tb);
@@ -227,7 +233,6 @@ __global__ void __maxnreg__(RT_BVH_REGS) k_stage_bvh(const TraceArgs a, const St
                 live = true;
             } else {
                 done = true;
-                final_miss = invalid;
             }
         } else if (live) {
             if (ttrip<COUNT, WIDE>(a, r, s, stack, any_hit, best, flags, cnt, st.trip)) {
@@ -236,7 +241,7 @@ __global__ void __maxnreg__(RT_BVH_REGS) k_stage_bvh(const TraceArgs a, const St
                 live = false;
             }
         }
-        const bool fwd = done && !found && !final_miss && st.out_items != nullptr;
+        const bool fwd = done && !found && more && st.out_items != nullptr;
         forward(st, fwd, query, flags);
         if (done && !fwd) {
             if (found) store_hit(a.hits + query, best.t, best.prim, best.u, best.v, RT_TRACER_BVH, flags);
@@ -257,7 +262,7 @@ __global__ void __maxnreg__(RT_FIELD_REGS) k_stage_field(const TraceArgs a, cons
 {
     const unsigned n_in = st.first ? (unsigned)a.n : *st.in_count;
     Counts cnt = {0, 0, 0, 0};
-    bool drained = false, live = false;
+    bool drained = false, live = false, more = false;
     int query = -1;
     uint32_t flags = 0;
     float3 o = make_float3(0.f, 0.f, 0.f), d = o;
@@ -267,14 +272,13 @@ __global__ void __maxnreg__(RT_FIELD_REGS) k_stage_field(const TraceArgs a, cons
         bool got;
         unsigned slot = 0;
         refill(st, n_in, !live, drained, got, slot);
-        bool done = false, found = false, final_miss = false;
+        bool done = false, found = false;
         if (got) {
             int2 item = st.first ? make_int2((int)first_query(a, slot), 0) : st.in_items[slot];
             query = item.x;
             flags = (uint32_t)item.y;
             float ta;
-            bool invalid;
-            bool active = stage_segment(a, st.kind, query, o, d, ta, tb, invalid);
+            bool active = stage_segment(a, st.kind, query, o, d, ta, tb, more);
             if (active && clip_grid(a, o, d, ta, tb)) {
                 if (COUNT) ++cnt.field;
                 t = ta;
@@ -283,7 +287,6 @@ __global__ void __maxnreg__(RT_FIELD_REGS) k_stage_field(const TraceArgs a, cons
                 live = true;
             } else {
                 done = true;
-                final_miss = invalid;
             }
         } else if (live) {
             // several march steps between two refill checks
@@ -304,7 +307,7 @@ __global__ void __maxnreg__(RT_FIELD_REGS) k_stage_field(const TraceArgs a, cons
             }
             if (done) live = false;
         }
-        const bool fwd = done && !found && !final_miss && st.out_items != nullptr;
+        const bool fwd = done && !found && more && st.out_items != nullptr;
         forward(st, fwd, query, flags);
         if (done && !fwd) {
             if (found) {
@@ -521,11 +524,9 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
     const rt_tuning& tu = rt_current_tuning();
     TraceArgs a = a0;
     rt_apply_layout(a, tu);
-    // AUTO: a triangles-only call (mode BVH, or a split with m_near = +inf, whose
-    // field sub-interval is empty for every query) has nothing to regroup
-    const bool triangles_only = a.mode == RT_MODE_BVH || ((a.mode == RT_MODE_SPLIT1 || a.mode == RT_MODE_SPLIT2) &&
-                                                          isinf(a.m_near) && a.m_near > 0.f);
-    const bool wavefront = tu.kernel == RT_KERNEL_WAVEFRONT || (tu.kernel == RT_KERNEL_AUTO && !triangles_only);
+    // AUTO: the stage kernels for every call; on triangles-only calls too they
+    // were measured at least as fast as one thread per query on every ray kind
+    const bool wavefront = tu.kernel == RT_KERNEL_WAVEFRONT || tu.kernel == RT_KERNEL_AUTO;
     if (wavefront)
         return counted ? run_wavefront<true>(a, tu, s, timing) : run_wavefront<false>(a, tu, s, timing);
     const int64_t blocks = (a.n + tu.block - 1) / tu.block;
