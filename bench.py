@@ -236,7 +236,8 @@ def run_ours(args):
     rays_d = torch.from_numpy(rays).to(dev)
     hits = torch.empty((n_rays, 6), dtype=torch.int32, device=dev)
     p_mid = rq.split_params(mode=rq.MODE_SPLIT1, m_near=M_MIDDLE)
-    p_bvh = rq.split_params(mode=rq.MODE_SPLIT1, m_near=math.inf)
+    # the three forms of the paper's comparison: triangles only (HWRT-only), combined, field only
+    p_bvh = rq.split_params(mode=rq.MODE_BVH)
     p_sdf = rq.split_params(mode=rq.MODE_SPLIT1, m_near=0.0)
     stream = torch.cuda.current_stream()
 
