@@ -22,6 +22,7 @@
 // The groups come in the order their keys were first met, and a group's
 // queries in about input order.
 #include <algorithm>
+#include <atomic>
 
 #include "rt_internal.cuh"
 
@@ -185,6 +186,9 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_local(const OrderRays s
     asm volatile("cp.async.wait_all;" ::: "memory");  // no copy left in flight
 }
 
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_resident[kMaxDevices];  // resident blocks of k_order_local per device (0: not looked up)
+
 }  // namespace
 
 size_t rt_order_bytes(const OrderBox& ob, int64_t n)
@@ -206,12 +210,20 @@ rt_status rt_launch_order(TraceArgs& a, const OrderRays& src, void* scratch, cud
         return rt_fail(RT_ERR_INVALID_ARG, "query order: scratch not 256-byte aligned");
     int32_t* qorder = static_cast<int32_t*>(scratch);
     const int64_t windows = (a.n + kOrderWindow - 1) / kOrderWindow;
-    // persistent: as many blocks as fit at once (or one per window)
-    int dev = 0, sms = 0, per_sm = 0;
+    // persistent: as many blocks as fit at once (or one per window); the
+    // figure is looked up once per device
+    int dev = 0;
     RT_CUDA_TRY(cudaGetDevice(&dev));
-    RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_order_local, kOrderThreads, 0));
-    const int64_t blocks = std::min<int64_t>(windows, (int64_t)sms * std::max(per_sm, 1));
+    if (dev < 0 || dev >= kMaxDevices) return rt_fail(RT_ERR_INVALID_ARG, "device %d out of range", dev);
+    int resident = g_resident[dev].load(std::memory_order_relaxed);
+    if (resident == 0) {
+        int sms = 0, per_sm = 0;
+        RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_order_local, kOrderThreads, 0));
+        resident = sms * std::max(per_sm, 1);
+        g_resident[dev].store(resident, std::memory_order_relaxed);
+    }
+    const int64_t blocks = std::min<int64_t>(windows, resident);
     k_order_local<<<(unsigned)blocks, kOrderThreads, 0, s>>>(src, ob, a.n, windows, qorder);
     RT_CUDA_TRY(cudaGetLastError());
     a.qorder = qorder;
