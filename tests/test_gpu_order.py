@@ -7,8 +7,9 @@ A query's record does not depend on which queries run beside it or when, so
 every record must equal the one traced in input order, bit for bit, any-hit
 records included.  Hit buffers start filled with a pattern no record has, so
 a query that the order dropped or traced twice (leaving another one out)
-shows.  Inputs include ragged sizes (1, 31, 32, 33, 257, 4173 queries: below
-the 64 the order skips, within one window, past it), invalid queries (NaN or
+shows.  Inputs include ragged sizes (1 to 63 queries: below the 64 the order
+skips; 64; within one window of 1024; exactly one; one past; several windows
+with a ragged last one), invalid queries (NaN or
 infinite origins, zero directions, t_min > t_max), origins far outside the
 scene's box, and mixed batches with empty ones among them, whose windows
 straddle batches.  Calls the order does not apply to (triangles only, field
@@ -78,7 +79,7 @@ PARAMS = {
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
-@pytest.mark.parametrize("n", [1, 31, 32, 33, 257, 4173])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 63, 64, 257, 1024, 1025, 2049, 4173])
 @pytest.mark.parametrize("pname", list(PARAMS))
 def test_order_changes_no_record(world, kernel, n, pname):
     rq, s, scene, sdf = world
