@@ -312,7 +312,12 @@ rt_status rt_trace_sdf(const rt_sdf* sdf, const rt_ray* d_rays, int64_t n, const
                        rt_hit* d_hits, void* stream);
 
 /* The combined query (Eq. 2 and the rules of rt_split_params) for n rays.
- * `params` is read on the host during the call. */
+ * `params` is read on the host during the call.  With the stage kernels, a
+ * closest-hit split call runs its near triangle stage and its field stage at
+ * the same time, on two streams of the library forked from `stream` and
+ * joined back into it by events (calls on one device share these streams; a
+ * lock keeps each call's launches together).  The records are those of the
+ * sub-intervals traced in order. */
 rt_status rt_trace_combined(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
                             const rt_split_params* params, rt_hit* d_hits, void* stream);
 
@@ -325,18 +330,20 @@ rt_status rt_trace_combined_counted(const rt_scene* scene, const rt_sdf* sdf, co
                                     unsigned long long* d_counters, void* stream);
 
 /* Same as rt_trace_combined, and also reports how long each kernel of the
- * call ran: stage_ms[k] for the k-th part (at most 4: the query order where
- * it applies (see rt_tuning.order_bits), then one launch per
- * sub-interval kind with the wavefront kernels, or the one launch of the
- * simple kernel), *n_stages the number of parts, stage_kind[k] RT_STAGE_*
- * (nullable).  stage_ms and stage_kind hold 4 entries.  Times come from CUDA
- * events recorded on `stream` between the launches; the call synchronises
- * `stream`.  Used to measure per-kernel throughput. */
+ * call ran: stage_ms[k] for the k-th part (at most 6: the query order where
+ * it applies (see rt_tuning.order_bits), then one launch per sub-interval
+ * kind with the wavefront kernels and, for closest-hit split calls, the
+ * merge of the near hits; or the one launch of the simple kernel), *n_stages
+ * the number of parts, stage_kind[k] RT_STAGE_* (nullable).  stage_ms and
+ * stage_kind hold 6 entries.  Each part is timed by CUDA events on the
+ * stream that ran it; in a closest-hit split call the near and field stages
+ * run at the same time on two streams, so their times overlap.  The call
+ * synchronises `stream`.  Used to measure per-kernel throughput. */
 enum { RT_STAGE_ALL = 0, RT_STAGE_BVH_FULL = 1, RT_STAGE_BVH_NEAR = 2, RT_STAGE_BVH_FAR = 3,
-       RT_STAGE_FIELD_FULL = 4, RT_STAGE_FIELD_SPLIT = 5, RT_STAGE_ORDER = 6 };
+       RT_STAGE_FIELD_FULL = 4, RT_STAGE_FIELD_SPLIT = 5, RT_STAGE_ORDER = 6, RT_STAGE_MERGE = 7 };
 rt_status rt_trace_combined_timed(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
-                                  const rt_split_params* params, rt_hit* d_hits, float stage_ms[4],
-                                  int32_t stage_kind[4], int32_t* n_stages, void* stream);
+                                  const rt_split_params* params, rt_hit* d_hits, float stage_ms[6],
+                                  int32_t stage_kind[6], int32_t* n_stages, void* stream);
 
 /* The combined query of rt_trace_combined, for callers that cannot allocate
  * device memory during the call: for example a renderer whose frame loop

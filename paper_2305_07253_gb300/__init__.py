@@ -397,15 +397,16 @@ def rt_trace_batches(scene: Scene | None, sdf: Sdf | None, batches, stream=None)
     return outs
 
 
-STAGE_NAMES = {0: "all", 1: "bvh_full", 2: "bvh_near", 3: "bvh_far", 4: "field_full", 5: "field_split", 6: "order"}
+STAGE_NAMES = {0: "all", 1: "bvh_full", 2: "bvh_near", 3: "bvh_far", 4: "field_full", 5: "field_split", 6: "order",
+               7: "merge"}
 
 
 def rt_trace_combined_timed(scene: Scene | None, sdf: Sdf | None, rays: torch.Tensor, params: rt_split_params,
                             hits: torch.Tensor | None = None, stream=None):
     """Returns (hits, [(stage name, ms), ...]) with the device time of each kernel launch."""
     hits = _rays_hits(rays, hits)
-    ms = (ctypes.c_float * 4)()
-    kinds = (ctypes.c_int32 * 4)()
+    ms = (ctypes.c_float * 6)()
+    kinds = (ctypes.c_int32 * 6)()
     n = ctypes.c_int32()
     _check(lib().rt_trace_combined_timed(scene.handle if scene else None, sdf.handle if sdf else None, _dptr(rays),
                                          rays.shape[0], ctypes.byref(params), _dptr(hits), ms, kinds,

@@ -475,8 +475,10 @@ extern "C" rt_status rt_sdf_sites(const rt_scene* sc, const rt_sdf* sdf, int32_t
     return rt_launch_df_sites(sc, sdf, stage, d_sites, (cudaStream_t)stream);
 }
 
-// allow_order = false: trace in input order whatever the tuning (the pieces of
-// rt_trace_combined_host, whose pipeline an extra kernel per piece slows down)
+// allow_order = false: trace in input order whatever the tuning, and the
+// stages in sequence on `stream` (the pieces of rt_trace_combined_host, whose
+// pipeline an extra kernel per piece slows down, and whose pieces run on
+// streams of their own)
 static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
                               const rt_split_params* p, rt_hit* hits, unsigned long long* counters,
                               void* stream, StageTiming* timing = nullptr, bool allow_order = true)
@@ -505,12 +507,12 @@ static rt_status trace_common(const rt_scene* sc, const rt_sdf* sdf, const rt_ra
     a.n = n;
     a.counters = counters;
     if (!allow_order || !rt_order_applies(*p)) a.ob.bits = 0;
-    return rt_launch_trace(a, counters != nullptr, (cudaStream_t)stream, timing);
+    return rt_launch_trace(a, counters != nullptr, (cudaStream_t)stream, timing, allow_order);
 }
 
 extern "C" rt_status rt_trace_combined_timed(const rt_scene* sc, const rt_sdf* sdf, const rt_ray* rays, int64_t n,
-                                             const rt_split_params* params, rt_hit* hits, float stage_ms[4],
-                                             int32_t stage_kind[4], int32_t* n_stages, void* stream)
+                                             const rt_split_params* params, rt_hit* hits, float stage_ms[6],
+                                             int32_t stage_kind[6], int32_t* n_stages, void* stream)
 {
     if (!stage_ms || !n_stages) return rt_fail(RT_ERR_INVALID_ARG, "null stage_ms or n_stages");
     *n_stages = 0;
@@ -518,7 +520,7 @@ extern "C" rt_status rt_trace_combined_timed(const rt_scene* sc, const rt_sdf* s
     StageTiming tm = {};
     int made = 0;
     rt_status st = RT_OK;
-    for (; made < 5; ++made) {
+    for (; made < 2 * kMaxTimedParts; ++made) {
         cudaError_t e = cudaEventCreate(&tm.events[made]);
         if (e != cudaSuccess) { st = rt_cuda_fail(e, "cudaEventCreate"); break; }
     }
@@ -530,7 +532,7 @@ extern "C" rt_status rt_trace_combined_timed(const rt_scene* sc, const rt_sdf* s
     if (st == RT_OK) {
         for (int k = 0; k < tm.n_launches; ++k) {
             float ms = 0.f;
-            cudaError_t e = cudaEventElapsedTime(&ms, tm.events[k], tm.events[k + 1]);
+            cudaError_t e = cudaEventElapsedTime(&ms, tm.events[2 * k], tm.events[2 * k + 1]);
             if (e != cudaSuccess) { st = rt_cuda_fail(e, "cudaEventElapsedTime"); break; }
             stage_ms[k] = ms;
             if (stage_kind) stage_kind[k] = tm.kinds[k];

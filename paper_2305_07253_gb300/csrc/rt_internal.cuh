@@ -172,9 +172,12 @@ inline void rt_apply_layout(TraceArgs& a, const rt_tuning& tu)
 // launchers implemented in the .cu files
 // timing: when non-null, events[k] is recorded before launch k and events[n] after
 // the last; kinds[k] receives the RT_STAGE_* of launch k; *n_launches the count
+// Timed parts of one call (rt_trace_combined_timed): part k ran between
+// events[2k] and events[2k+1], recorded on the stream that ran it.
+constexpr int kMaxTimedParts = 6;
 struct StageTiming {
-    cudaEvent_t events[5];
-    int32_t kinds[4];
+    cudaEvent_t events[2 * kMaxTimedParts];
+    int32_t kinds[kMaxTimedParts];
     int32_t n_launches;
 };
 
@@ -191,7 +194,10 @@ size_t rt_order_bytes(const OrderBox& ob, int64_t n);
 // Order queries 0..n-1 of a (rt_order.cu) into `scratch` (rt_order_bytes,
 // 256-byte aligned); on success a.qorder points into it.  Enqueued on s.
 rt_status rt_launch_order(TraceArgs& a, const OrderRays& src, void* scratch, cudaStream_t s);
-rt_status rt_launch_trace(const TraceArgs& a, bool counted, cudaStream_t s, StageTiming* timing = nullptr);
+// allow_concurrent = false: the stages of a closest-hit split call run in
+// sequence on s (no internal streams), as the pieces of rt_trace_combined_host need
+rt_status rt_launch_trace(const TraceArgs& a, bool counted, cudaStream_t s, StageTiming* timing = nullptr,
+                          bool allow_concurrent = true);
 rt_status rt_launch_backward(const TraceArgs& a, const float* grad_t, float* grad_grid, cudaStream_t s);
 rt_status rt_build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, cudaStream_t s,
                          rt_scene* out);

@@ -107,6 +107,20 @@ __global__ void k_trace(const TraceArgs a)
 // ---------------------------------------------------------------------------
 enum StageKind { ST_BVH_FULL = 0, ST_BVH_NEAR = 1, ST_BVH_FAR = 2, ST_FIELD_FULL = 3, ST_FIELD_SPLIT = 4 };
 
+// A near triangle hit of the concurrent program (run_wavefront): the query and
+// its record, copied over the field's record by k_merge_hits.  A near miss
+// that raised flags leaves an entry with prim kFlagsOnly, whose flags are
+// added to the record (in sequence they would travel on to the field stage).
+constexpr int32_t kFlagsOnly = -2;
+struct HitEntry {
+    int32_t query;
+    uint32_t flags;
+    float t, u, v;
+    int32_t prim;
+    int32_t pad[2];
+};
+static_assert(sizeof(HitEntry) == 32, "one 32-byte entry per hit");
+
 struct StageArgs {
     int32_t kind;
     int32_t first;             // input = every query 0..n-1 (validity is checked here)
@@ -117,6 +131,8 @@ struct StageArgs {
     unsigned* fetch;           // work counter of this stage
     int32_t refill_min;
     int32_t trip;              // traversal iterations between refill checks (trip_budget)
+    HitEntry* hit_list;        // non-null (near stage of the concurrent program): hits go here, misses write nothing
+    unsigned* hit_count;
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -170,6 +186,28 @@ __device__ __forceinline__ void forward(const StageArgs& st, bool fwd, int query
     if (lane_id() == (unsigned)leader) base = atomicAdd(st.out_count, (unsigned)__popc(m));
     base = __shfl_sync(kFull, base, leader);
     if (fwd) st.out_items[base + __popc(m & ((1u << lane_id()) - 1u))] = make_int2(query, (int)flags);
+}
+
+// Append the lanes with `hit` set to the hit list (one atomic per warp).
+__device__ __forceinline__ void append_hits(const StageArgs& st, bool hit, int query, const Hit& best, uint32_t flags)
+{
+    const unsigned m = __ballot_sync(kFull, hit);
+    if (m == 0) return;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane_id() == (unsigned)leader) base = atomicAdd(st.hit_count, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (hit) {
+        HitEntry e;
+        e.query = query;
+        e.flags = flags;
+        e.t = best.t;
+        e.u = best.u;
+        e.v = best.v;
+        e.prim = best.prim;
+        e.pad[0] = e.pad[1] = 0;
+        st.hit_list[base + __popc(m & ((1u << lane_id()) - 1u))] = e;
+    }
 }
 
 // Take new queries for the idle lanes when enough of them are idle (or all are).
@@ -243,13 +281,35 @@ __global__ void __maxnreg__(RT_BVH_REGS) k_stage_bvh(const TraceArgs a, const St
         }
         const bool fwd = done && !found && more && st.out_items != nullptr;
         forward(st, fwd, query, flags);
-        if (done && !fwd) {
+        if (st.hit_list) {
+            // concurrent program: the field stage writes every record; a near hit
+            // replaces it, a near miss's flags join it (k_merge_hits)
+            if (done && !found) best.prim = kFlagsOnly;
+            append_hits(st, done && (found || flags != 0u), query, best, flags);
+        } else if (done && !fwd) {
             if (found) store_hit(a.hits + query, best.t, best.prim, best.u, best.v, RT_TRACER_BVH, flags);
             else store_hit(a.hits + query, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
         }
         if (__ballot_sync(kFull, live || (!drained)) == 0) break;
     }
     if (COUNT) flush_counts(a, cnt);
+}
+
+// The near hits of the concurrent program over the field's records: a hit in
+// the near sub-interval is the closest hit (Section 2: sub-intervals in order)
+__global__ void __launch_bounds__(256) k_merge_hits(const HitEntry* __restrict__ list, const unsigned* __restrict__ count,
+                                                    rt_hit* __restrict__ hits)
+{
+    const unsigned n = *count;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const HitEntry e = list[i];
+        if (e.prim == kFlagsOnly) {
+            uint32_t* f = reinterpret_cast<uint32_t*>(hits + e.query) + 5;  // the record's flags word
+            *f |= e.flags;
+        } else {
+            store_hit(hits + e.query, e.t, e.prim, e.u, e.v, RT_TRACER_BVH, e.flags);
+        }
+    }
 }
 
 // 40 registers: 12 resident blocks of 128 threads per SM; more march chains in
@@ -437,8 +497,203 @@ int32_t public_kind(int k)
     }
 }
 
+// Streams and events of the concurrent program, one set per device, and the
+// lock that keeps one call's fork-to-join sequence of launches together.
+struct ConcStreams {
+    cudaStream_t near = nullptr, field = nullptr;
+    cudaEvent_t fork = nullptr, ordered = nullptr, near_done = nullptr, field_done = nullptr;
+    bool ready = false;
+};
+std::mutex g_conc_mu;
+ConcStreams g_conc[64];
+
+rt_status conc_streams(ConcStreams*& out)
+{
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return rt_fail(RT_ERR_INVALID_ARG, "device %d out of range", dev);
+    ConcStreams& c = g_conc[dev];
+    if (!c.ready) {
+        // the near stream at the highest priority: when both stages have blocks
+        // waiting for room (after the order kernel), the near stage's are placed
+        // first, and the field stage's fill the rest of each SM
+        int least = 0, greatest = 0;
+        RT_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        RT_CUDA_TRY(cudaStreamCreateWithPriority(&c.near, cudaStreamNonBlocking, greatest));
+        RT_CUDA_TRY(cudaStreamCreateWithPriority(&c.field, cudaStreamNonBlocking, least));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.ordered, cudaEventDisableTiming));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.near_done, cudaEventDisableTiming));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.field_done, cudaEventDisableTiming));
+        c.ready = true;
+    }
+    out = &c;
+    return RT_OK;
+}
+
+// Resident blocks per SM of the two concurrent stages when the tuning leaves
+// them free.  Both kernels are persistent, so their blocks must fit in an SM
+// side by side (registers: 2 x 128 x 56 + 9 x 128 x 40 = 60,416 of 65,536),
+// or the later launch waits for the earlier one's end.  Measured on the 1080p
+// GI workload, whole call: near 2 + field 9 0.595 ms, 3 + 9 0.608, 3 + 8
+// 0.614, 4 + 7 0.661; the stages in sequence 0.662.
+#ifndef RT_CONC_NEAR_BLOCKS
+#define RT_CONC_NEAR_BLOCKS 2
+#endif
+#ifndef RT_CONC_FIELD_BLOCKS
+#define RT_CONC_FIELD_BLOCKS 9
+#endif
+constexpr int kConcNearBlocks = RT_CONC_NEAR_BLOCKS;
+constexpr int kConcFieldBlocks = RT_CONC_FIELD_BLOCKS;
+
+// Work counters sit 128 bytes apart: atomics of different counters, from one
+// kernel or from two running side by side, then never share an L2 line.
+constexpr int kCtrStride = 32;
+
+// start / end of timed part k on stream s
+struct Marks {
+    StageTiming* t;
+    int part = 0;
+    rt_status begin(cudaStream_t s, int32_t kind)
+    {
+        if (!t) return RT_OK;
+        if (part >= kMaxTimedParts) return rt_fail(RT_ERR_INVALID_ARG, "too many timed parts");
+        t->kinds[part] = kind;
+        cudaError_t e = cudaEventRecord(t->events[2 * part], s);
+        return e == cudaSuccess ? RT_OK : rt_cuda_fail(e, "cudaEventRecord");
+    }
+    rt_status end(cudaStream_t s)
+    {
+        if (!t) return RT_OK;
+        cudaError_t e = cudaEventRecord(t->events[2 * part + 1], s);
+        ++part;
+        t->n_launches = part;
+        return e == cudaSuccess ? RT_OK : rt_cuda_fail(e, "cudaEventRecord");
+    }
+};
+
+StageArgs stage_args(int kind, const rt_tuning& tu)
+{
+    StageArgs sa = {};
+    sa.kind = kind;
+    sa.refill_min = (kind == ST_FIELD_FULL || kind == ST_FIELD_SPLIT) ? tu.refill_min_field : tu.refill_min;
+    sa.trip = trip_budget(sa.refill_min);
+    return sa;
+}
+
+// The concurrent program of a closest-hit split call (near triangles, field[,
+// far triangles]): the near stage and the field stage are independent except
+// for which record wins, so they run at the same time on two streams.  The
+// near stage (after the query order) traces every query's near sub-interval
+// and lists its hits; the field stage traces every query's field sub-interval
+// from t_1 in input order and writes every record (passing its misses to the
+// far stage, which writes theirs); then k_merge_hits puts each near hit over
+// its query's record, since a near hit is the closest hit.  The records equal
+// those of the stages run in sequence.
 template <bool COUNT>
-rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s, StageTiming* timing)
+rt_status run_concurrent(const TraceArgs& a, const int kinds[3], int n_st, const rt_tuning& tu, DeviceInfo* dev,
+                         cudaStream_t s, Marks& marks)
+{
+    ConcStreams* cs = nullptr;
+    std::lock_guard<std::mutex> lk(g_conc_mu);
+    rt_status st = conc_streams(cs);
+    if (st != RT_OK) return st;
+    const bool far = n_st > 2;
+    const size_t counters_bytes = 8 * kCtrStride * sizeof(unsigned);
+    const size_t order_bytes = rt_order_bytes(a.ob, a.n);
+    const size_t list_bytes = (size_t)a.n * sizeof(HitEntry);
+    const size_t queue_bytes = far ? (size_t)a.n * sizeof(int2) : 0;
+    void* scratch = nullptr;
+    RT_CUDA_TRY(cudaMallocFromPoolAsync(&scratch, counters_bytes + order_bytes + list_bytes + queue_bytes, dev->pool, s));
+    char* base = static_cast<char*>(scratch);
+    unsigned* ctr = reinterpret_cast<unsigned*>(base);
+    HitEntry* list = reinterpret_cast<HitEntry*>(base + counters_bytes + order_bytes);
+    int2* queue = reinterpret_cast<int2*>(base + counters_bytes + order_bytes + list_bytes);
+    rt_status rs = RT_OK;
+    cudaError_t e = cudaMemsetAsync(ctr, 0, counters_bytes, s);
+    if (e == cudaSuccess) e = cudaEventRecord(cs->fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs->near, cs->fork, 0);
+    if (e != cudaSuccess) rs = rt_cuda_fail(e, "concurrent program set-up");
+    rt_tuning tn = tu, tf = tu;
+    if (tu.blocks_per_sm == 0) {
+        tn.blocks_per_sm = kConcNearBlocks;
+        tf.blocks_per_sm = kConcFieldBlocks;
+    }
+    // near stream: the order, then the near stage
+    TraceArgs ao = a;
+    if (rs == RT_OK && order_bytes) {
+        rs = marks.begin(cs->near, RT_STAGE_ORDER);
+        OrderRays src = {};
+        src.rays[0] = a.rays;
+        src.count = 1;
+        if (rs == RT_OK) rs = rt_launch_order(ao, src, base + counters_bytes, cs->near);
+        if (rs == RT_OK) rs = marks.end(cs->near);
+    }
+    // the field stage starts with the near stage, after the order: started
+    // beside the order kernel, its blocks would hold the SMs the order and then
+    // the near stage need
+    if (rs == RT_OK) {
+        e = cudaEventRecord(cs->ordered, cs->near);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs->field, cs->ordered, 0);
+        if (e != cudaSuccess) rs = rt_cuda_fail(e, "concurrent program set-up");
+    }
+    if (rs == RT_OK) {
+        StageArgs sa = stage_args(kinds[0], tu);
+        sa.first = 1;
+        sa.fetch = &ctr[0 * kCtrStride];
+        sa.hit_list = list;
+        sa.hit_count = &ctr[6 * kCtrStride];
+        rs = marks.begin(cs->near, public_kind(kinds[0]));
+        if (rs == RT_OK) rs = launch_stage<COUNT>(ao, sa, tn, dev->sms, cs->near);
+        if (rs == RT_OK) rs = marks.end(cs->near);
+    }
+    // field stream: the field stage over every query in input order, then the far stage
+    TraceArgs af = a;
+    af.qorder = nullptr;
+    if (rs == RT_OK) {
+        StageArgs sa = stage_args(kinds[1], tu);
+        sa.first = 1;
+        sa.fetch = &ctr[1 * kCtrStride];
+        if (far) {
+            sa.out_items = queue;
+            sa.out_count = &ctr[3 * kCtrStride];
+        }
+        rs = marks.begin(cs->field, public_kind(kinds[1]));
+        if (rs == RT_OK) rs = launch_stage<COUNT>(af, sa, tf, dev->sms, cs->field);
+        if (rs == RT_OK) rs = marks.end(cs->field);
+    }
+    if (rs == RT_OK && far) {
+        StageArgs sa = stage_args(kinds[2], tu);
+        sa.in_items = queue;
+        sa.in_count = &ctr[3 * kCtrStride];
+        sa.fetch = &ctr[2 * kCtrStride];
+        rs = marks.begin(cs->field, public_kind(kinds[2]));
+        if (rs == RT_OK) rs = launch_stage<COUNT>(af, sa, tf, dev->sms, cs->field);
+        if (rs == RT_OK) rs = marks.end(cs->field);
+    }
+    // join, then the near hits over the field's records
+    e = cudaEventRecord(cs->near_done, cs->near);
+    if (e == cudaSuccess) e = cudaEventRecord(cs->field_done, cs->field);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, cs->near_done, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, cs->field_done, 0);
+    if (rs == RT_OK && e != cudaSuccess) rs = rt_cuda_fail(e, "concurrent program join");
+    if (rs == RT_OK) {
+        rs = marks.begin(s, RT_STAGE_MERGE);
+        if (rs == RT_OK) {
+            k_merge_hits<<<dev->sms * 4, 256, 0, s>>>(list, &ctr[6 * kCtrStride], a.hits);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) rs = rt_cuda_fail(e, "k_merge_hits");
+        }
+        if (rs == RT_OK) rs = marks.end(s);
+    }
+    e = cudaFreeAsync(scratch, s);
+    if (rs == RT_OK && e != cudaSuccess) rs = rt_cuda_fail(e, "cudaFreeAsync");
+    return rs;
+}
+
+template <bool COUNT>
+rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s, StageTiming* timing,
+                        bool allow_concurrent)
 {
     DeviceInfo* dev = nullptr;
     rt_status st = device_info(dev);
@@ -446,9 +701,14 @@ rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s,
     if (a.n > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "at most 2^31-1 queries per call");
     int kinds[3];
     const int n_st = stage_program(a, kinds);
+    Marks marks{timing};
+    if (timing) timing->n_launches = 0;
+    // closest-hit split calls: the near and field stages at the same time
+    if (allow_concurrent && n_st >= 2 && kinds[0] == ST_BVH_NEAR && !a.any_hit)
+        return run_concurrent<COUNT>(a, kinds, n_st, tu, dev, s, marks);
     // scratch: counters (fetch x3, queue sizes x2), the query order, and two
     // ping-pong queues
-    const size_t counters_bytes = 256;
+    const size_t counters_bytes = 8 * kCtrStride * sizeof(unsigned);
     const size_t order_bytes = rt_order_bytes(a.ob, a.n);
     const size_t queue_bytes = n_st > 1 ? (size_t)a.n * sizeof(int2) : 0;
     const size_t total = counters_bytes + order_bytes + (n_st > 1 ? queue_bytes : 0) + (n_st > 2 ? queue_bytes : 0);
@@ -462,40 +722,25 @@ rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s,
     cudaError_t e = cudaMemsetAsync(ctr, 0, counters_bytes, s);
     if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaMemsetAsync");
     TraceArgs ao = a;  // with the query order
-    int part = 0;      // timed parts: the order, then the stages
     if (order_bytes && rs == RT_OK) {
-        if (timing) {
-            e = cudaEventRecord(timing->events[part], s);
-            if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaEventRecord");
-            timing->kinds[part++] = RT_STAGE_ORDER;
-        }
+        rs = marks.begin(s, RT_STAGE_ORDER);
         OrderRays src = {};
         src.rays[0] = a.rays;
         src.count = 1;
         if (rs == RT_OK) rs = rt_launch_order(ao, src, base + counters_bytes, s);
+        if (rs == RT_OK) rs = marks.end(s);
     }
     for (int k = 0; k < n_st && rs == RT_OK; ++k) {
-        StageArgs sa;
-        sa.kind = kinds[k];
+        StageArgs sa = stage_args(kinds[k], tu);
         sa.first = k == 0;
         sa.in_items = k > 0 ? q[(k - 1) & 1] : nullptr;
-        sa.in_count = k > 0 ? &ctr[3 + ((k - 1) & 1)] : nullptr;
+        sa.in_count = k > 0 ? &ctr[(3 + ((k - 1) & 1)) * kCtrStride] : nullptr;
         sa.out_items = k + 1 < n_st ? q[k & 1] : nullptr;
-        sa.out_count = k + 1 < n_st ? &ctr[3 + (k & 1)] : nullptr;
-        sa.fetch = &ctr[k];
-        sa.refill_min = (kinds[k] == ST_FIELD_FULL || kinds[k] == ST_FIELD_SPLIT) ? tu.refill_min_field : tu.refill_min;
-        sa.trip = trip_budget(sa.refill_min);
-        if (timing) {
-            e = cudaEventRecord(timing->events[part], s);
-            if (e != cudaSuccess) { rs = rt_cuda_fail(e, "cudaEventRecord"); break; }
-            timing->kinds[part++] = public_kind(kinds[k]);
-        }
-        rs = launch_stage<COUNT>(ao, sa, tu, dev->sms, s);
-    }
-    if (timing && rs == RT_OK) {
-        e = cudaEventRecord(timing->events[part], s);
-        if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaEventRecord");
-        timing->n_launches = part;
+        sa.out_count = k + 1 < n_st ? &ctr[(3 + (k & 1)) * kCtrStride] : nullptr;
+        sa.fetch = &ctr[k * kCtrStride];
+        rs = marks.begin(s, public_kind(kinds[k]));
+        if (rs == RT_OK) rs = launch_stage<COUNT>(ao, sa, tu, dev->sms, s);
+        if (rs == RT_OK) rs = marks.end(s);
     }
     e = cudaFreeAsync(scratch, s);
     if (rs == RT_OK && e != cudaSuccess) rs = rt_cuda_fail(e, "cudaFreeAsync");
@@ -519,7 +764,8 @@ void launch_simple(const TraceArgs& a, int L, unsigned nb, int block, cudaStream
 
 }  // namespace
 
-rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, StageTiming* timing)
+rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, StageTiming* timing,
+                          bool allow_concurrent)
 {
     const rt_tuning& tu = rt_current_tuning();
     TraceArgs a = a0;
@@ -528,10 +774,12 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
     // were measured at least as fast as one thread per query on every ray kind
     const bool wavefront = tu.kernel == RT_KERNEL_WAVEFRONT || tu.kernel == RT_KERNEL_AUTO;
     if (wavefront)
-        return counted ? run_wavefront<true>(a, tu, s, timing) : run_wavefront<false>(a, tu, s, timing);
+        return counted ? run_wavefront<true>(a, tu, s, timing, allow_concurrent)
+                       : run_wavefront<false>(a, tu, s, timing, allow_concurrent);
     const int64_t blocks = (a.n + tu.block - 1) / tu.block;
     if (blocks > 0x7fffffffLL) return rt_fail(RT_ERR_INVALID_ARG, "too many rays");
-    int part = 0;
+    Marks marks{timing};
+    if (timing) timing->n_launches = 0;
     void* scratch = nullptr;
     const size_t order_bytes = rt_order_bytes(a.ob, a.n);
     if (order_bytes) {
@@ -540,26 +788,20 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
         rt_status st = device_info(dev);
         if (st != RT_OK) return st;
         RT_CUDA_TRY(cudaMallocFromPoolAsync(&scratch, order_bytes, dev->pool, s));
-        cudaError_t e0 = cudaSuccess;
-        if (timing) {
-            e0 = cudaEventRecord(timing->events[part], s);
-            timing->kinds[part++] = RT_STAGE_ORDER;
-        }
+        st = marks.begin(s, RT_STAGE_ORDER);
         OrderRays src = {};
         src.rays[0] = a.rays;
         src.count = 1;
-        st = e0 == cudaSuccess ? rt_launch_order(a, src, scratch, s) : rt_cuda_fail(e0, "cudaEventRecord");
+        if (st == RT_OK) st = rt_launch_order(a, src, scratch, s);
+        if (st == RT_OK) st = marks.end(s);
         if (st != RT_OK) {
             cudaFreeAsync(scratch, s);
             return st;
         }
     }
+    rt_status st = marks.begin(s, RT_STAGE_ALL);
     cudaError_t e = cudaSuccess;
-    if (timing) {
-        e = cudaEventRecord(timing->events[part], s);
-        timing->kinds[part++] = RT_STAGE_ALL;
-    }
-    if (e == cudaSuccess) {
+    if (st == RT_OK) {
         const unsigned nb = (unsigned)blocks;
         const int L = grid_layout_of(a);
         if (a.wnodes) {
@@ -570,17 +812,14 @@ rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, Sta
             else launch_simple<false, false>(a, L, nb, tu.block, s);
         }
         e = cudaGetLastError();
-    }
-    if (e == cudaSuccess && timing) {
-        e = cudaEventRecord(timing->events[part], s);
-        timing->n_launches = part;
+        if (e == cudaSuccess) st = marks.end(s);
     }
     if (scratch) {
         const cudaError_t ef = cudaFreeAsync(scratch, s);
         if (e == cudaSuccess) e = ef;
     }
     if (e != cudaSuccess) return rt_cuda_fail(e, "simple trace launch");
-    return RT_OK;
+    return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -695,8 +934,7 @@ extern "C" rt_status rt_trace_combined_noalloc(const rt_scene* sc, const rt_sdf*
     st = rt_launch_order(a, src, base + kNoAllocCounterBytes, s);
     if (st != RT_OK) return st;
     for (int k = 0; k < n_st; ++k) {
-        StageArgs sa;
-        sa.kind = kinds[k];
+        StageArgs sa = stage_args(kinds[k], tu);
         sa.first = k == 0;
         sa.in_items = k > 0 ? q[(k - 1) & 1] : nullptr;
         sa.in_count = k > 0 ? &ctr[3 + ((k - 1) & 1)] : nullptr;

@@ -398,7 +398,8 @@ def test_timed_variant_reports_each_launch(tiny):
     a = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p)
     b, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
     assert torch.equal(a, b)
-    assert [x[0] for x in st] == ["order", "bvh_near", "field_split", "bvh_far"]  # the default query order
+    # the query order, then the near stage beside the field and far stages, then the merge of the near hits
+    assert [x[0] for x in st] == ["order", "bvh_near", "field_split", "bvh_far", "merge"]
     assert all(ms > 0 for _, ms in st)
     prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
     try:
@@ -411,7 +412,7 @@ def test_timed_variant_reports_each_launch(tiny):
         c, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
     finally:
         rq.rt_set_tuning(prev)
-    assert torch.equal(a, c) and [x[0] for x in st] == ["bvh_near", "field_split", "bvh_far"]
+    assert torch.equal(a, c) and [x[0] for x in st] == ["bvh_near", "field_split", "bvh_far", "merge"]
 
 
 @pytest.mark.parametrize("any_hit", [False, True])
@@ -428,9 +429,10 @@ def test_zero_multipliers_launch_no_triangle_stage(tiny, any_hit):
     for kw, stages in cases:
         p = rq.split_params(any_hit=any_hit, **kw)
         a, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
-        # the query order runs where the first kernel traces near triangle sub-intervals
-        order = ["order"] if kw["m_near"] > 0 and not any_hit else []
-        assert [x[0] for x in st] == order + stages, kw
+        # with a near sub-interval, a closest-hit call takes the query order and runs the
+        # near stage beside the field stage, then merges the near hits
+        conc = kw["m_near"] > 0 and not any_hit
+        assert [x[0] for x in st] == (["order"] + stages + ["merge"] if conc else stages), kw
         prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
         try:
             b = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p)
