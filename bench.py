@@ -307,6 +307,8 @@ def run_ours(args):
                 return 32 * n_rays + step_bytes * steps + 24 * n_rays
             if stage == "merge":
                 return (32 + 24) * n_bvh_hits
+            if stage == "bvh_near_rest":  # its queries' bytes are counted under bvh_near
+                return 0
         if stage == "all":
             return 32 * n_rays + 24 * n_rays + 64 * nodes + 48 * tris + step_bytes * steps + q_in
         if stage == "bvh_full":
@@ -388,7 +390,8 @@ def run_ours(args):
     kernel_names = {"bvh_near": "k_stage_bvh (near triangle sub-interval)",
                     "field_split": "k_stage_field (distance-field sub-interval)",
                     "bvh_full": "k_stage_bvh", "field_full": "k_stage_field", "all": "k_trace",
-                    "order": "k_order_local (query order)", "merge": "k_merge_hits (near hits over the field's records)"}
+                    "order": "k_order_local (query order)", "merge": "k_merge_hits (near hits over the field's records)",
+                    "bvh_near_rest": "k_stage_bvh (near sub-interval, second launch after the field stage)"}
     stages = {name: {st: {"ms": ms, "algorithmic_bytes": stage_bytes(name, st),
                           "GBps": stage_bytes(name, st) / (ms * 1e-3) / 1e9,
                           "frac_of_hbm": stage_bytes(name, st) / (ms * 1e-3) / 1e9 / peak,

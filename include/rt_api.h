@@ -332,15 +332,17 @@ rt_status rt_trace_combined_counted(const rt_scene* scene, const rt_sdf* sdf, co
 /* Same as rt_trace_combined, and also reports how long each kernel of the
  * call ran: stage_ms[k] for the k-th part (at most 6: the query order where
  * it applies (see rt_tuning.order_bits), then one launch per sub-interval
- * kind with the wavefront kernels and, for closest-hit split calls, the
- * merge of the near hits; or the one launch of the simple kernel), *n_stages
+ * kind with the wavefront kernels and, for closest-hit split calls, a second
+ * near stage after the field (RT_STAGE_BVH_NEAR_REST) and the merge of the
+ * near hits; or the one launch of the simple kernel), *n_stages
  * the number of parts, stage_kind[k] RT_STAGE_* (nullable).  stage_ms and
  * stage_kind hold 6 entries.  Each part is timed by CUDA events on the
  * stream that ran it; in a closest-hit split call the near and field stages
  * run at the same time on two streams, so their times overlap.  The call
  * synchronises `stream`.  Used to measure per-kernel throughput. */
 enum { RT_STAGE_ALL = 0, RT_STAGE_BVH_FULL = 1, RT_STAGE_BVH_NEAR = 2, RT_STAGE_BVH_FAR = 3,
-       RT_STAGE_FIELD_FULL = 4, RT_STAGE_FIELD_SPLIT = 5, RT_STAGE_ORDER = 6, RT_STAGE_MERGE = 7 };
+       RT_STAGE_FIELD_FULL = 4, RT_STAGE_FIELD_SPLIT = 5, RT_STAGE_ORDER = 6, RT_STAGE_MERGE = 7,
+       RT_STAGE_BVH_NEAR_REST = 8 };
 rt_status rt_trace_combined_timed(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
                                   const rt_split_params* params, rt_hit* d_hits, float stage_ms[6],
                                   int32_t stage_kind[6], int32_t* n_stages, void* stream);

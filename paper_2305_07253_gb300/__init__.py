@@ -398,7 +398,7 @@ def rt_trace_batches(scene: Scene | None, sdf: Sdf | None, batches, stream=None)
 
 
 STAGE_NAMES = {0: "all", 1: "bvh_full", 2: "bvh_near", 3: "bvh_far", 4: "field_full", 5: "field_split", 6: "order",
-               7: "merge"}
+               7: "merge", 8: "bvh_near_rest"}
 
 
 def rt_trace_combined_timed(scene: Scene | None, sdf: Sdf | None, rays: torch.Tensor, params: rt_split_params,

@@ -671,6 +671,20 @@ rt_status run_concurrent(const TraceArgs& a, const int kinds[3], int n_st, const
         if (rs == RT_OK) rs = launch_stage<COUNT>(af, sa, tf, dev->sms, cs->field);
         if (rs == RT_OK) rs = marks.end(cs->field);
     }
+    // then a second near stage on the field stream, at full residency, sharing
+    // the first's work counter and hit list: when the near sub-intervals are the
+    // larger share of the work (short rays), it finishes them once the field
+    // is done; otherwise it finds the counter drained and ends at once
+    if (rs == RT_OK) {
+        StageArgs sa = stage_args(kinds[0], tu);
+        sa.first = 1;
+        sa.fetch = &ctr[0 * kCtrStride];
+        sa.hit_list = list;
+        sa.hit_count = &ctr[6 * kCtrStride];
+        rs = marks.begin(cs->field, RT_STAGE_BVH_NEAR_REST);
+        if (rs == RT_OK) rs = launch_stage<COUNT>(ao, sa, tu, dev->sms, cs->field);
+        if (rs == RT_OK) rs = marks.end(cs->field);
+    }
     // join, then the near hits over the field's records
     e = cudaEventRecord(cs->near_done, cs->near);
     if (e == cudaSuccess) e = cudaEventRecord(cs->field_done, cs->field);
@@ -703,8 +717,9 @@ rt_status run_wavefront(const TraceArgs& a, const rt_tuning& tu, cudaStream_t s,
     const int n_st = stage_program(a, kinds);
     Marks marks{timing};
     if (timing) timing->n_launches = 0;
-    // closest-hit split calls: the near and field stages at the same time
-    if (allow_concurrent && n_st >= 2 && kinds[0] == ST_BVH_NEAR && !a.any_hit)
+    // closest-hit split calls: the near and field stages at the same time (not
+    // with m_near = +inf, where the field sub-interval is empty for every query)
+    if (allow_concurrent && n_st >= 2 && kinds[0] == ST_BVH_NEAR && !a.any_hit && !isinf(a.m_near))
         return run_concurrent<COUNT>(a, kinds, n_st, tu, dev, s, marks);
     // scratch: counters (fetch x3, queue sizes x2), the query order, and two
     // ping-pong queues

@@ -162,8 +162,8 @@ def test_timed_call_reports_the_order(world):
         h31, st31 = rq.rt_trace_combined_timed(scene, sdf, rd[:31], p)  # below 64 queries: not ordered
     finally:
         rq.rt_set_tuning(prev)
-    assert [x[0] for x in st] == ["order", "bvh_near", "field_split", "merge"]
-    assert [x[0] for x in st31] == ["bvh_near", "field_split", "merge"]
+    assert [x[0] for x in st] == ["order", "bvh_near", "field_split", "bvh_near_rest", "merge"]
+    assert [x[0] for x in st31] == ["bvh_near", "field_split", "bvh_near_rest", "merge"]
     assert all(ms > 0 and math.isfinite(ms) for _, ms in st)
     assert torch.equal(h, _trace(rq, scene, sdf, rd, p, order_bits=0))
     assert torch.equal(h31, h[:31])

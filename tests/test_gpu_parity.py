@@ -398,8 +398,9 @@ def test_timed_variant_reports_each_launch(tiny):
     a = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p)
     b, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
     assert torch.equal(a, b)
-    # the query order, then the near stage beside the field and far stages, then the merge of the near hits
-    assert [x[0] for x in st] == ["order", "bvh_near", "field_split", "bvh_far", "merge"]
+    # the query order, then the near stage beside the field and far stages, the near
+    # stage's second launch after them, then the merge of the near hits
+    assert [x[0] for x in st] == ["order", "bvh_near", "field_split", "bvh_far", "bvh_near_rest", "merge"]
     assert all(ms > 0 for _, ms in st)
     prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
     try:
@@ -412,7 +413,7 @@ def test_timed_variant_reports_each_launch(tiny):
         c, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
     finally:
         rq.rt_set_tuning(prev)
-    assert torch.equal(a, c) and [x[0] for x in st] == ["bvh_near", "field_split", "bvh_far", "merge"]
+    assert torch.equal(a, c) and [x[0] for x in st] == ["bvh_near", "field_split", "bvh_far", "bvh_near_rest", "merge"]
 
 
 @pytest.mark.parametrize("any_hit", [False, True])
@@ -429,10 +430,10 @@ def test_zero_multipliers_launch_no_triangle_stage(tiny, any_hit):
     for kw, stages in cases:
         p = rq.split_params(any_hit=any_hit, **kw)
         a, st = rq.rt_trace_combined_timed(tiny.scene, tiny.sdf, tiny.rays_d, p)
-        # with a near sub-interval, a closest-hit call takes the query order and runs the
-        # near stage beside the field stage, then merges the near hits
+        # with a near sub-interval, a closest-hit call takes the query order, runs the
+        # near stage beside the field stage (and again after it), then merges the near hits
         conc = kw["m_near"] > 0 and not any_hit
-        assert [x[0] for x in st] == (["order"] + stages + ["merge"] if conc else stages), kw
+        assert [x[0] for x in st] == (["order"] + stages + ["bvh_near_rest", "merge"] if conc else stages), kw
         prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
         try:
             b = rq.rt_trace_combined(tiny.scene, tiny.sdf, tiny.rays_d, p)
