@@ -313,11 +313,11 @@ rt_status rt_trace_sdf(const rt_sdf* sdf, const rt_ray* d_rays, int64_t n, const
 
 /* The combined query (Eq. 2 and the rules of rt_split_params) for n rays.
  * `params` is read on the host during the call.  With the stage kernels, a
- * closest-hit split call runs its near triangle stage and its field stage at
- * the same time, on two streams of the library forked from `stream` and
- * joined back into it by events (calls on one device share these streams; a
- * lock keeps each call's launches together).  The records are those of the
- * sub-intervals traced in order. */
+ * closest-hit split call with 0 < m_near < inf runs its near triangle stage
+ * and its field stage at the same time, on two streams of the library forked
+ * from `stream` and joined back into it by events (calls on one device share
+ * these streams; a lock keeps each call's launches together).  The records
+ * are those of the sub-intervals traced in order. */
 rt_status rt_trace_combined(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
                             const rt_split_params* params, rt_hit* d_hits, void* stream);
 
@@ -389,7 +389,11 @@ enum { RT_MAX_BATCHES = 16 };
  * persistent stage launches (triangles, field, triangles, triangles): every query follows
  * its own batch's sub-interval program through it, so uneven batches share the
  * kernels instead of each paying its own launches and tails, and a frame is a
- * fixed sequence of launches that can be captured in a CUDA graph.
+ * fixed sequence of launches that can be captured in a CUDA graph.  When a
+ * batch has closest-hit split queries with 0 < m_near < inf, the first two
+ * launches run at the same time on the library's two streams, as in
+ * rt_trace_combined, and the field launch starts those queries at t_1 without
+ * waiting for their near result.
  *   - at most RT_MAX_BATCHES batches, at most 2^31-1 queries in total;
  *   - mode, any_hit, m_near and m_far may differ per batch; max_steps,
  *     hit_eps_vox, min_step_vox and refine_root must be equal in all batches;

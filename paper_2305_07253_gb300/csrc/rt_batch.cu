@@ -12,6 +12,16 @@
 // The pipeline is four persistent launches -- triangles, field, triangles,
 // triangles -- which covers every program above.  A query whose next sub-interval is not of
 // a launch's kind passes through it to the next launch's queue.
+//
+// When some batch has closest-hit near sub-intervals (0 < m_near < inf), the
+// first two launches run at the same time instead (the concurrent program,
+// rt_internal.cuh): the triangle launch takes the queries that start with
+// triangles, writes the records of triangles-only queries and lists the near
+// hits; the field launch takes every query with a field sub-interval straight
+// from the input, a closest-hit split query from t_1 as if its near
+// sub-interval had missed.  The last two launches follow the field launch, a
+// second triangle launch takes what the first left, and k_merge_hits puts the
+// near hits over the records.
 #include <mutex>
 
 #include "rt_trace_dev.cuh"
@@ -48,7 +58,11 @@ struct Pipe {
     unsigned* fetch;
     int32_t refill_min;
     int32_t trip;             // traversal iterations between refill checks (trip_budget)
+    int32_t conc;             // kSequential, or the first triangle / field launch of the concurrent program
+    HitEntry* hit_list;       // kConcTri: near hits of closest-hit split queries
+    unsigned* hit_count;
 };
+constexpr int32_t kSequential = 0, kConcTri = 1, kConcField = 2;
 
 __device__ __forceinline__ unsigned lane() { return threadIdx.x & 31u; }
 
@@ -130,6 +144,7 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
     int64_t qi = 0;
     uint32_t flags = 0;
     bool any_hit = false;
+    bool listed = false;     // kConcTri: a closest-hit near sub-interval, whose hit goes to the list
     BvhRay r;
     typename TravOf<WIDE>::state s;
     Hit best;
@@ -148,11 +163,16 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
             qi = g - e.offset;
             hits = e.hits;
             const int seg = seg_at(e.mode, e.any_hit, p);
+            listed = pp.conc == kConcTri && seg == SEG_B_NEAR;
             const float4 r0 = __ldg(e.rays + 2 * qi), r1 = __ldg(e.rays + 2 * qi + 1);
             const float3 o = make_float3(r0.x, r0.y, r0.z), d = make_float3(r1.x, r1.y, r1.z);
             const float tmin = r0.w, tmax = r1.w;
             has_next = false;
-            if (!pp.in_items && !valid_query(o, d, tmin, tmax)) {
+            if (pp.conc == kConcTri && seg_is_field(seg)) {
+                // the field launch beside this one takes the query
+            } else if (!pp.in_items && !valid_query(o, d, tmin, tmax)) {
+                // an invalid split query's miss is written by the field launch
+                done = !listed;
                 done = true;       // invalid: a miss, program over
             } else if (seg_is_field(seg)) {
                 pass = true;       // not this launch's kind: hand on unchanged
@@ -189,7 +209,13 @@ __global__ void k_batch_bvh(const TraceArgs a, const BatchTable tb, const Pipe p
         const bool more = (pass || (done && !found)) && has_next;
         const bool fwd = more && pp.out_items != nullptr;
         forward_item(pp, fwd, pack_item(g, flags, pass ? p : p + 1));
-        if ((done || pass) && !fwd) {
+        if (pp.conc == kConcTri) {
+            // a listed near sub-interval writes no record: its hit, or the flags
+            // of its miss, go to the list
+            if (done && listed && !found) best.prim = kFlagsOnly;
+            append_hit_entry(pp.hit_list, pp.hit_count, done && listed && (found || flags != 0u), hits + qi, best, flags);
+        }
+        if ((done || pass) && !fwd && !listed) {
             if (found) store_hit(hits + qi, best.t, best.prim, best.u, best.v, RT_TRACER_BVH, flags);
             else store_hit(hits + qi, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
         }
@@ -230,13 +256,23 @@ __global__ void __maxnreg__(40) k_batch_field(const TraceArgs a, const BatchTabl
             const BatchEntry e = stb[b];
             qi = g - e.offset;
             hits = e.hits;
-            const int seg = seg_at(e.mode, e.any_hit, p);
+            int seg = seg_at(e.mode, e.any_hit, p);
+            bool skip = false;
+            if (pp.conc == kConcField) {
+                // a closest-hit split query from t_1, as if its near sub-interval
+                // had missed (the triangle launch beside this one traces that);
+                // triangles-only queries are the triangle launch's alone
+                if (seg == SEG_B_NEAR) seg = seg_at(e.mode, e.any_hit, ++p);
+                skip = seg == SEG_B_FULL;
+            }
             const float4 r0 = __ldg(e.rays + 2 * qi), r1 = __ldg(e.rays + 2 * qi + 1);
             o = make_float3(r0.x, r0.y, r0.z);
             d = make_float3(r1.x, r1.y, r1.z);
             const float tmin = r0.w, tmax = r1.w;
             has_next = false;
-            if (!pp.in_items && !valid_query(o, d, tmin, tmax)) {
+            if (skip) {
+                // nothing to do here
+            } else if (!pp.in_items && !valid_query(o, d, tmin, tmax)) {
                 done = true;
             } else if (!seg_is_field(seg)) {
                 pass = true;
@@ -396,21 +432,48 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
     rt_apply_layout(a, tu);
     a.n = total;
     a.counters = nullptr;
-    bool order = false;  // the query order, if some batch starts with near triangle sub-intervals
-    for (int k = 0; k < n_batches; ++k) order |= batches[k].n > 0 && rt_order_applies(batches[k].params);
-    if (!order) a.ob.bits = 0;
+    // closest-hit near sub-intervals in some batch: the query order (unless the
+    // tuning turns it off) and the concurrent program
+    bool near_split = false;
+    int64_t n_listed = 0;  // queries whose near hit may be listed
+    for (int k = 0; k < n_batches; ++k) {
+        const bool ns = batches[k].n > 0 && rt_order_applies(batches[k].params);
+        near_split |= ns;
+        const rt_split_params& p = batches[k].params;
+        if ((p.mode == RT_MODE_SPLIT1 || p.mode == RT_MODE_SPLIT2) && !p.any_hit) n_listed += batches[k].n;
+    }
+    if (!near_split) a.ob.bits = 0;
+    const bool conc = near_split;
     cudaStream_t s = (cudaStream_t)stream;
 
     const size_t ctr_bytes = 256, qbytes = (size_t)total * sizeof(int2), order_bytes = rt_order_bytes(a.ob, total);
+    const size_t list_bytes = conc ? (size_t)n_listed * sizeof(HitEntry) : 0;
     void* scratch = nullptr;
-    RT_CUDA_TRY(cudaMallocFromPoolAsync(&scratch, ctr_bytes + order_bytes + 2 * qbytes, dev->pool, s));
+    RT_CUDA_TRY(cudaMallocFromPoolAsync(&scratch, ctr_bytes + order_bytes + 2 * qbytes + list_bytes, dev->pool, s));
     char* base = static_cast<char*>(scratch);
     unsigned* ctr = reinterpret_cast<unsigned*>(base);
     int2* q[2] = {reinterpret_cast<int2*>(base + ctr_bytes + order_bytes),
                   reinterpret_cast<int2*>(base + ctr_bytes + order_bytes + qbytes)};
+    HitEntry* list = reinterpret_cast<HitEntry*>(base + ctr_bytes + order_bytes + 2 * qbytes);
+    unsigned* hit_count = &ctr[16];
     rt_status rs = RT_OK;
     cudaError_t e = cudaMemsetAsync(ctr, 0, ctr_bytes, s);
     if (e != cudaSuccess) rs = rt_cuda_fail(e, "cudaMemsetAsync");
+
+    ConcStreams* cs = nullptr;
+    std::unique_lock<std::mutex> lk(rt_conc_mutex(), std::defer_lock);
+    cudaStream_t s_tri = s, s_field = s;  // the streams of the first two launches
+    if (conc && rs == RT_OK) {
+        lk.lock();
+        rs = rt_conc_streams(cs);
+        if (rs == RT_OK) {
+            e = cudaEventRecord(cs->fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs->near, cs->fork, 0);
+            if (e != cudaSuccess) rs = rt_cuda_fail(e, "concurrent program set-up");
+            s_tri = cs->near;
+            s_field = cs->field;
+        }
+    }
     if (order_bytes && rs == RT_OK) {
         // the queries of every batch in one order, as one index space
         OrderRays src = {};
@@ -419,25 +482,47 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
             src.offset[k] = tb.e[k].offset;
         }
         src.count = n_batches;
-        rs = rt_launch_order(a, src, base + ctr_bytes, s);
+        rs = rt_launch_order(a, src, base + ctr_bytes, s_tri);
     }
+    if (conc && rs == RT_OK) {
+        // the field launch starts after the order kernel, whose SMs its blocks would take
+        e = cudaEventRecord(cs->ordered, cs->near);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs->field, cs->ordered, 0);
+        if (e != cudaSuccess) rs = rt_cuda_fail(e, "concurrent program set-up");
+    }
+    TraceArgs af = a;  // the concurrent field launch reads the input in its own order
+    if (conc) af.qorder = nullptr;
     // launches: triangles, field, triangles, triangles; ctr[k] = fetch counter of
-    // launch k, ctr[8 + k] = number of queries launch k hands on (queues ping-pong)
-    for (int k = 0; k < kLaunches && rs == RT_OK; ++k) {
+    // launch k, ctr[8 + k] = number of queries launch k hands on (queues ping-pong);
+    // in the concurrent program the first launch hands nothing on, and a fifth
+    // (a second first launch, sharing its counter and list) follows the fourth
+    const int n_launch = conc ? kLaunches + 1 : kLaunches;
+    for (int k = 0; k < n_launch && rs == RT_OK; ++k) {
+        const bool helper = k == kLaunches;
+        const int kk = helper ? 0 : k;
         Pipe pp;
-        pp.in_items = k > 0 ? q[(k - 1) & 1] : nullptr;
-        pp.in_count = k > 0 ? &ctr[8 + k - 1] : nullptr;
+        // the concurrent field launch, like the first, takes every query from the input
+        const bool from_input = kk == 0 || (conc && kk == 1);
+        pp.in_items = from_input ? nullptr : q[(kk - 1) & 1];
+        pp.in_count = from_input ? nullptr : &ctr[8 + kk - 1];
         pp.n_first = (unsigned)total;
-        pp.out_items = k + 1 < kLaunches ? q[k & 1] : nullptr;
-        pp.out_count = k + 1 < kLaunches ? &ctr[8 + k] : nullptr;
-        pp.fetch = &ctr[k];
-        pp.refill_min = k == 1 ? tu.refill_min_field : tu.refill_min;
+        pp.out_items = kk + 1 < kLaunches && !(conc && kk == 0) ? q[kk & 1] : nullptr;
+        pp.out_count = pp.out_items ? &ctr[8 + kk] : nullptr;
+        pp.fetch = &ctr[kk];
+        pp.refill_min = kk == 1 ? tu.refill_min_field : tu.refill_min;
         pp.trip = trip_budget(pp.refill_min);
-        if (k == 1 && need_grid) {
+        pp.conc = !conc ? kSequential : (kk == 0 ? kConcTri : (kk == 1 ? kConcField : kSequential));
+        pp.hit_list = list;
+        pp.hit_count = hit_count;
+        rt_tuning tk = tu;
+        if (conc && tu.blocks_per_sm == 0 && !helper && kk <= 1) tk.blocks_per_sm = kk == 0 ? kConcNearBlocks : kConcFieldBlocks;
+        const cudaStream_t sk = !conc ? s : (k == 0 ? s_tri : s_field);
+        const TraceArgs& ak = kk == 1 ? af : a;
+        if (kk == 1 && need_grid) {
             switch (grid_layout_of(a)) {
-#define RT_BATCH_FIELD(LL)                                                                            \
-    case LL:                                                                                          \
-        k_batch_field<false, LL><<<grid_for(k_batch_field<false, LL>, tu, dev->sms), tu.block, 0, s>>>(a, tb, pp); \
+#define RT_BATCH_FIELD(LL)                                                                                     \
+    case LL:                                                                                                   \
+        k_batch_field<false, LL><<<grid_for(k_batch_field<false, LL>, tk, dev->sms), tu.block, 0, sk>>>(ak, tb, pp); \
         break;
                 RT_BATCH_FIELD(GL_PLAIN_F32)
                 RT_BATCH_FIELD(GL_PLAIN_F16)
@@ -449,17 +534,27 @@ extern "C" rt_status rt_trace_batches(const rt_scene* sc, const rt_sdf* sdf, con
                 RT_BATCH_FIELD(GL_CASC_F16)
 #undef RT_BATCH_FIELD
             }
-        } else if (k == 1) {
+        } else if (kk == 1) {
             // no batch uses the field: pass everything through an empty field launch
-            k_batch_field<false, GL_PLAIN_F32><<<grid_for(k_batch_field<false, GL_PLAIN_F32>, tu, dev->sms), tu.block, 0, s>>>(
-                a, tb, pp);
+            k_batch_field<false, GL_PLAIN_F32><<<grid_for(k_batch_field<false, GL_PLAIN_F32>, tk, dev->sms), tu.block, 0, sk>>>(
+                ak, tb, pp);
         } else if (a.wnodes) {
-            k_batch_bvh<false, true><<<grid_for(k_batch_bvh<false, true>, tu, dev->sms), tu.block, 0, s>>>(a, tb, pp);
+            k_batch_bvh<false, true><<<grid_for(k_batch_bvh<false, true>, tk, dev->sms), tu.block, 0, sk>>>(ak, tb, pp);
         } else {
-            k_batch_bvh<false, false><<<grid_for(k_batch_bvh<false, false>, tu, dev->sms), tu.block, 0, s>>>(a, tb, pp);
+            k_batch_bvh<false, false><<<grid_for(k_batch_bvh<false, false>, tk, dev->sms), tu.block, 0, sk>>>(ak, tb, pp);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) rs = rt_cuda_fail(e, "stage launch");
+    }
+    if (conc && cs) {
+        // join (also after a failed launch, so that no library stream is left
+        // waiting on this call), then the near hits over the records
+        e = cudaEventRecord(cs->near_done, cs->near);
+        if (e == cudaSuccess) e = cudaEventRecord(cs->field_done, cs->field);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, cs->near_done, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, cs->field_done, 0);
+        if (rs == RT_OK && e != cudaSuccess) rs = rt_cuda_fail(e, "concurrent program join");
+        if (rs == RT_OK) rs = rt_launch_merge_hits(list, hit_count, dev->sms, s);
     }
     e = cudaFreeAsync(scratch, s);
     if (rs == RT_OK && e != cudaSuccess) rs = rt_cuda_fail(e, "cudaFreeAsync");

@@ -34,6 +34,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/rt_api.h"
 
 #define RT_STACK_DEPTH 64
@@ -194,6 +196,50 @@ size_t rt_order_bytes(const OrderBox& ob, int64_t n);
 // Order queries 0..n-1 of a (rt_order.cu) into `scratch` (rt_order_bytes,
 // 256-byte aligned); on success a.qorder points into it.  Enqueued on s.
 rt_status rt_launch_order(TraceArgs& a, const OrderRays& src, void* scratch, cudaStream_t s);
+// The concurrent programs (rt_trace.cu for one call, rt_batch.cu for mixed
+// batches): closest-hit near triangle sub-intervals run beside the field
+// sub-intervals, which start at t_1 without waiting for the near result.  The
+// near stage lists its hits; afterwards k_merge_hits writes each over the
+// record the later stages left (a near hit lies before t_1, so it is the
+// closest, Section 2).  A near miss that raised flags lists an entry with prim
+// kFlagsOnly, whose flags are ORed into the record.
+constexpr int32_t kFlagsOnly = -2;
+struct HitEntry {
+    rt_hit* dst;  // the query's record
+    uint32_t flags;
+    float t, u, v;
+    int32_t prim;
+    int32_t pad;
+};
+static_assert(sizeof(HitEntry) == 32, "one 32-byte entry per hit");
+// Two library streams per device for the concurrent programs: near (highest
+// priority) and field (lowest), with the events that fork and join them.
+// Callers hold rt_conc_mutex() from the fork to the join.
+struct ConcStreams {
+    cudaStream_t near = nullptr, field = nullptr;
+    cudaEvent_t fork = nullptr, ordered = nullptr, near_done = nullptr, field_done = nullptr;
+    bool ready = false;
+};
+std::mutex& rt_conc_mutex();
+rt_status rt_conc_streams(ConcStreams*& out);
+// k_merge_hits over the *count entries of list, on s
+rt_status rt_launch_merge_hits(const HitEntry* list, const unsigned* count, int sms, cudaStream_t s);
+// Resident blocks of 128 threads per SM of the two concurrent stages when the
+// tuning leaves them free.  Both kernels are persistent, so their blocks must
+// fit in an SM side by side (registers: near 2 x 128 x 56 (64 for the batch
+// kernel) + field 9 x 128 x 40, at most 62,464 of 65,536), or the later launch
+// waits for the earlier one's end.  Measured on the 1080p GI workload, whole
+// call: near 2 + field 9 0.595 ms, 3 + 9 0.608, 2 + 10 0.603, 2 + 8 0.611,
+// 4 + 7 0.661, 1 + 11 1.015; the stages in sequence 0.662.
+#ifndef RT_CONC_NEAR_BLOCKS
+#define RT_CONC_NEAR_BLOCKS 2
+#endif
+#ifndef RT_CONC_FIELD_BLOCKS
+#define RT_CONC_FIELD_BLOCKS 9
+#endif
+constexpr int kConcNearBlocks = RT_CONC_NEAR_BLOCKS;
+constexpr int kConcFieldBlocks = RT_CONC_FIELD_BLOCKS;
+
 // allow_concurrent = false: the stages of a closest-hit split call run in
 // sequence on s (no internal streams), as the pieces of rt_trace_combined_host need
 rt_status rt_launch_trace(const TraceArgs& a, bool counted, cudaStream_t s, StageTiming* timing = nullptr,

@@ -107,20 +107,6 @@ __global__ void k_trace(const TraceArgs a)
 // ---------------------------------------------------------------------------
 enum StageKind { ST_BVH_FULL = 0, ST_BVH_NEAR = 1, ST_BVH_FAR = 2, ST_FIELD_FULL = 3, ST_FIELD_SPLIT = 4 };
 
-// A near triangle hit of the concurrent program (run_wavefront): the query and
-// its record, copied over the field's record by k_merge_hits.  A near miss
-// that raised flags leaves an entry with prim kFlagsOnly, whose flags are
-// added to the record (in sequence they would travel on to the field stage).
-constexpr int32_t kFlagsOnly = -2;
-struct HitEntry {
-    int32_t query;
-    uint32_t flags;
-    float t, u, v;
-    int32_t prim;
-    int32_t pad[2];
-};
-static_assert(sizeof(HitEntry) == 32, "one 32-byte entry per hit");
-
 struct StageArgs {
     int32_t kind;
     int32_t first;             // input = every query 0..n-1 (validity is checked here)
@@ -186,28 +172,6 @@ __device__ __forceinline__ void forward(const StageArgs& st, bool fwd, int query
     if (lane_id() == (unsigned)leader) base = atomicAdd(st.out_count, (unsigned)__popc(m));
     base = __shfl_sync(kFull, base, leader);
     if (fwd) st.out_items[base + __popc(m & ((1u << lane_id()) - 1u))] = make_int2(query, (int)flags);
-}
-
-// Append the lanes with `hit` set to the hit list (one atomic per warp).
-__device__ __forceinline__ void append_hits(const StageArgs& st, bool hit, int query, const Hit& best, uint32_t flags)
-{
-    const unsigned m = __ballot_sync(kFull, hit);
-    if (m == 0) return;
-    const int leader = __ffs(m) - 1;
-    unsigned base = 0;
-    if (lane_id() == (unsigned)leader) base = atomicAdd(st.hit_count, (unsigned)__popc(m));
-    base = __shfl_sync(kFull, base, leader);
-    if (hit) {
-        HitEntry e;
-        e.query = query;
-        e.flags = flags;
-        e.t = best.t;
-        e.u = best.u;
-        e.v = best.v;
-        e.prim = best.prim;
-        e.pad[0] = e.pad[1] = 0;
-        st.hit_list[base + __popc(m & ((1u << lane_id()) - 1u))] = e;
-    }
 }
 
 // Take new queries for the idle lanes when enough of them are idle (or all are).
@@ -285,7 +249,7 @@ __global__ void __maxnreg__(RT_BVH_REGS) k_stage_bvh(const TraceArgs a, const St
             // concurrent program: the field stage writes every record; a near hit
             // replaces it, a near miss's flags join it (k_merge_hits)
             if (done && !found) best.prim = kFlagsOnly;
-            append_hits(st, done && (found || flags != 0u), query, best, flags);
+            append_hit_entry(st.hit_list, st.hit_count, done && (found || flags != 0u), a.hits + query, best, flags);
         } else if (done && !fwd) {
             if (found) store_hit(a.hits + query, best.t, best.prim, best.u, best.v, RT_TRACER_BVH, flags);
             else store_hit(a.hits + query, __int_as_float(0x7f800000), -1, 0.f, 0.f, RT_TRACER_MISS, flags);
@@ -297,17 +261,16 @@ __global__ void __maxnreg__(RT_BVH_REGS) k_stage_bvh(const TraceArgs a, const St
 
 // The near hits of the concurrent program over the field's records: a hit in
 // the near sub-interval is the closest hit (Section 2: sub-intervals in order)
-__global__ void __launch_bounds__(256) k_merge_hits(const HitEntry* __restrict__ list, const unsigned* __restrict__ count,
-                                                    rt_hit* __restrict__ hits)
+__global__ void __launch_bounds__(256) k_merge_hits(const HitEntry* __restrict__ list, const unsigned* __restrict__ count)
 {
     const unsigned n = *count;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const HitEntry e = list[i];
         if (e.prim == kFlagsOnly) {
-            uint32_t* f = reinterpret_cast<uint32_t*>(hits + e.query) + 5;  // the record's flags word
+            uint32_t* f = reinterpret_cast<uint32_t*>(e.dst) + 5;  // the record's flags word
             *f |= e.flags;
         } else {
-            store_hit(hits + e.query, e.t, e.prim, e.u, e.v, RT_TRACER_BVH, e.flags);
+            store_hit(e.dst, e.t, e.prim, e.u, e.v, RT_TRACER_BVH, e.flags);
         }
     }
 }
@@ -497,54 +460,10 @@ int32_t public_kind(int k)
     }
 }
 
-// Streams and events of the concurrent program, one set per device, and the
+// Streams and events of the concurrent programs, one set per device, and the
 // lock that keeps one call's fork-to-join sequence of launches together.
-struct ConcStreams {
-    cudaStream_t near = nullptr, field = nullptr;
-    cudaEvent_t fork = nullptr, ordered = nullptr, near_done = nullptr, field_done = nullptr;
-    bool ready = false;
-};
 std::mutex g_conc_mu;
 ConcStreams g_conc[64];
-
-rt_status conc_streams(ConcStreams*& out)
-{
-    int dev = 0;
-    RT_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return rt_fail(RT_ERR_INVALID_ARG, "device %d out of range", dev);
-    ConcStreams& c = g_conc[dev];
-    if (!c.ready) {
-        // the near stream at the highest priority: when both stages have blocks
-        // waiting for room (after the order kernel), the near stage's are placed
-        // first, and the field stage's fill the rest of each SM
-        int least = 0, greatest = 0;
-        RT_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-        RT_CUDA_TRY(cudaStreamCreateWithPriority(&c.near, cudaStreamNonBlocking, greatest));
-        RT_CUDA_TRY(cudaStreamCreateWithPriority(&c.field, cudaStreamNonBlocking, least));
-        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming));
-        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.ordered, cudaEventDisableTiming));
-        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.near_done, cudaEventDisableTiming));
-        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.field_done, cudaEventDisableTiming));
-        c.ready = true;
-    }
-    out = &c;
-    return RT_OK;
-}
-
-// Resident blocks per SM of the two concurrent stages when the tuning leaves
-// them free.  Both kernels are persistent, so their blocks must fit in an SM
-// side by side (registers: 2 x 128 x 56 + 9 x 128 x 40 = 60,416 of 65,536),
-// or the later launch waits for the earlier one's end.  Measured on the 1080p
-// GI workload, whole call: near 2 + field 9 0.595 ms, 3 + 9 0.608, 3 + 8
-// 0.614, 4 + 7 0.661; the stages in sequence 0.662.
-#ifndef RT_CONC_NEAR_BLOCKS
-#define RT_CONC_NEAR_BLOCKS 2
-#endif
-#ifndef RT_CONC_FIELD_BLOCKS
-#define RT_CONC_FIELD_BLOCKS 9
-#endif
-constexpr int kConcNearBlocks = RT_CONC_NEAR_BLOCKS;
-constexpr int kConcFieldBlocks = RT_CONC_FIELD_BLOCKS;
 
 // Work counters sit 128 bytes apart: atomics of different counters, from one
 // kernel or from two running side by side, then never share an L2 line.
@@ -596,7 +515,7 @@ rt_status run_concurrent(const TraceArgs& a, const int kinds[3], int n_st, const
 {
     ConcStreams* cs = nullptr;
     std::lock_guard<std::mutex> lk(g_conc_mu);
-    rt_status st = conc_streams(cs);
+    rt_status st = rt_conc_streams(cs);
     if (st != RT_OK) return st;
     const bool far = n_st > 2;
     const size_t counters_bytes = 8 * kCtrStride * sizeof(unsigned);
@@ -693,11 +612,7 @@ rt_status run_concurrent(const TraceArgs& a, const int kinds[3], int n_st, const
     if (rs == RT_OK && e != cudaSuccess) rs = rt_cuda_fail(e, "concurrent program join");
     if (rs == RT_OK) {
         rs = marks.begin(s, RT_STAGE_MERGE);
-        if (rs == RT_OK) {
-            k_merge_hits<<<dev->sms * 4, 256, 0, s>>>(list, &ctr[6 * kCtrStride], a.hits);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) rs = rt_cuda_fail(e, "k_merge_hits");
-        }
+        if (rs == RT_OK) rs = rt_launch_merge_hits(list, &ctr[6 * kCtrStride], dev->sms, s);
         if (rs == RT_OK) rs = marks.end(s);
     }
     e = cudaFreeAsync(scratch, s);
@@ -778,6 +693,39 @@ void launch_simple(const TraceArgs& a, int L, unsigned nb, int block, cudaStream
 }
 
 }  // namespace
+
+std::mutex& rt_conc_mutex() { return g_conc_mu; }
+
+rt_status rt_conc_streams(ConcStreams*& out)
+{
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return rt_fail(RT_ERR_INVALID_ARG, "device %d out of range", dev);
+    ConcStreams& c = g_conc[dev];
+    if (!c.ready) {
+        // the near stream at the highest priority: when both stages have blocks
+        // waiting for room (after the order kernel), the near stage's are placed
+        // first, and the field stage's fill the rest of each SM
+        int least = 0, greatest = 0;
+        RT_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        RT_CUDA_TRY(cudaStreamCreateWithPriority(&c.near, cudaStreamNonBlocking, greatest));
+        RT_CUDA_TRY(cudaStreamCreateWithPriority(&c.field, cudaStreamNonBlocking, least));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.ordered, cudaEventDisableTiming));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.near_done, cudaEventDisableTiming));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&c.field_done, cudaEventDisableTiming));
+        c.ready = true;
+    }
+    out = &c;
+    return RT_OK;
+}
+
+rt_status rt_launch_merge_hits(const HitEntry* list, const unsigned* count, int sms, cudaStream_t s)
+{
+    k_merge_hits<<<sms * 4, 256, 0, s>>>(list, count);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
 
 rt_status rt_launch_trace(const TraceArgs& a0, bool counted, cudaStream_t s, StageTiming* timing,
                           bool allow_concurrent)

@@ -808,4 +808,29 @@ __device__ __forceinline__ void store_hit(rt_hit* out, float t, int32_t prim, fl
     p[2] = make_float2(__int_as_float(tracer), __uint_as_float(flags));
 }
 
+// Append the lanes with `hit` set to a near-hit list (one atomic per warp):
+// the record dst, and the hit found (prim kFlagsOnly: none, flags only).
+__device__ __forceinline__ void append_hit_entry(HitEntry* list, unsigned* count, bool hit, rt_hit* dst,
+                                                 const Hit& best, uint32_t flags)
+{
+    const unsigned full = 0xffffffffu, lane = threadIdx.x & 31u;
+    const unsigned m = __ballot_sync(full, hit);
+    if (m == 0) return;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == (unsigned)leader) base = atomicAdd(count, (unsigned)__popc(m));
+    base = __shfl_sync(full, base, leader);
+    if (hit) {
+        HitEntry e;
+        e.dst = dst;
+        e.flags = flags;
+        e.t = best.t;
+        e.u = best.u;
+        e.v = best.v;
+        e.prim = best.prim;
+        e.pad = 0;
+        list[base + __popc(m & ((1u << lane) - 1u))] = e;
+    }
+}
+
 }  // namespace rtdev

@@ -452,6 +452,18 @@ def _mixed_batches(w, rq):
     lights = np.random.default_rng(2).uniform(0.3, np.array(s.room) - 0.3, size=(4, 3))
     sh = R.shadow_rays(p, nn, lights, 64, bias)
     mk = lambda **kw: rq.split_params(**kw)  # noqa: E731
+    c = np.array(s.room) / 2
+    odd = np.array([
+        [*c, 1.0, 1, 0, 0, 1.0],            # zero-length interval
+        [np.nan, 1, 1, 0, 1, 0, 0, 10],      # NaN origin
+        [-5, -5, -5, 0, 0, 0, 1, 100],       # outside the room
+        [*c, 0.0, 0, 1, 0, 100],             # axis-aligned direction
+        [*c, 3.0, 1, 0, 0, 2.0],             # t_min > t_max
+    ], dtype=np.float32)
+    odd = np.concatenate([odd, gi[:59]])
+    # closest-hit split batches with 0 < m_near < inf make the first two launches
+    # run side by side; the m_near = inf and m_near = 0 batches then go through
+    # that program too, as do the odd (invalid) queries
     return [
         (prim, mk(mode=rq.MODE_BVH)),
         (gi, mk(mode=rq.MODE_SPLIT1, m_near=2.0)),
@@ -461,6 +473,11 @@ def _mixed_batches(w, rq):
         (gi[:777], mk(mode=rq.MODE_SPLIT1, m_near=2.0, any_hit=True)),
         (gi[:0], mk(mode=rq.MODE_SDF)),
         (gi[:555], mk(mode=rq.MODE_SDF)),
+        (gi[:600], mk(mode=rq.MODE_SPLIT1, m_near=float("inf"))),
+        (gi[:300], mk(mode=rq.MODE_SPLIT2, m_near=0.0, m_far=2.0)),
+        (odd, mk(mode=rq.MODE_SPLIT2, m_near=2.0, m_far=2.0)),
+        (odd, mk(mode=rq.MODE_BVH)),
+        (odd, mk(mode=rq.MODE_SPLIT1, m_near=2.0, any_hit=True)),
     ]
 
 
@@ -473,6 +490,23 @@ def test_batches_equal_one_call_per_batch(tiny, tuning):
         if p.any_hit:
             assert torch.equal(got[:, 4] > 0, ref[:, 4] > 0)
             assert torch.equal(got[:, 4] == rq.TRACER_SDF, ref[:, 4] == rq.TRACER_SDF)
+        else:
+            assert torch.equal(got, ref), (p.mode, p.m_near)
+
+
+def test_batches_without_near_split_equal_one_call_per_batch(tiny):
+    """Without a closest-hit batch with 0 < m_near < inf the four launches run
+    in sequence; the records are the same as one call per batch."""
+    rq = tiny.rq
+    keep = [(r, p) for r, p in _mixed_batches(tiny, rq)
+            if p.any_hit or p.mode in (rq.MODE_BVH, rq.MODE_SDF) or not 0 < p.m_near < float("inf")]
+    assert len(keep) >= 6
+    batches = [(_cuda(r), p) for r, p in keep]
+    outs = rq.rt_trace_batches(tiny.scene, tiny.sdf, batches)
+    for (rays, p), got in zip(batches, outs):
+        ref = rq.rt_trace_combined(tiny.scene, tiny.sdf, rays, p)
+        if p.any_hit:
+            assert torch.equal(got[:, 4] > 0, ref[:, 4] > 0)
         else:
             assert torch.equal(got, ref), (p.mode, p.m_near)
 
