@@ -337,8 +337,9 @@ rt_status rt_trace_combined_counted(const rt_scene* scene, const rt_sdf* sdf, co
  * near hits; or the one launch of the simple kernel), *n_stages
  * the number of parts, stage_kind[k] RT_STAGE_* (nullable).  stage_ms and
  * stage_kind hold 6 entries.  Each part is timed by CUDA events on the
- * stream that ran it; in a closest-hit split call the near and field stages
- * run at the same time on two streams, so their times overlap.  The call
+ * stream that ran it; in a closest-hit split call with 0 < m_near < inf the
+ * near and field stages run at the same time on two streams, so their times
+ * overlap.  The call
  * synchronises `stream`.  Used to measure per-kernel throughput. */
 enum { RT_STAGE_ALL = 0, RT_STAGE_BVH_FULL = 1, RT_STAGE_BVH_NEAR = 2, RT_STAGE_BVH_FAR = 3,
        RT_STAGE_FIELD_FULL = 4, RT_STAGE_FIELD_SPLIT = 5, RT_STAGE_ORDER = 6, RT_STAGE_MERGE = 7,
@@ -366,7 +367,9 @@ rt_status rt_trace_combined_timed(const rt_scene* scene, const rt_sdf* sdf, cons
  *     results: serialise them, e.g. on one stream.  The counters are cleared
  *     on `stream` at the start of every call.
  *   - Always runs the wavefront stage kernels (the tuning's block, residency,
- *     refill, layout and query order apply); results equal rt_trace_combined's.
+ *     refill, layout and query order apply), their stages one after the other
+ *     on `stream` (not on the library's two streams); results equal
+ *     rt_trace_combined's.
  *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
 rt_status rt_trace_combined_noalloc(const rt_scene* scene, const rt_sdf* sdf, const rt_ray* d_rays, int64_t n,
                                     const rt_split_params* params, rt_hit* d_hits, void* stream);

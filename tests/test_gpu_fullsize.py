@@ -82,6 +82,36 @@ def test_fullsize_combined_every_ray(frame, m):
     assert rep["sdf_bit_equal"] == 1.0, rep
 
 
+@pytest.mark.parametrize("t_ao", [0.5, 10.0])
+def test_fullsize_ao_rays_both_programs_same_records(frame, t_ao):
+    """4,194,304 AO rays (262,144 surface points, 16 cosine rays each, Section 3
+    occlusion queries, closest hit) at m = 2 and m = 1.  The default path runs
+    the near triangle stage beside the field stage and then a second near launch
+    that takes what the first left: at t_ao = 0.5 m the near sub-intervals are
+    most of the work and that second launch traces a large share of them; at
+    10 m the field stage dominates.  The records must equal those of the
+    one-thread-per-query kernel, which traces each query's sub-intervals in
+    order, and every 16th query is checked against the checker."""
+    rq, s = frame["rq"], frame["s"]
+    pts, nn = R.surface_points(s, 1 << 18, 31)
+    rays = R.ao_rays(pts, nn, np.full(1 << 18, 16, dtype=np.int64), 32, t_ao, 1e-3 * s.diagonal)
+    rays_d = torch.from_numpy(rays).cuda()
+    for m in (2.0, 1.0):
+        p = rq.split_params(mode=rq.MODE_SPLIT1, m_near=m)
+        a = rq.rt_trace_combined(frame["scene"], frame["sdf"], rays_d, p)
+        prev = rq.rt_set_tuning(kernel=rq.KERNEL_SIMPLE)
+        try:
+            b = rq.rt_trace_combined(frame["scene"], frame["sdf"], rays_d, p)
+        finally:
+            rq.rt_set_tuning(prev)
+        assert torch.equal(a, b), (t_ao, m)
+        idx = np.arange(0, rays.shape[0], 16)
+        ti = torch.from_numpy(idx).cuda()
+        rep = _check(frame, dict(mode=1, m_near=m), rays[idx], rays_d[ti], hits=a[ti])
+        print(f"t_ao={t_ao} m={m}: {rep}")
+        assert rep["sdf_bit_equal"] == 1.0, rep
+
+
 def test_fullsize_one_thread_per_query_same_records(frame):
     """The benchmark also times the one-thread-per-query kernel: same records."""
     rq = frame["rq"]
