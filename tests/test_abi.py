@@ -41,6 +41,16 @@ def test_binding_export_list_matches_header():
     assert sorted(rq.EXPORTS) == _declared()
 
 
+def test_stage_names_match_the_header_enum():
+    """rt_trace_combined_timed reports each part's RT_STAGE_* kind; the binding
+    names them from the header's enum (RT_STAGE_BVH_NEAR -> "bvh_near")."""
+    import paper_2305_07253_gb300 as rq
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    enum = {int(v): k.lower() for k, v in re.findall(r"\bRT_STAGE_([A-Z_]+)\s*=\s*(\d+)", src)}
+    assert len(enum) >= 9 and enum[8] == "bvh_near_rest"
+    assert rq.STAGE_NAMES == enum
+
+
 def test_struct_sizes_match_header():
     import paper_2305_07253_gb300 as rq
     assert ctypes.sizeof(rq.rt_split_params) == 32
