@@ -414,7 +414,8 @@ def run_ours(args):
         "work_counts": {k: {"nodes": v[0], "tris": v[1], "steps": v[2], "field_queries": v[3], **outcome[k]}
                         for k, v in counts.items()},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": kernel_names.get(dom_stage, dom_stage) + ", combined m=2",
+                     "traffic": traffic, "kernel": kernel_names.get(dom_stage, dom_stage) + ", combined m=2"
+                     + (", beside the near stage on the same SMs" if "merge" in comb else ""),
                      "algorithmic_bytes_per_launch": ab, "launch_ms": dom_ms, "peak_kind": f"of {peak_kind}",
                      "step": {"algorithmic_bytes": stage_bytes("combined", "all"),
                               "GBps": stage_bytes("combined", "all") / (ms_mid * 1e-3) / 1e9},
