@@ -216,3 +216,52 @@ def test_cascade_endpoints_equal_pure_techniques(any_hit):
     assert hit.mean() > 0.9
     lv = cas.level_of(rays[hit, 0:3].astype(np.float64) + h["t"][hit, None] * rays[hit, 4:7].astype(np.float64))
     assert len(set(lv.tolist())) >= 2
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_near_hits_over_the_field_from_t1_equal_the_in_order_query(mode):
+    """The sub-intervals of Eq. 2 are ordered: a hit in [t_min, t_1] lies before
+    any point of [t_1, t_max].  So a closest-hit query can trace its field (and
+    far) sub-intervals from t_1 without waiting for its near result, and put the
+    near hit, where there is one, over their record (Section 2; the concurrent
+    program of the stage kernels relies on it).  Checked on the checker alone:
+    the near sub-interval as a triangles-only query on [t_min, t_1], the rest
+    as a query starting at t_1 with m_near = 0, merged, against the in-order
+    query, with the t_1 of every query taken from the checker (float mode, so t_1
+    is a float and the rays can carry it)."""
+    s = S.make_scene("tiny")
+    bvh = O.BVH(s.verts, s.tris)
+    n, L = 16, 4
+    shell = O.Cascade(s.camera.eye, 0.0625, n, L, values=np.zeros((L, n, n, n)))
+    vals = np.stack([bvh.sdf_points(shell.points(k)) for k in range(L)])
+    cas = O.Cascade(s.camera.eye, 0.0625, n, L, values=vals)
+    rays = R.gi_rays(s, 3000, 46, s.diagonal)
+    for m in (0.5, 2.0, 8.0):
+        p = O.make_params(mode=mode, m_near=m, m_far=2.0)
+        ref, t12 = O.trace_combined(bvh, cas, rays, p, 32, split_points=True)
+        t1 = t12[:, 0]
+        assert np.all(np.isfinite(t1)) and np.array_equal(t1.astype(np.float32).astype(np.float64), t1)
+        near_rays = rays.copy()
+        near_rays[:, 7] = t1
+        near = O.trace_combined(bvh, cas, near_rays, O.make_params(mode=0), 32)
+        rest_rays = rays.copy()
+        rest_rays[:, 3] = t1
+        rest = O.trace_combined(bvh, cas, rest_rays, O.make_params(mode=mode, m_near=0.0, m_far=2.0), 32)
+        if mode == 1:
+            # with m_near > 0 the field sub-interval [t_1, t_max] is empty when t_1 = t_max
+            # (with m_near = 0 it would be the closed point t_max): a miss there
+            empty = t1 >= rays[:, 7]
+            rest["tracer"][empty] = 0
+            rest["t"][empty] = np.inf
+            rest["prim"][empty] = -1
+        got = rest.copy()
+        hit = near["tracer"] == 1
+        got[hit] = near[hit]
+        assert 0 < hit.sum() < rays.shape[0], (mode, m)
+        for f in ("tracer", "prim"):
+            np.testing.assert_array_equal(got[f], ref[f], err_msg=f"{f} mode={mode} m={m}")
+        fin = np.isfinite(ref["t"])
+        np.testing.assert_array_equal(np.isfinite(got["t"]), fin)
+        np.testing.assert_array_equal(got["t"][fin], ref["t"][fin])
+        np.testing.assert_array_equal(got["u"][hit], ref["u"][hit])
+        np.testing.assert_array_equal(got["v"][hit], ref["v"][hit])
